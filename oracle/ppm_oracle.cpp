@@ -1,0 +1,1025 @@
+/*
+ * ppm_oracle.cpp -- plain FP64 CPU oracle for the PPM+PPB 1-D sweeps.
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by the tests, the smoke check and the
+ * benchmark's CPU-baseline leg; never by the CUDA library.  See ppm_oracle.h
+ * for what pins each step.
+ *
+ * The paper (Woodward et al., Sec. 1 and Sec. 4) names the ingredients of the
+ * pass but prints no formulas; each step below states the published method it
+ * restates and the reading taken where the paper is silent:
+ *   - perturbation form about a hydrostatic base state (Sec. 1, "subtract it
+ *     out"): rho' = rho - rho0, E' = E - p0/(gamma-1), p' = p - p0;
+ *   - interface values one order higher than the parabola (Sec. 1): the
+ *     fourth-order centred formula of Colella & Woodward (1984);
+ *   - smoothness judged on the 5-cell stencil centred on the cell, no
+ *     monotonicity constraints where smooth (Sec. 1): third differences
+ *     compared against first and second differences (a reading);
+ *   - parabola, monotonicity constraints, flattening and characteristic
+ *     tracing: Colella & Woodward (1984);
+ *   - approximate Riemann solver: acoustic guess plus one two-shock update,
+ *     written in difference form so equal states give back exactly p' and u;
+ *   - PPB fractional-volume advection (Sec. 1, Sec. 4; van Leer's scheme VI
+ *     lineage): FV with its three first moments, parabolic sub-cell profile,
+ *     exact swept-region integrals, Zalesak (1979) flux-corrected transport
+ *     for 0 <= FV <= 1;
+ *   - directional splitting (Sec. 1, Sec. 4), ghost width 4 (Sec. 4).
+ * Compile with -ffp-contract=off: no fused multiply-adds.
+ */
+#include "ppm_oracle.h"
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace {
+
+constexpr int G = 4;                     // ghost cells per side (Sec. 4: stencil reaches 4 cells)
+constexpr double C_SMOOTH = 0.5;         // detector: smooth iff T <= C_SMOOTH * S + EPS_SMOOTH * scale
+constexpr double EPS_SMOOTH = 1e-9;      // detector floor, relative to rho / c / p of the cell
+constexpr double EPS_SHOCK = 0.33;       // flattening: relative pressure jump
+constexpr double OMEGA1 = 0.75, OMEGA2 = 10.0;
+constexpr double P_FLOOR = 1e-10;        // Riemann: p* >= P_FLOOR * min(pL, pR)
+
+std::atomic<long long> g_cnt[6];
+int g_threads = 0;
+
+// --------------------------------------------------------------------------
+// Scalar types: plain double, and a counted double for the flop census.
+// --------------------------------------------------------------------------
+struct Counted {
+    double v;
+    static thread_local long long flops;
+    static thread_local long long selects;
+    Counted() : v(0.0) {}
+    Counted(double x) : v(x) {}  // NOLINT: implicit by design
+};
+thread_local long long Counted::flops = 0;
+thread_local long long Counted::selects = 0;
+
+inline Counted operator+(Counted a, Counted b) { ++Counted::flops; return Counted(a.v + b.v); }
+inline Counted operator-(Counted a, Counted b) { ++Counted::flops; return Counted(a.v - b.v); }
+inline Counted operator*(Counted a, Counted b) { ++Counted::flops; return Counted(a.v * b.v); }
+inline Counted operator/(Counted a, Counted b) { ++Counted::flops; return Counted(a.v / b.v); }
+inline Counted operator-(Counted a) { return Counted(-a.v); }
+inline Counted &operator+=(Counted &a, Counted b) { a = a + b; return a; }
+inline Counted &operator-=(Counted &a, Counted b) { a = a - b; return a; }
+inline Counted &operator*=(Counted &a, Counted b) { a = a * b; return a; }
+inline bool operator<(Counted a, Counted b) { ++Counted::selects; return a.v < b.v; }
+inline bool operator>(Counted a, Counted b) { ++Counted::selects; return a.v > b.v; }
+inline bool operator<=(Counted a, Counted b) { ++Counted::selects; return a.v <= b.v; }
+inline bool operator>=(Counted a, Counted b) { ++Counted::selects; return a.v >= b.v; }
+inline bool operator!=(Counted a, Counted b) { ++Counted::selects; return a.v != b.v; }
+
+inline double val(double x) { return x; }
+inline double val(Counted x) { return x.v; }
+inline double Sqrt(double x) { return std::sqrt(x); }
+inline Counted Sqrt(Counted x) { ++Counted::flops; return Counted(std::sqrt(x.v)); }
+inline double Abs(double x) { return std::fabs(x); }
+inline Counted Abs(Counted x) { ++Counted::selects; return Counted(std::fabs(x.v)); }
+inline double Max(double a, double b) { return a > b ? a : b; }
+inline Counted Max(Counted a, Counted b) { ++Counted::selects; return a.v > b.v ? a : b; }
+inline double Min(double a, double b) { return a < b ? a : b; }
+inline Counted Min(Counted a, Counted b) { ++Counted::selects; return a.v < b.v ? a : b; }
+
+template <class R> inline R Clamp(R x, R lo, R hi) { return Min(Max(x, lo), hi); }
+
+// --------------------------------------------------------------------------
+// Base state and source tables: linear interpolation on a uniform grid.
+// --------------------------------------------------------------------------
+template <class R>
+R lerp_tab(const oracle_problem *pb, const double *tab, R s) {
+    R u = (s - R(pb->s0)) / R(pb->ds);
+    double fl = std::floor(val(u));
+    int i = (int)std::min(std::max(fl, 0.0), (double)(pb->ntab - 2));
+    R w = u - R((double)i);
+    return R(tab[i]) + w * (R(tab[i + 1]) - R(tab[i]));
+}
+
+template <class R>
+struct BasePoint {
+    R rho0, p0, g[3];
+};
+
+// Hydrostatic base state and gravity at a point (Sec. 1: the initial,
+// spherically symmetric state saved on the grid).
+template <class R>
+BasePoint<R> base_at(const oracle_problem *pb, const R xyz[3]) {
+    BasePoint<R> b;
+    b.g[0] = b.g[1] = b.g[2] = R(0.0);
+    if (pb->grav == 0) {
+        b.rho0 = R(pb->rho0[0]);
+        b.p0 = R(pb->p0[0]);
+    } else if (pb->grav == 1) {
+        b.rho0 = lerp_tab(pb, pb->rho0, xyz[2]);
+        b.p0 = lerp_tab(pb, pb->p0, xyz[2]);
+        b.g[2] = lerp_tab(pb, pb->g, xyz[2]);
+    } else {
+        R r = Sqrt(xyz[0] * xyz[0] + xyz[1] * xyz[1] + xyz[2] * xyz[2]);
+        b.rho0 = lerp_tab(pb, pb->rho0, r);
+        b.p0 = lerp_tab(pb, pb->p0, r);
+        if (r > R(0.0)) {
+            R gor = lerp_tab(pb, pb->g, r) / r;
+            for (int d = 0; d < 3; ++d) b.g[d] = gor * xyz[d];
+        }
+    }
+    return b;
+}
+
+// Table coordinate of a point for the heating / damping profiles.
+template <class R>
+R source_coord(const oracle_problem *pb, const R xyz[3]) {
+    if (pb->grav == 1) return xyz[2];
+    return Sqrt(xyz[0] * xyz[0] + xyz[1] * xyz[1] + xyz[2] * xyz[2]);
+}
+
+inline int extent(const oracle_problem *pb, int a) { return a == 0 ? pb->nx : (a == 1 ? pb->ny : pb->nz); }
+inline double origin(const oracle_problem *pb, int a) { return a == 0 ? pb->x0 : (a == 1 ? pb->y0 : pb->z0); }
+
+// Ghost-cell index mapping along a pencil (periodic wrap or mirror).
+inline int map_cell(int i, int n, int bc_lo, int bc_hi, bool *flip) {
+    *flip = false;
+    if (i < 0) {
+        if (bc_lo == 0) return i + n;
+        *flip = true;
+        return -1 - i;
+    }
+    if (i >= n) {
+        if (bc_hi == 0) return i - n;
+        *flip = true;
+        return 2 * n - 1 - i;
+    }
+    return i;
+}
+
+// Position (in cells from the low boundary) of face j+1/2 after mapping
+// through the boundary conditions.
+inline int map_face(int j, int n, int bc_lo, int bc_hi) {
+    int P = j + 1;
+    if (P < 0) return bc_lo == 0 ? P + n : -P;
+    if (P > n) return bc_hi == 0 ? P - n : 2 * n - P;
+    if (P == n && bc_hi == 0) return 0;
+    return P;
+}
+
+inline size_t cell_index(const oracle_problem *pb, int axis, int i, int ja, int jb) {
+    int ijk[3];
+    ijk[axis] = i;
+    ijk[(axis + 1) % 3] = ja;
+    ijk[(axis + 2) % 3] = jb;
+    return ((size_t)ijk[2] * pb->ny + ijk[1]) * pb->nx + ijk[0];
+}
+
+template <class R>
+void cell_position(const oracle_problem *pb, int axis, int i, int ja, int jb, R xyz[3]) {
+    int ijk[3];
+    ijk[axis] = i;
+    ijk[(axis + 1) % 3] = ja;
+    ijk[(axis + 2) % 3] = jb;
+    for (int d = 0; d < 3; ++d) xyz[d] = R(origin(pb, d)) + (R((double)ijk[d]) + R(0.5)) * R(pb->dx);
+}
+
+// --------------------------------------------------------------------------
+// One pencil: all per-cell and per-face arrays of one 1-D pass.
+// Cell i lives at [i+G] for i in [-G, n+G); face j+1/2 lives at [j+G].
+// --------------------------------------------------------------------------
+enum { V_R = 0, V_U = 1, V_V = 2, V_W = 3, V_P = 4, NH = 5 };
+
+template <class R>
+struct Pencil {
+    int n = 0, axis = 0, ja = 0, jb = 0;
+    bool wall_lo = false, wall_hi = false;
+    // conserved, deviation form, rotated frame (n = along the pass)
+    std::vector<R> rd, mn, mt1, mt2, ed, fv, on, ot1, ot2;
+    // base state at cells and faces
+    std::vector<R> rho0c, p0c, gn, rho0f, p0f;
+    // primitives
+    std::vector<R> rho, cs, c2, pfull;
+    std::vector<R> W[NH];                       // rho', u, v, w, p'
+    std::vector<R> af[NH];                      // interface values
+    std::vector<char> smooth[NH];
+    std::vector<R> flat;
+    std::vector<R> PL[NH], PR[NH], PD[NH], P6[NH];
+    std::vector<R> WL[NH], WR[NH];              // traced states left/right of face j+1/2
+    std::vector<R> us, ps, Fr, Fn, Ft1, Ft2, FE; // Riemann + fluxes at faces
+    std::vector<R> rdn, mnn, mt1n, mt2n, edn;   // hydro update
+    std::vector<R> meff, aeff;                  // PPB bound-limited profile coefficients
+    std::vector<R> GL, GH, KL, KH, T1, T2;      // PPB face transfers
+    std::vector<R> PHI, KM;                     // mass transfer and its first moment
+    std::vector<R> Rp, Rm, Gf, Kf;              // FCT
+    std::vector<R> fvn, onn, ot1n, ot2n;
+    long long c_nonsmooth = 0, c_flat = 0, c_theta = 0, c_fct = 0, c_clamp = 0;
+
+    void alloc(int n_) {
+        n = n_;
+        size_t m = (size_t)n + 2 * G;
+        for (auto *v : {&rd, &mn, &mt1, &mt2, &ed, &fv, &on, &ot1, &ot2, &rho0c, &p0c, &gn,
+                        &rho0f, &p0f, &rho, &cs, &c2, &pfull, &flat, &us, &ps, &Fr, &Fn, &Ft1,
+                        &Ft2, &FE, &rdn, &mnn, &mt1n, &mt2n, &edn, &meff, &aeff, &GL, &GH, &KL,
+                        &KH, &T1, &T2, &PHI, &KM, &Rp, &Rm, &Gf, &Kf, &fvn, &onn, &ot1n, &ot2n})
+            v->assign(m, R(0.0));
+        for (int k = 0; k < NH; ++k) {
+            for (auto *v : {&W[k], &af[k], &PL[k], &PR[k], &PD[k], &P6[k], &WL[k], &WR[k]})
+                v->assign(m, R(0.0));
+            smooth[k].assign(m, 1);
+        }
+    }
+    static int at(int i) { return i + G; }
+};
+
+// Step a1: gather one pencil with ghosts, subtract the base state.
+template <class R>
+void gather(const oracle_problem *pb, Pencil<R> &P, double *const q[9]) {
+    const int a = P.axis, n = P.n;
+    const int bl = pb->bc[2 * a], bh = pb->bc[2 * a + 1];
+    P.wall_lo = (bl == 1);
+    P.wall_hi = (bh == 1);
+    const R gm1 = R(pb->gamma - 1.0);
+    const int t1 = (a + 1) % 3, t2 = (a + 2) % 3;
+    for (int i = -G; i < n + G; ++i) {
+        bool flip;
+        int m = map_cell(i, n, bl, bh, &flip);
+        size_t c = cell_index(pb, a, m, P.ja, P.jb);
+        R xyz[3];
+        cell_position(pb, a, m, P.ja, P.jb, xyz);
+        BasePoint<R> b = base_at(pb, xyz);
+        const int k = Pencil<R>::at(i);
+        R sgn = flip ? R(-1.0) : R(1.0);
+        P.rho0c[k] = b.rho0;
+        P.p0c[k] = b.p0;
+        P.gn[k] = flip ? -b.g[a] : b.g[a];
+        P.rd[k] = R(q[0][c]) - b.rho0;
+        P.mn[k] = flip ? -R(q[1 + a][c]) : R(q[1 + a][c]);
+        P.mt1[k] = R(q[1 + t1][c]);
+        P.mt2[k] = R(q[1 + t2][c]);
+        P.ed[k] = R(q[4][c]) - b.p0 / gm1;
+        P.fv[k] = R(q[5][c]);
+        P.on[k] = flip ? -R(q[6 + a][c]) : R(q[6 + a][c]);
+        P.ot1[k] = R(q[6 + t1][c]);
+        P.ot2[k] = R(q[6 + t2][c]);
+        (void)sgn;
+    }
+    // base state at faces j+1/2, j in [-G, n+G-1]
+    const R lo = R(origin(pb, a));
+    for (int j = -G; j < n + G; ++j) {
+        int Pf = map_face(j, n, bl, bh);
+        R xyz[3];
+        cell_position(pb, a, 0, P.ja, P.jb, xyz);
+        xyz[a] = lo + R((double)Pf) * R(pb->dx);
+        BasePoint<R> b = base_at(pb, xyz);
+        P.rho0f[Pencil<R>::at(j)] = b.rho0;
+        P.p0f[Pencil<R>::at(j)] = b.p0;
+    }
+}
+
+// Step a1 (cont.): primitive variables in perturbation form; p' from E'
+// with the base energy cancelled exactly (Sec. 1).
+template <class R>
+void primitives(const oracle_problem *pb, Pencil<R> &P) {
+    const R gam = R(pb->gamma), gm1 = R(pb->gamma - 1.0);
+    for (int i = -G; i < P.n + G; ++i) {
+        const int k = Pencil<R>::at(i);
+        R rho = P.rho0c[k] + P.rd[k];
+        R u = P.mn[k] / rho, v = P.mt1[k] / rho, w = P.mt2[k] / rho;
+        R ke = R(0.5) * (P.mn[k] * u + (P.mt1[k] * v + P.mt2[k] * w));
+        R pd = gm1 * (P.ed[k] - ke);
+        R p = P.p0c[k] + pd;
+        R c2 = gam * p / rho;
+        P.rho[k] = rho;
+        P.pfull[k] = p;
+        P.c2[k] = c2;
+        P.cs[k] = Sqrt(c2);
+        P.W[V_R][k] = P.rd[k];
+        P.W[V_U][k] = u;
+        P.W[V_V][k] = v;
+        P.W[V_W][k] = w;
+        P.W[V_P][k] = pd;
+    }
+}
+
+// Step a2: interface values, fourth order (one order above the parabola, Sec. 1).
+template <class R>
+void interface_values(Pencil<R> &P) {
+    for (int v = 0; v < NH; ++v)
+        for (int j = -G + 1; j <= P.n + G - 3; ++j) {
+            const auto &a = P.W[v];
+            const int k = Pencil<R>::at(j);
+            P.af[v][k] = (R(7.0) * (a[k] + a[k + 1]) - (a[k - 1] + a[k + 2])) * R(1.0 / 12.0);
+        }
+}
+
+// Step a3: smoothness on the 5-cell stencil centred on the cell (Sec. 1).
+// Reading: third differences T against first/second differences S;
+// smooth iff T <= C_SMOOTH * S + EPS_SMOOTH * scale, where scale is the
+// cell's full density (for rho'), sound speed (velocities) or full pressure
+// (p'), so that round-off noise on flat data counts as smooth.
+template <class R>
+void smoothness(Pencil<R> &P) {
+    for (int v = 0; v < NH; ++v)
+        for (int i = -G + 2; i <= P.n + G - 3; ++i) {
+            const auto &a = P.W[v];
+            const int k = Pencil<R>::at(i);
+            const R scale = (v == V_R) ? P.rho[k] : ((v == V_P) ? P.pfull[k] : P.cs[k]);
+            R d1m2 = a[k - 1] - a[k - 2];
+            R d1m1 = a[k] - a[k - 1];
+            R d10 = a[k + 1] - a[k];
+            R d1p1 = a[k + 2] - a[k + 1];
+            R d2m = d1m1 - d1m2, d20 = d10 - d1m1, d2p = d1p1 - d10;
+            R T = Max(Abs(d20 - d2m), Abs(d2p - d20));
+            R S = Max(Max(Abs(d1m1), Abs(d10)), Max(Max(Abs(d2m), Abs(d20)), Abs(d2p)));
+            P.smooth[v][k] = (T <= R(C_SMOOTH) * S + R(EPS_SMOOTH) * scale) ? 1 : 0;
+        }
+    for (int i = 0; i < P.n; ++i) {
+        const int k = Pencil<R>::at(i);
+        bool any = false;
+        for (int v = 0; v < NH; ++v) any = any || !P.smooth[v][k];
+        if (any) ++P.c_nonsmooth;
+    }
+}
+
+// Step a3 (cont.): shock flattening coefficient (Colella & Woodward 1984),
+// without the neighbour maximum so the stencil stays within +-2 cells.
+template <class R>
+void flattening(Pencil<R> &P) {
+    for (int i = -G + 2; i <= P.n + G - 3; ++i) {
+        const int k = Pencil<R>::at(i);
+        const auto &pd = P.W[V_P];
+        const auto &u = P.W[V_U];
+        R dp1 = pd[k + 1] - pd[k - 1];
+        R dp2 = pd[k + 2] - pd[k - 2];
+        R pmin = Min(P.pfull[k + 1], P.pfull[k - 1]);
+        R f = R(0.0);
+        if (Abs(dp1) > R(EPS_SHOCK) * pmin && u[k - 1] - u[k + 1] > R(0.0)) {
+            R r = (dp2 != R(0.0)) ? dp1 / dp2 : R(1.0);
+            f = Clamp(R(OMEGA2) * (r - R(OMEGA1)), R(0.0), R(1.0));
+        }
+        P.flat[k] = f;
+        if (i >= 0 && i < P.n && val(f) > 0.0) ++P.c_flat;
+    }
+}
+
+// Step a4: parabolas; constraints only where the detector found the cell
+// non-smooth (Sec. 1), in the form of Colella & Woodward (1984).
+template <class R>
+void parabolas(Pencil<R> &P) {
+    for (int v = 0; v < NH; ++v)
+        for (int i = -G + 2; i <= P.n + G - 3; ++i) {
+            const int k = Pencil<R>::at(i);
+            const auto &A = P.W[v];
+            R a = A[k];
+            R aL = P.af[v][k - 1], aR = P.af[v][k];
+            R f = P.flat[k];
+            if (f > R(0.0)) {
+                aL = aL + f * (a - aL);
+                aR = aR + f * (a - aR);
+            }
+            if (!P.smooth[v][k]) {
+                aL = Clamp(aL, Min(A[k - 1], a), Max(A[k - 1], a));
+                aR = Clamp(aR, Min(a, A[k + 1]), Max(a, A[k + 1]));
+                if ((aR - a) * (a - aL) <= R(0.0)) {
+                    aL = a;
+                    aR = a;
+                } else {
+                    R da = aR - aL;
+                    R dm = a - R(0.5) * (aL + aR);
+                    R d6 = da * da * R(1.0 / 6.0);
+                    if (da * dm > d6)
+                        aL = R(3.0) * a - R(2.0) * aR;
+                    else if (-d6 > da * dm)
+                        aR = R(3.0) * a - R(2.0) * aL;
+                }
+            }
+            P.PL[v][k] = aL;
+            P.PR[v][k] = aR;
+            P.PD[v][k] = aR - aL;
+            P.P6[v][k] = R(6.0) * (a - R(0.5) * (aL + aR));
+        }
+}
+
+// Average of the parabola over a domain of dependence of width sigma (in
+// cells) next to the right edge (fR) or the left edge (fL) of the cell.
+template <class R>
+inline R fR(const Pencil<R> &P, int v, int k, R s) {
+    return P.PR[v][k] - R(0.5) * s * (P.PD[v][k] - (R(1.0) - R(2.0 / 3.0) * s) * P.P6[v][k]);
+}
+template <class R>
+inline R fL(const Pencil<R> &P, int v, int k, R s) {
+    return P.PL[v][k] + R(0.5) * s * (P.PD[v][k] + (R(1.0) - R(2.0 / 3.0) * s) * P.P6[v][k]);
+}
+
+// Step a5: characteristic tracing of the three wave families u-c, u, u+c
+// (Colella & Woodward 1984), plus half a step of the buoyancy acceleration
+// (rho'/rho) g (Sec. 1 perturbation form).
+template <class R>
+void trace(const oracle_problem *pb, Pencil<R> &P, R dt) {
+    const R dtdx = dt / R(pb->dx);
+    for (int i = -G + 2; i <= P.n + G - 3; ++i) {
+        const int k = Pencil<R>::at(i);
+        const R u = P.W[V_U][k], c = P.cs[k], c2 = P.c2[k];
+        const R C = P.rho[k] * c;
+        const R lm = u - c, l0 = u, lp = u + c;
+        const R gp = (P.rd[k] / P.rho[k]) * P.gn[k];
+        const R hg = R(0.5) * dt * gp;
+        // right edge -> left state of face i+1/2
+        {
+            R st[NH];
+            R sp = Max(lp, R(0.0)) * dtdx;
+            for (int v = 0; v < NH; ++v) st[v] = fR(P, v, k, sp);
+            R ref_r = st[V_R], ref_u = st[V_U], ref_p = st[V_P], ref_v = st[V_V], ref_w = st[V_W];
+            if (l0 > R(0.0)) {
+                R s0 = l0 * dtdx;
+                R dr = ref_r - fR(P, V_R, k, s0);
+                R dp = ref_p - fR(P, V_P, k, s0);
+                st[V_R] = st[V_R] - (dr - dp / c2);
+                st[V_V] = st[V_V] - (ref_v - fR(P, V_V, k, s0));
+                st[V_W] = st[V_W] - (ref_w - fR(P, V_W, k, s0));
+            }
+            if (lm > R(0.0)) {
+                R sm = lm * dtdx;
+                R du = ref_u - fR(P, V_U, k, sm);
+                R dp = ref_p - fR(P, V_P, k, sm);
+                R A = R(0.5) * (dp - C * du);
+                st[V_R] = st[V_R] - A / c2;
+                st[V_U] = st[V_U] + A / C;
+                st[V_P] = st[V_P] - A;
+            }
+            st[V_U] = st[V_U] + hg;
+            for (int v = 0; v < NH; ++v) P.WL[v][k] = st[v];
+        }
+        // left edge -> right state of face i-1/2
+        {
+            R st[NH];
+            R sm = Max(-lm, R(0.0)) * dtdx;
+            for (int v = 0; v < NH; ++v) st[v] = fL(P, v, k, sm);
+            R ref_r = st[V_R], ref_u = st[V_U], ref_p = st[V_P], ref_v = st[V_V], ref_w = st[V_W];
+            if (l0 < R(0.0)) {
+                R s0 = -l0 * dtdx;
+                R dr = ref_r - fL(P, V_R, k, s0);
+                R dp = ref_p - fL(P, V_P, k, s0);
+                st[V_R] = st[V_R] - (dr - dp / c2);
+                st[V_V] = st[V_V] - (ref_v - fL(P, V_V, k, s0));
+                st[V_W] = st[V_W] - (ref_w - fL(P, V_W, k, s0));
+            }
+            if (lp < R(0.0)) {
+                R s1 = -lp * dtdx;
+                R du = ref_u - fL(P, V_U, k, s1);
+                R dp = ref_p - fL(P, V_P, k, s1);
+                R A = R(0.5) * (dp + C * du);
+                st[V_R] = st[V_R] - A / c2;
+                st[V_U] = st[V_U] - A / C;
+                st[V_P] = st[V_P] - A;
+            }
+            st[V_U] = st[V_U] + hg;
+            for (int v = 0; v < NH; ++v) P.WR[v][k - 1] = st[v];
+        }
+    }
+}
+
+// Steps a6-a7: approximate Riemann solver and fluxes at face j+1/2.
+template <class R>
+void riemann_fluxes(const oracle_problem *pb, Pencil<R> &P) {
+    const R gam = R(pb->gamma), gm1 = R(pb->gamma - 1.0);
+    const R kk = R((pb->gamma + 1.0) / (2.0 * pb->gamma));
+    const R gg1 = R(pb->gamma / (pb->gamma - 1.0));
+    for (int j = -G + 2; j <= P.n + G - 4; ++j) {
+        const int k = Pencil<R>::at(j);
+        const R r0 = P.rho0f[k], p0 = P.p0f[k];
+        const R rdL = P.WL[V_R][k], uL = P.WL[V_U][k], pdL = P.WL[V_P][k];
+        const R rdR = P.WR[V_R][k], uR = P.WR[V_U][k], pdR = P.WR[V_P][k];
+        const R rL = r0 + rdL, pL = p0 + pdL;
+        const R rR = r0 + rdR, pR = p0 + pdR;
+        const R CL = Sqrt(gam * pL * rL), CR = Sqrt(gam * pR * rR);
+        const R pfl = R(P_FLOOR) * Min(pL, pR);
+        // acoustic guess, difference form
+        R den = CL + CR;
+        R pst = pdL + CL * (CR * (uL - uR) + (pdR - pdL)) / den;
+        R ust = uL + (CR * (uR - uL) + (pdL - pdR)) / den;
+        if (p0 + pst < pfl) pst = pfl - p0;
+        // one two-shock impedance update
+        const R WLi = CL * Sqrt(R(1.0) + kk * (pst - pdL) / pL);
+        const R WRi = CR * Sqrt(R(1.0) + kk * (pst - pdR) / pR);
+        den = WLi + WRi;
+        pst = pdL + WLi * (WRi * (uL - uR) + (pdR - pdL)) / den;
+        ust = uL + (WRi * (uR - uL) + (pdL - pdR)) / den;
+        if (p0 + pst < pfl) pst = pfl - p0;
+        if ((j == -1 && P.wall_lo) || (j == P.n - 1 && P.wall_hi)) ust = R(0.0);
+        // upwind side of the contact
+        const bool left = (ust >= R(0.0));
+        const R rds = left ? rdL : rdR;
+        const R pds = left ? pdL : pdR;
+        const R rs = left ? rL : rR;
+        const R pss = left ? pL : pR;
+        const R vst = left ? P.WL[V_V][k] : P.WR[V_V][k];
+        const R wst = left ? P.WL[V_W][k] : P.WR[V_W][k];
+        const R dps = pst - pds;
+        const R rdst = rds + rs * dps / (gam * pss + R(0.5) * gm1 * dps);
+        // fluxes (Sec. 1 perturbation form)
+        const R rst = r0 + rdst;
+        const R Fr = rst * ust;
+        const R h0 = gg1 * p0;
+        P.us[k] = ust;
+        P.ps[k] = pst;
+        P.Fr[k] = Fr;
+        P.Fn[k] = Fr * ust + pst;
+        P.Ft1[k] = Fr * vst;
+        P.Ft2[k] = Fr * wst;
+        P.FE[k] = ust * (gg1 * pst + h0) + R(0.5) * (ust * ust + (vst * vst + wst * wst)) * Fr;
+    }
+}
+
+// Step a8: conservative update with the gravity sources of the perturbation
+// equations: momentum += dt rho' g (time-centred rho'), energy += dt g times
+// the time-centred mass flux.
+template <class R>
+void hydro_update(const oracle_problem *pb, Pencil<R> &P, R dt) {
+    const R dtdx = dt / R(pb->dx);
+    for (int i = -1; i <= P.n; ++i) {
+        const int k = Pencil<R>::at(i);
+        const R g = P.gn[k];
+        const R rdn = P.rd[k] - dtdx * (P.Fr[k] - P.Fr[k - 1]);
+        P.rdn[k] = rdn;
+        P.mnn[k] = P.mn[k] - dtdx * (P.Fn[k] - P.Fn[k - 1]) + dt * g * (R(0.5) * (P.rd[k] + rdn));
+        P.mt1n[k] = P.mt1[k] - dtdx * (P.Ft1[k] - P.Ft1[k - 1]);
+        P.mt2n[k] = P.mt2[k] - dtdx * (P.Ft2[k] - P.Ft2[k - 1]);
+        P.edn[k] = P.ed[k] - dtdx * (P.FE[k] - P.FE[k - 1]) + dt * g * (R(0.5) * (P.Fr[k - 1] + P.Fr[k]));
+    }
+}
+
+// Step a9a: PPB sub-cell profile along the pass,
+// f(xi) = FV + m xi + a2 (xi^2 - 1/12), a2 = (m_{i+1} - m_{i-1})/4,
+// scaled by theta in [0,1] when it would leave [0,1] on the cell.
+template <class R>
+void ppb_profiles(Pencil<R> &P) {
+    for (int i = -G + 1; i <= P.n + G - 2; ++i) {
+        const int k = Pencil<R>::at(i);
+        const R F = P.fv[k], m = P.on[k];
+        const R a2 = R(0.25) * (P.on[k + 1] - P.on[k - 1]);
+        const R ep = R(0.5) * m + a2 * R(1.0 / 6.0);
+        const R em = a2 * R(1.0 / 6.0) - R(0.5) * m;
+        R gmax = Max(ep, em), gmin = Min(ep, em);
+        if (a2 != R(0.0)) {
+            const R xv = -m / (R(2.0) * a2);
+            if (Abs(xv) < R(0.5)) {
+                const R gv = m * xv + a2 * (xv * xv - R(1.0 / 12.0));
+                gmax = Max(gmax, gv);
+                gmin = Min(gmin, gv);
+            }
+        }
+        R th = R(1.0);
+        if (F + gmax > R(1.0)) th = Min(th, (R(1.0) - F) / gmax);
+        if (F + gmin < R(0.0)) th = Min(th, F / (-gmin));
+        if (i >= 0 && i < P.n && val(th) < 1.0) ++P.c_theta;
+        P.meff[k] = th * m;
+        P.aeff[k] = th * a2;
+    }
+}
+
+// Step a9b: PPB transfers across face j+1/2: exact integrals of the donor's
+// profile over the swept region of width |u*| dt/dx (content and first
+// moment about the donor's centre), their donor-cell counterparts, and the
+// donor-cell transfer of the transverse moments.  Signed: positive = to +x.
+template <class R>
+void ppb_fluxes(const oracle_problem *pb, Pencil<R> &P, R dt) {
+    const R dtdx = dt / R(pb->dx);
+    for (int j = -G + 2; j <= P.n + G - 4; ++j) {
+        const int k = Pencil<R>::at(j);
+        const R sig = P.us[k] * dtdx;
+        const R phi = dtdx * P.Fr[k];
+        const bool fromleft = (sig >= R(0.0));
+        const int d = fromleft ? k : k + 1;
+        const R s = fromleft ? sig : -sig;
+        R M1 = R(0.5) - R(0.5) * s;
+        const R M2 = R(0.25) - R(0.5) * s + s * s * R(1.0 / 3.0);
+        R M3 = R(0.125) - R(0.375) * s + R(0.5) * s * s - R(0.25) * s * s * s;
+        if (!fromleft) {
+            M1 = -M1;
+            M3 = -M3;
+        }
+        const R F = P.fv[d], me = P.meff[d], ae = P.aeff[d];
+        const R phibar = F + me * M1 + ae * (M2 - R(1.0 / 12.0));
+        const R psibar = F * M1 + me * M2 + ae * (M3 - M1 * R(1.0 / 12.0));
+        P.GL[k] = phi * F;
+        P.GH[k] = phi * phibar;
+        P.KL[k] = phi * F * M1;
+        P.KH[k] = phi * psibar;
+        P.T1[k] = phi * P.ot1[d];
+        P.T2[k] = phi * P.ot2[d];
+        P.PHI[k] = phi;
+        P.KM[k] = phi * M1;
+    }
+}
+
+// Step a9c: Zalesak (1979) flux-corrected transport of rho*FV: the donor-cell
+// transfer plus the limited antidiffusive part.  Reading: the bounds are the
+// physical ones, 0 <= FV <= 1, not local extrema, so smooth extrema are never
+// clipped (Sec. 1: the PPB representation is almost never constrained).
+template <class R>
+void ppb_fct(Pencil<R> &P) {
+    for (int i = -1; i <= P.n; ++i) {
+        const int k = Pencil<R>::at(i);
+        const R rold = P.rho0c[k] + P.rd[k];
+        const R rnew = P.rho0c[k] + P.rdn[k];
+        const R cL = rold * P.fv[k] - (P.GL[k] - P.GL[k - 1]);
+        const R FVL = cL / rnew;
+        const R fmax = R(1.0);
+        const R fmin = R(0.0);
+        const R Ap = P.GH[k] - P.GL[k];
+        const R Am = P.GH[k - 1] - P.GL[k - 1];
+        const R Pp = Max(R(0.0), Am) - Min(R(0.0), Ap);
+        const R Pm = Max(R(0.0), Ap) - Min(R(0.0), Am);
+        const R Qp = (fmax - FVL) * rnew;
+        const R Qm = (FVL - fmin) * rnew;
+        P.Rp[k] = (Pp > R(0.0)) ? Clamp(Qp / Pp, R(0.0), R(1.0)) : R(0.0);
+        P.Rm[k] = (Pm > R(0.0)) ? Clamp(Qm / Pm, R(0.0), R(1.0)) : R(0.0);
+    }
+    for (int j = -1; j <= P.n - 1; ++j) {
+        const int k = Pencil<R>::at(j);
+        const R A = P.GH[k] - P.GL[k];
+        const R C = (A >= R(0.0)) ? Min(P.Rp[k + 1], P.Rm[k]) : Min(P.Rp[k], P.Rm[k + 1]);
+        if (val(A) != 0.0 && val(C) < 1.0) ++P.c_fct;
+        P.Gf[k] = P.GL[k] + C * A;
+        P.Kf[k] = P.KL[k] + C * (P.KH[k] - P.KL[k]);
+    }
+}
+
+// Step a9d: new FV and moments.  Content staying in the cell moves by the
+// mean of its two face displacements, content crossing a face by that
+// face's displacement; first moments are re-taken about the receiving
+// cell's centre.  The same rules move the mass (uniform density in each
+// piece), and the FV moment is the fluid-2 content moment minus FV times
+// the mass moment (so a uniform FV keeps a zero moment in compressing
+// flow).  Then each |m_d| <= 6 FV (1-FV): the largest first moment any
+// sub-cell profile with values in [0,1] can have (a step inside the cell).
+template <class R>
+void ppb_update(const oracle_problem *pb, Pencil<R> &P, R dt) {
+    const R dtdx = dt / R(pb->dx);
+    for (int i = 0; i < P.n; ++i) {
+        const int k = Pencil<R>::at(i);
+        const R rold = P.rho0c[k] + P.rd[k];
+        const R rnew = P.rho0c[k] + P.rdn[k];
+        const R sm = P.us[k - 1] * dtdx, sp = P.us[k] * dtdx;
+        const R cold = rold * P.fv[k];
+        R c_out = R(0.0), z_out = R(0.0), z_in = R(0.0);
+        R m_out = R(0.0), zr_out = R(0.0), zr_in = R(0.0);
+        if (sp >= R(0.0)) {
+            c_out = c_out + P.Gf[k];
+            z_out = z_out + P.Kf[k];
+            m_out = m_out + P.PHI[k];
+            zr_out = zr_out + P.KM[k];
+        } else {
+            const R sh = sp + R(1.0);
+            z_in = z_in + (-P.Kf[k] - P.Gf[k] * sh);
+            zr_in = zr_in + (-P.KM[k] - P.PHI[k] * sh);
+        }
+        if (sm >= R(0.0)) {
+            const R sh = sm - R(1.0);
+            z_in = z_in + (P.Kf[k - 1] + P.Gf[k - 1] * sh);
+            zr_in = zr_in + (P.KM[k - 1] + P.PHI[k - 1] * sh);
+        } else {
+            c_out = c_out - P.Gf[k - 1];
+            z_out = z_out - P.Kf[k - 1];
+            m_out = m_out - P.PHI[k - 1];
+            zr_out = zr_out - P.KM[k - 1];
+        }
+        // difference form: X_new = X + (X dPhi - dQ) / rho_new, with dPhi the
+        // net mass outflow and dQ the net outflow of rho*X, so that a cell
+        // with no net transfer keeps its values bit for bit
+        const R sbar = R(0.5) * (sm + sp);
+        const R dZc = (cold - c_out) * sbar + z_in - z_out;
+        const R Zr = (rold - m_out) * sbar + zr_in - zr_out;
+        const R dPhi = P.PHI[k] - P.PHI[k - 1];
+        const R dG = P.Gf[k] - P.Gf[k - 1];
+        R fvn = Clamp(P.fv[k] + (P.fv[k] * dPhi - dG) / rnew, R(0.0), R(1.0));
+        R onn = P.on[k] + (P.on[k] * dPhi + R(12.0) * (dZc - fvn * Zr)) / rnew;
+        R o1 = P.ot1[k] + (P.ot1[k] * dPhi - (P.T1[k] - P.T1[k - 1])) / rnew;
+        R o2 = P.ot2[k] + (P.ot2[k] * dPhi - (P.T2[k] - P.T2[k - 1])) / rnew;
+        const R bnd = R(6.0) * fvn * (R(1.0) - fvn);
+        if (Abs(onn) > bnd || Abs(o1) > bnd || Abs(o2) > bnd) {
+            onn = Clamp(onn, -bnd, bnd);
+            o1 = Clamp(o1, -bnd, bnd);
+            o2 = Clamp(o2, -bnd, bnd);
+            ++P.c_clamp;
+        }
+        P.fvn[k] = fvn;
+        P.onn[k] = onn;
+        P.ot1n[k] = o1;
+        P.ot2n[k] = o2;
+    }
+}
+
+// Heating and damping (applied after the Z pass of X Y Z and the X pass of
+// Z Y X): E' += dt*heat(s); velocities scaled by max(0, 1 - dt*damp(s)) with
+// the kinetic energy removed from E'.
+template <class R>
+void sources(const oracle_problem *pb, Pencil<R> &P, R dt) {
+    if (!pb->heat && !pb->damp) return;
+    for (int i = 0; i < P.n; ++i) {
+        const int k = Pencil<R>::at(i);
+        R xyz[3];
+        cell_position(pb, P.axis, i, P.ja, P.jb, xyz);
+        const R s = source_coord(pb, xyz);
+        if (pb->heat) P.edn[k] = P.edn[k] + dt * lerp_tab(pb, pb->heat, s);
+        if (pb->damp) {
+            const R kd = lerp_tab(pb, pb->damp, s);
+            const R f = Max(R(0.0), R(1.0) - dt * kd);
+            const R rho = P.rho0c[k] + P.rdn[k];
+            const R ke = R(0.5) * (P.mnn[k] * P.mnn[k] + (P.mt1n[k] * P.mt1n[k] + P.mt2n[k] * P.mt2n[k])) / rho;
+            P.mnn[k] = P.mnn[k] * f;
+            P.mt1n[k] = P.mt1n[k] * f;
+            P.mt2n[k] = P.mt2n[k] * f;
+            P.edn[k] = P.edn[k] - (R(1.0) - f * f) * ke;
+        }
+    }
+}
+
+// Whole pass on one gathered pencil.
+template <class R>
+void pass(const oracle_problem *pb, Pencil<R> &P, R dt, int with_sources) {
+    primitives(pb, P);
+    interface_values(P);
+    smoothness(P);
+    flattening(P);
+    parabolas(P);
+    trace(pb, P, dt);
+    riemann_fluxes(pb, P);
+    hydro_update(pb, P, dt);
+    ppb_profiles(P);
+    ppb_fluxes(pb, P, dt);
+    ppb_fct(P);
+    ppb_update(pb, P, dt);
+    if (with_sources) sources(pb, P, dt);
+}
+
+// Step a1 inverse: back to full variables in the unrotated frame.
+template <class R>
+void scatter(const oracle_problem *pb, const Pencil<R> &P, double *q[9]) {
+    const int a = P.axis, t1 = (a + 1) % 3, t2 = (a + 2) % 3;
+    const R gm1 = R(pb->gamma - 1.0);
+    for (int i = 0; i < P.n; ++i) {
+        const int k = Pencil<R>::at(i);
+        size_t c = cell_index(pb, a, i, P.ja, P.jb);
+        q[0][c] = val(P.rho0c[k] + P.rdn[k]);
+        q[1 + a][c] = val(P.mnn[k]);
+        q[1 + t1][c] = val(P.mt1n[k]);
+        q[1 + t2][c] = val(P.mt2n[k]);
+        q[4][c] = val(P.p0c[k] / gm1 + P.edn[k]);
+        q[5][c] = val(P.fvn[k]);
+        q[6 + a][c] = val(P.onn[k]);
+        q[6 + t1][c] = val(P.ot1n[k]);
+        q[6 + t2][c] = val(P.ot2n[k]);
+    }
+}
+
+template <class R>
+void flush_counters(const Pencil<R> &P) {
+    g_cnt[0] += P.c_nonsmooth;
+    g_cnt[1] += P.c_flat;
+    g_cnt[2] += P.c_theta;
+    g_cnt[3] += P.c_fct;
+    g_cnt[4] += P.c_clamp;
+    g_cnt[5] += P.n;
+}
+
+template <class R>
+void sweep_all(const oracle_problem *pb, double *q[9], int axis, double dt, int with_sources,
+               bool parallel) {
+    const int n = extent(pb, axis);
+    const int na = extent(pb, (axis + 1) % 3), nb = extent(pb, (axis + 2) % 3);
+    const long long npen = (long long)na * nb;
+    auto body = [&](Pencil<R> &P, long long p) {
+        P.ja = (int)(p % na);
+        P.jb = (int)(p / na);
+        P.c_nonsmooth = P.c_flat = P.c_theta = P.c_fct = P.c_clamp = 0;
+        gather(pb, P, q);
+        pass(pb, P, R(dt), with_sources);
+        scatter(pb, P, q);
+        flush_counters(P);
+    };
+    if (parallel) {
+#pragma omp parallel num_threads(g_threads > 0 ? g_threads : omp_get_max_threads())
+        {
+            Pencil<R> P;
+            P.alloc(n);
+            P.axis = axis;
+#pragma omp for schedule(static)
+            for (long long p = 0; p < npen; ++p) body(P, p);
+        }
+    } else {
+        Pencil<R> P;
+        P.alloc(n);
+        P.axis = axis;
+        for (long long p = 0; p < npen; ++p) body(P, p);
+    }
+}
+
+bool has_sources(const oracle_problem *pb) { return pb->heat || pb->damp; }
+
+}  // namespace
+
+extern "C" {
+
+void oracle_sweep(const oracle_problem *pb, double *q[9], int axis, double dt, int with_sources) {
+    sweep_all<double>(pb, q, axis, dt, with_sources && has_sources(pb), true);
+}
+
+void oracle_double_step(const oracle_problem *pb, double *q[9], double dt) {
+    const int src = has_sources(pb) ? 1 : 0;
+    oracle_sweep(pb, q, 0, dt, 0);
+    oracle_sweep(pb, q, 1, dt, 0);
+    oracle_sweep(pb, q, 2, dt, src);
+    oracle_sweep(pb, q, 2, dt, 0);
+    oracle_sweep(pb, q, 1, dt, 0);
+    oracle_sweep(pb, q, 0, dt, src);
+}
+
+double oracle_cfl_dt(const oracle_problem *pb, double *const q[9], double cfl) {
+    const double gam = pb->gamma, gm1 = pb->gamma - 1.0;
+    double smax = 0.0;
+    const long long ncell = (long long)pb->nx * pb->ny * pb->nz;
+#pragma omp parallel for reduction(max : smax) num_threads(g_threads > 0 ? g_threads : omp_get_max_threads())
+    for (long long c = 0; c < ncell; ++c) {
+        int i = (int)(c % pb->nx), j = (int)((c / pb->nx) % pb->ny), k = (int)(c / ((long long)pb->nx * pb->ny));
+        double xyz[3];
+        cell_position<double>(pb, 0, i, j, k, xyz);
+        BasePoint<double> b = base_at<double>(pb, xyz);
+        double rho = q[0][c];
+        double u = q[1][c] / rho, v = q[2][c] / rho, w = q[3][c] / rho;
+        double ke = 0.5 * (q[1][c] * u + q[2][c] * v + q[3][c] * w);
+        double ed = q[4][c] - b.p0 / gm1;
+        double p = b.p0 + gm1 * (ed - ke);
+        double cs = std::sqrt(gam * p / rho);
+        double s = std::max(std::max(std::fabs(u), std::fabs(v)), std::fabs(w)) + cs;
+        smax = std::max(smax, s);
+    }
+    return cfl * pb->dx / smax;
+}
+
+void oracle_sweep_pencil(const oracle_problem *pb, int axis, int ja, int jb, double *const in[9],
+                         double *out[9], double dt, int with_sources) {
+    // Build a one-pencil grid view: copy the pencil into a full-size scratch
+    // only along the pencil by indexing through a private problem whose
+    // transverse extents are those of the grid (positions must stay exact).
+    const int n = extent(pb, axis);
+    Pencil<double> P;
+    P.alloc(n);
+    P.axis = axis;
+    P.ja = ja;
+    P.jb = jb;
+    // gather from the pencil arrays
+    const int bl = pb->bc[2 * axis], bh = pb->bc[2 * axis + 1];
+    P.wall_lo = (bl == 1);
+    P.wall_hi = (bh == 1);
+    const double gm1 = pb->gamma - 1.0;
+    const int t1 = (axis + 1) % 3, t2 = (axis + 2) % 3;
+    for (int i = -G; i < n + G; ++i) {
+        bool flip;
+        int m = map_cell(i, n, bl, bh, &flip);
+        double xyz[3];
+        cell_position<double>(pb, axis, m, ja, jb, xyz);
+        BasePoint<double> b = base_at<double>(pb, xyz);
+        const int k = Pencil<double>::at(i);
+        P.rho0c[k] = b.rho0;
+        P.p0c[k] = b.p0;
+        P.gn[k] = flip ? -b.g[axis] : b.g[axis];
+        P.rd[k] = in[0][m] - b.rho0;
+        P.mn[k] = flip ? -in[1 + axis][m] : in[1 + axis][m];
+        P.mt1[k] = in[1 + t1][m];
+        P.mt2[k] = in[1 + t2][m];
+        P.ed[k] = in[4][m] - b.p0 / gm1;
+        P.fv[k] = in[5][m];
+        P.on[k] = flip ? -in[6 + axis][m] : in[6 + axis][m];
+        P.ot1[k] = in[6 + t1][m];
+        P.ot2[k] = in[6 + t2][m];
+    }
+    const double lo = origin(pb, axis);
+    for (int j = -G; j < n + G; ++j) {
+        int Pf = map_face(j, n, bl, bh);
+        double xyz[3];
+        cell_position<double>(pb, axis, 0, ja, jb, xyz);
+        xyz[axis] = lo + (double)Pf * pb->dx;
+        BasePoint<double> b = base_at<double>(pb, xyz);
+        P.rho0f[Pencil<double>::at(j)] = b.rho0;
+        P.p0f[Pencil<double>::at(j)] = b.p0;
+    }
+    pass(pb, P, dt, with_sources && has_sources(pb));
+    for (int i = 0; i < n; ++i) {
+        const int k = Pencil<double>::at(i);
+        out[0][i] = P.rho0c[k] + P.rdn[k];
+        out[1 + axis][i] = P.mnn[k];
+        out[1 + t1][i] = P.mt1n[k];
+        out[1 + t2][i] = P.mt2n[k];
+        out[4][i] = P.p0c[k] / gm1 + P.edn[k];
+        out[5][i] = P.fvn[k];
+        out[6 + axis][i] = P.onn[k];
+        out[6 + t1][i] = P.ot1n[k];
+        out[6 + t2][i] = P.ot2n[k];
+    }
+    flush_counters(P);
+}
+
+void oracle_diagnostics(const oracle_problem *pb, double *const q[9], double totals[7], int nbins,
+                        double rmax, double *profiles, double *max_mach) {
+    const double gam = pb->gamma, gm1 = pb->gamma - 1.0;
+    const double dV = pb->dx * pb->dx * pb->dx;
+    const long long ncell = (long long)pb->nx * pb->ny * pb->nz;
+    double t[7] = {0, 0, 0, 0, 0, 0, 0};
+    std::vector<double> acc((size_t)(nbins > 0 ? nbins : 0) * 6, 0.0);
+    double mmax = 0.0;
+    for (long long c = 0; c < ncell; ++c) {
+        int i = (int)(c % pb->nx), j = (int)((c / pb->nx) % pb->ny), k = (int)(c / ((long long)pb->nx * pb->ny));
+        double xyz[3];
+        cell_position<double>(pb, 0, i, j, k, xyz);
+        BasePoint<double> b = base_at<double>(pb, xyz);
+        const double rho = q[0][c];
+        t[0] += rho;
+        t[1] += q[1][c];
+        t[2] += q[2][c];
+        t[3] += q[3][c];
+        t[4] += q[4][c];
+        t[5] += rho * q[5][c];
+        t[6] += q[5][c];
+        const double u = q[1][c] / rho, v = q[2][c] / rho, w = q[3][c] / rho;
+        const double ke = 0.5 * (q[1][c] * u + q[2][c] * v + q[3][c] * w);
+        const double p = b.p0 + gm1 * ((q[4][c] - b.p0 / gm1) - ke);
+        const double cs = std::sqrt(gam * p / rho);
+        const double speed = std::sqrt(u * u + v * v + w * w);
+        mmax = std::max(mmax, speed / cs);
+        if (nbins > 0) {
+            const double r = std::sqrt(xyz[0] * xyz[0] + xyz[1] * xyz[1] + xyz[2] * xyz[2]);
+            const int bin = (int)std::floor(r / rmax * nbins);
+            if (bin >= 0 && bin < nbins) {
+                const double ur = r > 0.0 ? (u * xyz[0] + v * xyz[1] + w * xyz[2]) / r : 0.0;
+                double *a = &acc[(size_t)bin * 6];
+                a[0] += 1.0;
+                a[1] += rho;
+                a[2] += p;
+                a[3] += q[5][c];
+                a[4] += speed;
+                a[5] += ur * ur;
+            }
+        }
+    }
+    for (int m = 0; m < 7; ++m) totals[m] = t[m] * dV;
+    for (int b = 0; b < nbins; ++b) {
+        const double *a = &acc[(size_t)b * 6];
+        for (int m = 0; m < 5; ++m) profiles[b * 5 + m] = a[0] > 0.0 ? a[1 + m] / a[0] : 0.0;
+    }
+    if (max_mach) *max_mach = mmax;
+}
+
+void oracle_counters(long long out[6]) {
+    for (int i = 0; i < 6; ++i) out[i] = g_cnt[i].load();
+}
+
+void oracle_reset_counters(void) {
+    for (int i = 0; i < 6; ++i) g_cnt[i] = 0;
+}
+
+void oracle_count_flops(const oracle_problem *pb, double *const q[9], int axis, double dt, double out[2]) {
+    const long long ncell = (long long)pb->nx * pb->ny * pb->nz;
+    std::vector<std::vector<double>> copy(9, std::vector<double>((size_t)ncell));
+    double *qc[9];
+    for (int v = 0; v < 9; ++v) {
+        std::memcpy(copy[v].data(), q[v], sizeof(double) * (size_t)ncell);
+        qc[v] = copy[v].data();
+    }
+    Counted::flops = 0;
+    Counted::selects = 0;
+    // count only the pass itself (gather/scatter excluded)
+    const int n = extent(pb, axis);
+    const int na = extent(pb, (axis + 1) % 3), nb = extent(pb, (axis + 2) % 3);
+    Pencil<Counted> P;
+    P.alloc(n);
+    P.axis = axis;
+    long long fl = 0, se = 0;
+    for (long long p = 0; p < (long long)na * nb; ++p) {
+        P.ja = (int)(p % na);
+        P.jb = (int)(p / na);
+        gather(pb, P, qc);
+        Counted::flops = 0;
+        Counted::selects = 0;
+        pass(pb, P, Counted(dt), 0);
+        fl += Counted::flops;
+        se += Counted::selects;
+    }
+    out[0] = (double)fl / (double)ncell;
+    out[1] = (double)se / (double)ncell;
+}
+
+void oracle_set_threads(int n) { g_threads = n; }
+
+int oracle_get_threads(void) {
+#ifdef _OPENMP
+    return g_threads > 0 ? g_threads : omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+}  // extern "C"

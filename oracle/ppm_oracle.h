@@ -1,0 +1,88 @@
+/*
+ * ppm_oracle.h -- plain FP64 CPU oracle for the PPM+PPB 1-D sweeps.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This is the slow, obviously-correct statement of
+ * what the directionally split PPM gas dynamics + PPB fractional-volume sweep
+ * computes (Woodward et al., Sec. 1 and Sec. 4).  Only the tests, the
+ * package's smoke check and the benchmark's CPU-baseline leg may load it; the
+ * CUDA library never includes, links or calls it, and the two share no code.
+ *
+ * Every function works on full (not base-subtracted) FP64 state arrays
+ * q[9] = (rho, rho*u, rho*v, rho*w, E, FV, m_x, m_y, m_z), each nx*ny*nz with
+ * x fastest.  Internally each 1-D pass gathers one pencil at a time, subtracts
+ * the hydrostatic base state (Sec. 1, "subtract it out ... very carefully"),
+ * runs the pass step by step on whole-pencil arrays, and scatters back.
+ *
+ * Parity status of each step (what pins it, besides the CUDA path agreeing):
+ *   interface values, parabolas, tracing, Riemann, fluxes, update: pinned by
+ *     exact Riemann solutions (Sod, Lax), exact preservation of uniform and
+ *     hydrostatic states, conservation, axis-permutation symmetry, and the
+ *     measured convergence order on smooth advection;
+ *   PPB advection: pinned by bounds, conservation, exact transport of linear
+ *     and quadratic profiles and of the first moment at constant velocity;
+ *   smoothness-detector constants, flattening constants, PPB curvature and
+ *     FCT limiter details: parity unpinned against the paper (it prints no
+ *     formulas for them); pinned only through the invariants above.
+ */
+#ifndef PPM_ORACLE_H
+#define PPM_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    int nx, ny, nz;
+    double x0, y0, z0;      /* low corner of the grid */
+    double dx;              /* uniform cubic cells (Sec. 1: uniform Cartesian grid) */
+    double gamma;           /* gamma-law gas */
+    int bc[6];              /* -x,+x,-y,+y,-z,+z : 0 periodic, 1 reflecting */
+    int grav;               /* 0 none (uniform base), 1 plane-parallel in z, 2 central */
+    int ntab;               /* profile tables on s_i = s0 + i*ds, i < ntab (ntab >= 2) */
+    double s0, ds;
+    const double *rho0, *p0, *g;   /* base density, pressure, signed acceleration along +s */
+    const double *heat, *damp;     /* optional (NULL): heating rate, damping rate */
+} oracle_problem;
+
+/* One 1-D pass along axis (0=x,1=y,2=z) over the whole grid, in place.
+ * sources != 0 applies heating/damping to every cell after the pass. */
+void oracle_sweep(const oracle_problem *pb, double *q[9], int axis, double dt, int sources);
+
+/* One Strang double step: X Y Z [sources] Z Y X [sources], same dt. */
+void oracle_double_step(const oracle_problem *pb, double *q[9], double dt);
+
+/* dt = cfl * dx / max over cells of (max_d |u_d| + c). */
+double oracle_cfl_dt(const oracle_problem *pb, double *const q[9], double cfl);
+
+/* One pass of a single pencil: in[v][i], out[v][i] for i < n (n = extent of
+ * the grid along axis); (ja, jb) are the pencil's transverse cell indices in
+ * cyclic order (axis+1, axis+2). */
+void oracle_sweep_pencil(const oracle_problem *pb, int axis, int ja, int jb,
+                         double *const in[9], double *out[9], double dt, int sources);
+
+/* Conserved totals (x dV) M, Px, Py, Pz, E, sum rho*FV, sum FV; spherical
+ * shell averages (nbins bins of width rmax/nbins; per bin rho, p, FV, |u|,
+ * u_r^2, volume-weighted; empty bins 0); max Mach number. */
+void oracle_diagnostics(const oracle_problem *pb, double *const q[9], double totals[7],
+                        int nbins, double rmax, double *profiles, double *max_mach);
+
+/* Event counters since the last reset: [0] cells with a non-smooth hydro
+ * variable, [1] cells flattened, [2] PPB profiles bound-limited, [3] faces
+ * FCT-limited (C<1), [4] moment-bound clamps, [5] cells visited. */
+void oracle_counters(long long out[6]);
+void oracle_reset_counters(void);
+
+/* Counted arithmetic: runs one pass along axis on a copy of q with every
+ * add/sub/mul/div/sqrt counted.  out[0] = flops per cell, out[1] = selects
+ * (min/max/abs/compare) per cell. */
+void oracle_count_flops(const oracle_problem *pb, double *const q[9], int axis, double dt,
+                        double out[2]);
+
+/* Threads used by the OpenMP loops (0 = library default). */
+void oracle_set_threads(int n);
+int oracle_get_threads(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
