@@ -1,0 +1,150 @@
+/*
+ * ppm.h -- C ABI of libppm.so: directionally split PPM gas dynamics with PPB
+ * fractional-volume advection on a uniform 3-D Cartesian grid, on one GPU.
+ *
+ * The method is the one summarised by Woodward, Lin, Mao, Andrassy & Herwig,
+ * "Simulating 3-D Stellar Hydrodynamics using PPM and PPB Multifluid Gas
+ * Dynamics on CPU and CPU+GPU Nodes": Sec. 1 (high-order interface values,
+ * constraints only where the 5-cell smoothness test fails, subtraction of the
+ * hydrostatic initial state, PPB advection of the fractional volume FV),
+ * Sec. 4 (1-D passes over grid pencils, stencil reaching 4 cells).
+ *
+ * Conventions shared by every call
+ *   - Return value: PPM_OK (0) or a negative ppm_status.  After an error the
+ *     context stays usable unless the status is PPM_ECUDA; ppm_last_error()
+ *     gives a one-line message.
+ *   - State: 9 arrays q[0..8] = (rho, rho*u, rho*v, rho*w, E, FV, m_x, m_y,
+ *     m_z), each nx*ny*nz doubles with x fastest (index (k*ny + j)*nx + i).
+ *     rho and E are full values (the base state is never subtracted in the
+ *     caller's arrays).  FV is the volume fraction of the tracked fluid and
+ *     m_d = 12 * integral over the cell of xi_d * FV (xi in [-1/2,1/2]).
+ *   - Memory: the library owns all device memory; caller arrays are read or
+ *     written only during the call and never retained.  Host pointers may
+ *     be pageable or pinned.
+ *   - Threads: one context per host thread at a time.  Work is queued on the
+ *     context's stream (given at creation, or created by the library).
+ */
+#ifndef PPM_H
+#define PPM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ppm_ctx ppm_ctx;
+
+typedef enum {
+    PPM_OK = 0,
+    PPM_EINVAL = -1,     /* bad argument (sizes, pointers, ranges) */
+    PPM_ENOMEM = -2,     /* device or host allocation failed */
+    PPM_ECUDA = -3,      /* CUDA runtime error: the context must be destroyed */
+    PPM_ENONPHYS = -4,   /* a pass produced rho<=0, p<=0 or a non-finite value */
+    PPM_ECFL = -5,       /* requested time step exceeds the CFL limit (cfl > 1) */
+    PPM_ETIMEOUT = -6,   /* a bounded device wait gave up */
+    PPM_ESTATE = -7      /* call out of order (e.g. step with device dt before any cfl_dt) */
+} ppm_status;
+
+typedef enum { PPM_BC_PERIODIC = 0, PPM_BC_REFLECT = 1 } ppm_bc;
+
+typedef enum {
+    PPM_GRAV_NONE = 0,     /* uniform base state (rho0[0], p0[0]), no gravity */
+    PPM_GRAV_PLANE_Z = 1,  /* base state and gravity g(z) along +z, tables in z */
+    PPM_GRAV_CENTRAL = 2   /* spherically symmetric base, g(r) radial, tables in r */
+} ppm_grav_kind;
+
+typedef enum {
+    PPM_FP64_PLAIN = 0,     /* FP64 storage of full rho, E and FP64 arithmetic */
+    PPM_FP32_DEVIATION = 1  /* FP32 storage of rho-rho0, E-p0/(gamma-1); FP32 arithmetic,
+                               FP64 base tables, conversions and reductions */
+} ppm_precision;
+
+typedef enum { PPM_MEM_HOST = 0, PPM_MEM_DEVICE = 1 } ppm_mem;
+
+/* Hydrostatic base state (Sec. 1: "save the initial, spherically symmetric
+ * state ... and subtract it out") on a uniform coordinate grid
+ * s_i = s0 + i*ds, i < ntab (ntab >= 2); s = z (PLANE_Z) or r (CENTRAL),
+ * linear interpolation, ends extrapolated from the last interval.
+ * g is the signed acceleration along +s.  Arrays are host FP64 and copied. */
+typedef struct {
+    int kind;              /* ppm_grav_kind */
+    int ntab;
+    double s0, ds;
+    const double *rho0, *p0, *g;
+} ppm_gravity;
+
+typedef struct {
+    double x0, y0, z0;     /* low corner of the grid */
+    double dx;             /* cell size (cubic cells) */
+    int precision;         /* ppm_precision */
+    const double *heat;    /* optional: heating rate per unit volume on the gravity grid (NULL) */
+    const double *damp;    /* optional: velocity damping rate on the gravity grid (NULL) */
+    void *stream;          /* cudaStream_t to queue work on, or NULL for a private stream */
+    int device;            /* CUDA device ordinal */
+} ppm_options;
+
+/* Create a context: nx, ny, nz >= 4; gamma > 1; bc[6] per face
+ * (-x,+x,-y,+y,-z,+z), periodic faces must come in pairs; grav, opt not NULL.
+ * Allocates the state (9 values per cell in the chosen precision) and copies
+ * the tables to the device.  EINVAL / ENOMEM / ECUDA. */
+int ppm_create(ppm_ctx **out, int nx, int ny, int nz, double gamma, const int bc[6],
+               const ppm_gravity *grav, const ppm_options *opt);
+
+/* Upload the whole state from host FP64 arrays (full variables, layout above).
+ * FP32 form: rho - rho0 and E - p0/(gamma-1) are formed in FP64 on the device
+ * before rounding.  Invalidates the device time step (call ppm_cfl_dt). */
+int ppm_set_state(ppm_ctx *ctx, const double *const q[9]);
+
+/* Download the whole state to host FP64 arrays (full variables). */
+int ppm_get_state(ppm_ctx *ctx, double *const q[9]);
+
+/* Same for the sub-box lo <= (i,j,k) < hi; arrays are (hi-lo) boxes with x
+ * fastest, on the host (mem = PPM_MEM_HOST) or on the context's device
+ * (PPM_MEM_DEVICE). */
+int ppm_set_region(ppm_ctx *ctx, const int lo[3], const int hi[3], const double *const q[9], int mem);
+int ppm_get_region(ppm_ctx *ctx, const int lo[3], const int hi[3], double *const q[9], int mem);
+
+/* CFL time step (spec dt rule): dt = cfl * dx / max over cells of
+ * (max_d |u_d| + c), c = sqrt(gamma p / rho), reduced in FP64 on the device.
+ * 0 < cfl <= 1 (else ECFL).  dt_out may be NULL: the value then stays on the
+ * device for ppm_step(ctx, 0).  Returns ENONPHYS if a previous pass flagged a
+ * non-physical cell. */
+int ppm_cfl_dt(ppm_ctx *ctx, double cfl, double *dt_out);
+
+/* One Strang double step (Sec. 1 / Sec. 4 directional splitting):
+ * passes X Y Z [sources] Z Y X [sources], all with the same dt, as one CUDA
+ * graph launch.  dt > 0 uses that value; dt <= 0 uses the device value from
+ * the last ppm_cfl_dt or, after a step, the CFL maximum fused into that
+ * step's last pass (ESTATE if there is none).  Never waits for the device. */
+int ppm_step(ppm_ctx *ctx, double dt);
+
+/* One 1-D pass along axis (0=x, 1=y, 2=z) with time step dt > 0;
+ * sources != 0 applies heating/damping after the pass. */
+int ppm_sweep(ppm_ctx *ctx, int axis, double dt, int sources);
+
+/* FP64 reductions of the current state:
+ * totals[7] = (M, Px, Py, Pz, E, sum rho*FV, sum FV), each times dx^3;
+ * profiles (may be NULL when nbins == 0): nbins x 5 volume averages of
+ * (rho, p, FV, |u|, u_r^2) over shells of width rmax/nbins about the
+ * coordinate origin (Sec. 1: averages on spherical surfaces), 0 <= nbins <= 1024;
+ * max_mach (may be NULL): max |u|/c.  Synchronises with the device. */
+int ppm_diagnostics(ppm_ctx *ctx, double totals[7], int nbins, double rmax, double *profiles,
+                    double *max_mach);
+
+/* Wait for all queued work; returns ENONPHYS if a pass flagged a
+ * non-physical cell since the last check (the flag is then cleared). */
+int ppm_sync(ppm_ctx *ctx);
+
+/* Number of kernel launches queued by this context so far (for accounting). */
+long long ppm_launch_count(const ppm_ctx *ctx);
+
+/* Last error message of this context (or of the last failed ppm_create when
+ * ctx is NULL). */
+const char *ppm_last_error(const ppm_ctx *ctx);
+
+/* Release all device memory, the graph and (if private) the stream. */
+void ppm_destroy(ppm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PPM_H */

@@ -1,0 +1,253 @@
+"""GB300-native PPM + PPB multifluid sweeps: Python binding of libppm.so.
+
+Argument marshalling only: every step of the method runs in the CUDA kernels
+of ``libppm.so`` (built from ``csrc/`` by :func:`build`).  The calls have the
+names of the C ABI in ``include/ppm.h``:
+
+    ctx = Context(shape, gamma, bc, grav_kind, tables, origin, dx, precision)
+    ctx.set_state(q)          # 9 float64 arrays, full variables, (nz, ny, nx)
+    dt = ctx.cfl_dt(0.7)
+    ctx.step(dt)              # one Strang double step X Y Z [src] Z Y X [src]
+    q = ctx.get_state()
+    totals, profiles, max_mach = ctx.diagnostics(nbins, rmax)
+
+PyTorch is only used, where a caller wants it, for device buffers and
+streams (``set_region(..., device tensors)``, ``stream=torch stream``).
+There is no CPU fallback: if the library is missing the import of a
+Context fails.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+from . import build as _build_mod
+
+__all__ = ["Context", "PpmError", "build", "library_path", "FP64_PLAIN", "FP32_DEVIATION",
+           "BC_PERIODIC", "BC_REFLECT", "GRAV_NONE", "GRAV_PLANE_Z", "GRAV_CENTRAL"]
+
+FP64_PLAIN = 0
+FP32_DEVIATION = 1
+BC_PERIODIC = 0
+BC_REFLECT = 1
+GRAV_NONE = 0
+GRAV_PLANE_Z = 1
+GRAV_CENTRAL = 2
+MEM_HOST = 0
+MEM_DEVICE = 1
+
+STATUS = {0: "PPM_OK", -1: "PPM_EINVAL", -2: "PPM_ENOMEM", -3: "PPM_ECUDA", -4: "PPM_ENONPHYS",
+          -5: "PPM_ECFL", -6: "PPM_ETIMEOUT", -7: "PPM_ESTATE"}
+
+_DP = C.POINTER(C.c_double)
+_lib = None
+
+
+class PpmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _Gravity(C.Structure):
+    _fields_ = [("kind", C.c_int), ("ntab", C.c_int), ("s0", C.c_double), ("ds", C.c_double),
+                ("rho0", _DP), ("p0", _DP), ("g", _DP)]
+
+
+class _Options(C.Structure):
+    _fields_ = [("x0", C.c_double), ("y0", C.c_double), ("z0", C.c_double), ("dx", C.c_double),
+                ("precision", C.c_int), ("heat", _DP), ("damp", _DP), ("stream", C.c_void_p),
+                ("device", C.c_int)]
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    return _build_mod.build(force=force, verbose=verbose)
+
+
+def library_path() -> str:
+    return _build_mod.LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build_mod.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"libppm.so is not built ({path}); run paper_1810_13416_gb300.build()")
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    Q = _DP * 9
+    I3 = C.c_int * 3
+    lib.ppm_create.argtypes = [C.POINTER(P), C.c_int, C.c_int, C.c_int, C.c_double, C.c_int * 6,
+                               C.POINTER(_Gravity), C.POINTER(_Options)]
+    lib.ppm_set_state.argtypes = [P, Q]
+    lib.ppm_get_state.argtypes = [P, Q]
+    lib.ppm_set_region.argtypes = [P, I3, I3, Q, C.c_int]
+    lib.ppm_get_region.argtypes = [P, I3, I3, Q, C.c_int]
+    lib.ppm_cfl_dt.argtypes = [P, C.c_double, _DP]
+    lib.ppm_step.argtypes = [P, C.c_double]
+    lib.ppm_sweep.argtypes = [P, C.c_int, C.c_double, C.c_int]
+    lib.ppm_diagnostics.argtypes = [P, _DP, C.c_int, C.c_double, _DP, _DP]
+    lib.ppm_sync.argtypes = [P]
+    lib.ppm_launch_count.argtypes = [P]
+    lib.ppm_launch_count.restype = C.c_longlong
+    lib.ppm_last_error.argtypes = [P]
+    lib.ppm_last_error.restype = C.c_char_p
+    lib.ppm_destroy.argtypes = [P]
+    lib.ppm_destroy.restype = None
+    _lib = lib
+    return lib
+
+
+def _f64(a) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a
+
+
+def _ptrs(arrs) -> "C.Array":
+    return (_DP * 9)(*[a.ctypes.data_as(_DP) for a in arrs])
+
+
+class Context:
+    """One grid on one GPU (a ``ppm_ctx``)."""
+
+    def __init__(self, shape, gamma: float, bc: Sequence[int], grav_kind: int, s0: float, ds: float,
+                 rho0, p0, g, origin=(0.0, 0.0, 0.0), dx: float = 1.0, precision: int = FP32_DEVIATION,
+                 heat=None, damp=None, stream=None, device: int = 0):
+        self.lib = _load()
+        self.shape = tuple(int(v) for v in shape)
+        self._keep = [_f64(rho0), _f64(p0), _f64(g)]
+        gr = _Gravity(int(grav_kind), int(self._keep[0].size), float(s0), float(ds),
+                      self._keep[0].ctypes.data_as(_DP), self._keep[1].ctypes.data_as(_DP),
+                      self._keep[2].ctypes.data_as(_DP))
+        hp = dp = None
+        if heat is not None:
+            self._keep.append(_f64(heat))
+            hp = self._keep[-1].ctypes.data_as(_DP)
+        if damp is not None:
+            self._keep.append(_f64(damp))
+            dp = self._keep[-1].ctypes.data_as(_DP)
+        sptr = None
+        if stream is not None:
+            sptr = int(getattr(stream, "cuda_stream", stream))
+        opt = _Options(float(origin[0]), float(origin[1]), float(origin[2]), float(dx), int(precision),
+                       hp, dp, sptr, int(device))
+        h = C.c_void_p()
+        rc = self.lib.ppm_create(C.byref(h), self.shape[0], self.shape[1], self.shape[2], float(gamma),
+                                 (C.c_int * 6)(*[int(b) for b in bc]), C.byref(gr), C.byref(opt))
+        if rc != 0:
+            raise PpmError(rc, self.lib.ppm_last_error(None).decode())
+        self.h = h
+        self.precision = precision
+        self.ncell = self.shape[0] * self.shape[1] * self.shape[2]
+
+    @classmethod
+    def from_problem(cls, p, precision: int = FP32_DEVIATION, stream=None, device: int = 0):
+        """Build from any object with the fields of a problem description
+        (shape, gamma, bc, grav, tables(s0, ds, rho0, p0, g, heat, damp),
+        origin, dx)."""
+        t = p.tables
+        return cls(p.shape, p.gamma, p.bc, p.grav, t.s0, t.ds, t.rho0, t.p0, t.g, origin=p.origin,
+                   dx=p.dx, precision=precision, heat=getattr(t, "heat", None),
+                   damp=getattr(t, "damp", None), stream=stream, device=device)
+
+    # ------------------------------------------------------------------
+    def _check(self, rc: int):
+        if rc != 0:
+            raise PpmError(rc, self.lib.ppm_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ppm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ------------------------------------------------------------------
+    def set_state(self, q: Sequence[np.ndarray]):
+        arrs = [_f64(a) for a in q]
+        assert len(arrs) == 9 and all(a.size == self.ncell for a in arrs)
+        self._check(self.lib.ppm_set_state(self.h, _ptrs(arrs)))
+
+    def get_state(self) -> List[np.ndarray]:
+        nx, ny, nz = self.shape
+        out = [np.empty((nz, ny, nx)) for _ in range(9)]
+        self._check(self.lib.ppm_get_state(self.h, _ptrs(out)))
+        return out
+
+    def get_state_into(self, out: Sequence[np.ndarray]):
+        self._check(self.lib.ppm_get_state(self.h, _ptrs(out)))
+
+    @staticmethod
+    def _sync_torch():
+        # device tensors may still be in production on torch's streams, which
+        # the library's stream does not wait for
+        import torch
+        torch.cuda.synchronize()
+
+    def set_region(self, lo, hi, q, device: bool = False):
+        """q: 9 host float64 arrays, or 9 CUDA float64 tensors when device=True."""
+        if device:
+            self._sync_torch()
+            ptrs = (_DP * 9)(*[C.cast(C.c_void_p(int(t.data_ptr())), _DP) for t in q])
+        else:
+            q = [_f64(a) for a in q]
+            ptrs = _ptrs(q)
+        self._check(self.lib.ppm_set_region(self.h, (C.c_int * 3)(*lo), (C.c_int * 3)(*hi), ptrs,
+                                            MEM_DEVICE if device else MEM_HOST))
+
+    def get_region(self, lo, hi, out=None, device: bool = False):
+        b = [hi[d] - lo[d] for d in range(3)]
+        if out is None:
+            out = [np.empty((b[2], b[1], b[0])) for _ in range(9)]
+        if device:
+            self._sync_torch()
+            ptrs = (_DP * 9)(*[C.cast(C.c_void_p(int(t.data_ptr())), _DP) for t in out])
+        else:
+            ptrs = _ptrs(out)
+        self._check(self.lib.ppm_get_region(self.h, (C.c_int * 3)(*lo), (C.c_int * 3)(*hi), ptrs,
+                                            MEM_DEVICE if device else MEM_HOST))
+        return out
+
+    def cfl_dt(self, cfl: float, fetch: bool = True) -> Optional[float]:
+        if fetch:
+            v = C.c_double()
+            self._check(self.lib.ppm_cfl_dt(self.h, float(cfl), C.byref(v)))
+            return v.value
+        self._check(self.lib.ppm_cfl_dt(self.h, float(cfl), None))
+        return None
+
+    def step(self, dt: float = 0.0):
+        self._check(self.lib.ppm_step(self.h, float(dt)))
+
+    def sweep(self, axis: int, dt: float, sources: bool = False):
+        self._check(self.lib.ppm_sweep(self.h, int(axis), float(dt), int(bool(sources))))
+
+    def diagnostics(self, nbins: int = 0, rmax: float = 1.0):
+        tot = np.zeros(7)
+        prof = np.zeros(max(nbins, 1) * 5)
+        mm = C.c_double()
+        self._check(self.lib.ppm_diagnostics(self.h, tot.ctypes.data_as(_DP), int(nbins), float(rmax),
+                                             prof.ctypes.data_as(_DP), C.byref(mm)))
+        return tot, prof[: nbins * 5].reshape(nbins, 5), mm.value
+
+    def sync(self):
+        self._check(self.lib.ppm_sync(self.h))
+
+    @property
+    def launch_count(self) -> int:
+        return int(self.lib.ppm_launch_count(self.h))

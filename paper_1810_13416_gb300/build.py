@@ -1,0 +1,77 @@
+"""Compile libppm.so for sm_103a with nvcc (no torch extension machinery).
+
+The three translation units (FP32 pass, FP64 pass, C ABI) compile in
+parallel, then link into ``libppm.so`` next to this file.
+"""
+from __future__ import annotations
+
+import os
+import subprocess
+import sys
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "csrc")
+INCLUDE = os.path.join(os.path.dirname(HERE), "include")
+LIB = os.path.join(HERE, "libppm.so")
+BUILD = os.path.join(HERE, "_build")
+UNITS = ["sweep_f32", "sweep_f64", "ppm_api"]
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE]
+_lock = threading.Lock()
+
+
+def _nvcc() -> str:
+    for c in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", "nvcc"):
+        if c and (os.path.isabs(c) and os.path.exists(c) or not os.path.isabs(c)):
+            return c
+    return "nvcc"
+
+
+def _sources():
+    srcs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh", ".h"))]
+    srcs.append(os.path.join(INCLUDE, "ppm.h"))
+    return srcs
+
+
+def stale() -> bool:
+    if not os.path.exists(LIB):
+        return True
+    t = os.path.getmtime(LIB)
+    return any(os.path.getmtime(s) > t for s in _sources())
+
+
+def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
+    """Build libppm.so if missing or older than its sources; returns its path."""
+    with _lock:
+        if not force and not stale():
+            return LIB
+        os.makedirs(BUILD, exist_ok=True)
+        nvcc = _nvcc()
+        extra = list(extra_flags or [])
+        procs = []
+        for u in UNITS:
+            obj = os.path.join(BUILD, u + ".o")
+            cmd = [nvcc, *ARCH, *FLAGS, *extra, "-Xptxas", "-v", "-c", os.path.join(CSRC, u + ".cu"), "-o", obj]
+            procs.append((u, cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+        logs = []
+        for u, cmd, p in procs:
+            out = p.communicate()[0].decode(errors="replace")
+            logs.append(out)
+            if p.returncode != 0:
+                raise RuntimeError(f"nvcc failed for {u}:\n{' '.join(cmd)}\n{out}")
+            if verbose:
+                print(out, file=sys.stderr)
+        tmp = LIB + f".tmp{os.getpid()}"
+        cmd = [nvcc, *ARCH, "-shared", "-o", tmp] + [os.path.join(BUILD, u + ".o") for u in UNITS]
+        r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{' '.join(cmd)}\n{r.stdout.decode(errors='replace')}")
+        os.replace(tmp, LIB)
+        with open(os.path.join(BUILD, "ptxas.log"), "w") as f:
+            f.write("\n".join(logs))
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv, verbose=True))

@@ -1,0 +1,718 @@
+// ppm_api.cu -- the C ABI of libppm.so (include/ppm.h): context, state
+// conversion, CFL and diagnostic reductions, and the CUDA-graph double step.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/ppm.h"
+#include "sweep.cuh"
+
+namespace ppm {
+void launch_sweep_f32(const SweepArgs<float> &a, dim3 grid, dim3 block, cudaStream_t st);
+void launch_sweep_f64(const SweepArgs<double> &a, dim3 grid, dim3 block, cudaStream_t st);
+}  // namespace ppm
+
+using namespace ppm;
+
+namespace {
+
+constexpr int NVAR = 9;
+constexpr int SWEEP_BLOCK = 128;
+constexpr int MAX_BINS = 1024;
+
+// Device scalars shared by the kernels of one context.
+struct DevScal {
+    double dt;                 // time step used by the passes
+    double dt_user;            // > 0: explicit dt for the next step
+    unsigned long long smax;   // bits of the running max of (max_d|u_d| + c)
+    double cfl;                // CFL number for the device dt
+    int flags;                 // FLAG_NONPHYS ...
+    int pad;
+};
+
+thread_local std::string g_create_error;
+
+}  // namespace
+
+struct ppm_ctx {
+    int n[3];
+    long long ncell;
+    double gamma;
+    int bc[6];
+    int grav;
+    int prec;
+    double org[3], dx;
+    int ntab;
+    double s0, ds;
+    double rho0c, p0c;         // uniform base (no gravity)
+    int has_heat, has_damp;
+    int device;
+    cudaStream_t stream;
+    bool own_stream;
+    void *state;               // 9 * ncell values (float or double)
+    double *t64;               // FP64 tables: rho0, p0, g, heat, damp (5 * ntab)
+    float *t32;                // FP32 copies
+    DevScal *ds_dev;
+    double *h_pinned;          // 8 doubles of pinned host scratch
+    double *stage;             // FP64 staging for host regions
+    long long stage_cells;
+    double *diag_acc;          // diagnostics accumulators
+    cudaGraph_t graph;
+    cudaGraphExec_t gexec;
+    cudaGraphNode_t dt_node;   // first node of the step graph (dt_kernel)
+    bool have_speed;           // a valid device max speed exists for dt <= 0
+    long long launches;
+    std::string err;
+};
+
+namespace {
+
+int fail(ppm_ctx *c, int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (c)
+        c->err = buf;
+    else
+        g_create_error = buf;
+    return code;
+}
+
+#define CK(ctx, call)                                                                          \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail((ctx), PPM_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_),      \
+                        __FILE__, __LINE__);                                                   \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Argument structs for the passes
+// ---------------------------------------------------------------------------
+template <typename R>
+SweepArgs<R> make_args(ppm_ctx *c, int axis) {
+    SweepArgs<R> a;
+    memset(&a, 0, sizeof(a));
+    const int nx = c->n[0], ny = c->n[1], nz = c->n[2];
+    a.q = static_cast<R *>(c->state);
+    a.vs = c->ncell;
+    a.axis = axis;
+    a.n = c->n[axis];
+    const long long sx = 1, sy = nx, sz = (long long)nx * ny;
+    if (axis == 0) {  // pencils along x: lanes over y, blocks over z
+        a.s_axis = sx; a.nlane = ny; a.s_lane = sy; a.lane_dim = 1; a.nblk = nz; a.s_blk = sz; a.blk_dim = 2;
+    } else if (axis == 1) {  // along y: lanes over x, blocks over z
+        a.s_axis = sy; a.nlane = nx; a.s_lane = sx; a.lane_dim = 0; a.nblk = nz; a.s_blk = sz; a.blk_dim = 2;
+    } else {  // along z: lanes over x, blocks over y
+        a.s_axis = sz; a.nlane = nx; a.s_lane = sx; a.lane_dim = 0; a.nblk = ny; a.s_blk = sy; a.blk_dim = 1;
+    }
+    a.bc_lo = c->bc[2 * axis];
+    a.bc_hi = c->bc[2 * axis + 1];
+    a.grav = c->grav;
+    for (int d = 0; d < 3; ++d) a.org[d] = c->org[d];
+    a.dx = c->dx;
+    const R *t = std::is_same<R, float>::value ? (const R *)c->t32 : (const R *)c->t64;
+    a.t_rho0 = t;
+    a.t_p0 = t + c->ntab;
+    a.t_g = t + 2 * c->ntab;
+    a.t_heat = c->has_heat ? t + 3 * c->ntab : nullptr;
+    a.t_damp = c->has_damp ? t + 4 * c->ntab : nullptr;
+    a.ntab = c->ntab;
+    a.rho0_c = (R)c->rho0c;
+    a.p0_c = (R)c->p0c;
+    a.s0 = c->s0;
+    a.ds = c->ds;
+    a.gamma = c->gamma;
+    a.dt = &c->ds_dev->dt;
+    a.smax = &c->ds_dev->smax;
+    a.flags = &c->ds_dev->flags;
+    return a;
+}
+
+int launch_sweep(ppm_ctx *c, int axis, int sources, int cfl) {
+    dim3 block(SWEEP_BLOCK);
+    if (c->prec == PPM_FP32_DEVIATION) {
+        SweepArgs<float> a = make_args<float>(c, axis);
+        a.sources = sources;
+        a.cfl = cfl;
+        dim3 grid((a.nlane + SWEEP_BLOCK - 1) / SWEEP_BLOCK, a.nblk);
+        launch_sweep_f32(a, grid, block, c->stream);
+    } else {
+        SweepArgs<double> a = make_args<double>(c, axis);
+        a.sources = sources;
+        a.cfl = cfl;
+        dim3 grid((a.nlane + SWEEP_BLOCK - 1) / SWEEP_BLOCK, a.nblk);
+        launch_sweep_f64(a, grid, block, c->stream);
+    }
+    c->launches++;
+    CK(c, cudaGetLastError());
+    return PPM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Small kernels
+// ---------------------------------------------------------------------------
+// dt for the next step: explicit value, or CFL * dx / (max speed of the state
+// left by the previous step); then clear the running maximum.
+__global__ void dt_kernel(DevScal *s, double dx, double dt_user) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const double smax = __longlong_as_double((long long)s->smax);
+        s->dt = (dt_user > 0.0) ? dt_user : s->cfl * dx / smax;
+        s->smax = 0ull;
+    }
+}
+
+// Write one device scalar from a kernel argument (no host buffer involved).
+__global__ void set_scalar_kernel(double *dst, double v) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *dst = v;
+}
+
+// Base state of a grid cell (FP64 tables, non-contracted as in the passes).
+template <typename R>
+__device__ __forceinline__ Base<R> cell_base(const SweepArgs<R> &A, int i, int j, int k) {
+    R xyz[3] = {coord(A, 0, i), coord(A, 1, j), coord(A, 2, k)};
+    return base_at(A, xyz);
+}
+
+// FP64 full variables (a (hi-lo) box, x fastest) -> internal state.
+template <typename R, bool PLAIN>
+__global__ void set_region_kernel(SweepArgs<double> A64, R *st, long long ncell, int nx, int ny,
+                                  int lo0, int lo1, int lo2, int bx, int by, int bz,
+                                  const double *const *src, long long src_off) {
+    const long long nb = (long long)bx * by * bz;
+    const double gm1 = A64.gamma - 1.0;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nb;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(t % bx), j = (int)((t / bx) % by), k = (int)(t / ((long long)bx * by));
+        const int gi = lo0 + i, gj = lo1 + j, gk = lo2 + k;
+        const long long cidx = ((long long)gk * ny + gj) * nx + gi;
+        double v[NVAR];
+        for (int q = 0; q < NVAR; ++q) v[q] = src[q][src_off + t];
+        if (!PLAIN) {
+            const Base<double> b = cell_base(A64, gi, gj, gk);
+            v[0] = xsub(v[0], b.rho0);
+            v[4] = xsub(v[4], xdiv(b.p0, gm1));
+            // FV in [0,1], stored folded; moments within the FP32 bound
+            const double fv = fmin(fmax(v[5], 0.0), 1.0);
+            const float s = (fv > 0.5) ? (float)(-fabs(fv - 1.0)) : (float)fv;
+            const float bnd = fv_moment_bound(s);
+            for (int q = 0; q < 5; ++q) st[q * ncell + cidx] = (R)v[q];
+            st[5 * ncell + cidx] = (R)s;
+            for (int q = 6; q < 9; ++q) st[q * ncell + cidx] = (R)fminf(fmaxf((float)v[q], -bnd), bnd);
+            continue;
+        }
+        for (int q = 0; q < NVAR; ++q) st[q * ncell + cidx] = (R)v[q];
+    }
+}
+
+template <typename R, bool PLAIN>
+__global__ void get_region_kernel(SweepArgs<double> A64, const R *st, long long ncell, int nx, int ny,
+                                  int lo0, int lo1, int lo2, int bx, int by, int bz,
+                                  double *const *dst, long long dst_off) {
+    const long long nb = (long long)bx * by * bz;
+    const double gm1 = A64.gamma - 1.0;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nb;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(t % bx), j = (int)((t / bx) % by), k = (int)(t / ((long long)bx * by));
+        const int gi = lo0 + i, gj = lo1 + j, gk = lo2 + k;
+        const long long cidx = ((long long)gk * ny + gj) * nx + gi;
+        double v[NVAR];
+        for (int q = 0; q < NVAR; ++q) v[q] = (double)st[q * ncell + cidx];
+        if (!PLAIN) {
+            const Base<double> b = cell_base(A64, gi, gj, gk);
+            v[0] = xadd(b.rho0, v[0]);
+            v[4] = xadd(xdiv(b.p0, gm1), v[4]);
+            v[5] = signbit(v[5]) ? 1.0 + v[5] : v[5];
+        }
+        for (int q = 0; q < NVAR; ++q) dst[q][dst_off + t] = v[q];
+    }
+}
+
+__device__ __forceinline__ void block_max_atomic(double v, unsigned long long *out) {
+    __shared__ double sm[32];
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sm[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = (l < (int)(blockDim.x >> 5)) ? sm[l] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (l == 0) atomicMax(out, (unsigned long long)__double_as_longlong(v));
+    }
+}
+
+// max over cells of (max_d |u_d| + c), in the precision of the state.
+template <typename R, bool PLAIN>
+__global__ void cfl_kernel(SweepArgs<R> A, const R *st, long long ncell, int nx, int ny,
+                           unsigned long long *out) {
+    const R gam = (R)A.gamma, gm1 = (R)(A.gamma - 1.0);
+    R smax = 0;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < ncell;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(t % nx), j = (int)((t / nx) % ny), k = (int)(t / ((long long)nx * ny));
+        const Base<R> b = cell_base(A, i, j, k);
+        const R rd = PLAIN ? xsub(st[t], b.rho0) : st[t];
+        const R ed = PLAIN ? xsub(st[4 * ncell + t], xdiv(b.p0, gm1)) : st[4 * ncell + t];
+        const R rho = b.rho0 + rd;
+        const R ri = (R)1 / rho;
+        const R mx = st[ncell + t], my = st[2 * ncell + t], mz = st[3 * ncell + t];
+        const R u = mx * ri, v = my * ri, w = mz * ri;
+        const R ke = (R)0.5 * (mx * u + (my * v + mz * w));
+        const R p = b.p0 + gm1 * (ed - ke);
+        const R s = rmax(rmax(rabs(u), rabs(v)), rabs(w)) + rsq(gam * p * ri);
+        smax = rmax(smax, s);
+    }
+    block_max_atomic((double)smax, out);
+}
+
+// FP64 diagnostics: totals and shell averages.  acc layout: [0..6] totals,
+// [8..8+6*nbins) per bin (count, rho, p, FV, |u|, u_r^2), [7] max Mach bits.
+template <typename R, bool PLAIN>
+__global__ void diag_kernel(SweepArgs<double> A64, const R *st, long long ncell, int nx, int ny,
+                            int nbins, double rmax_, double *acc) {
+    extern __shared__ double sbin[];
+    __shared__ double stot[7][32];
+    for (int b = threadIdx.x; b < 6 * nbins; b += blockDim.x) sbin[b] = 0.0;
+    __syncthreads();
+    const double gam = A64.gamma, gm1 = A64.gamma - 1.0;
+    double tot[7] = {0, 0, 0, 0, 0, 0, 0};
+    double mmax = 0.0;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < ncell;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(t % nx), j = (int)((t / nx) % ny), k = (int)(t / ((long long)nx * ny));
+        double xyz[3] = {coord(A64, 0, i), coord(A64, 1, j), coord(A64, 2, k)};
+        const Base<double> b = base_at(A64, xyz);
+        double rho, E;
+        if (PLAIN) {
+            rho = (double)st[t];
+            E = (double)st[4 * ncell + t];
+        } else {
+            rho = b.rho0 + (double)st[t];
+            E = b.p0 / gm1 + (double)st[4 * ncell + t];
+        }
+        const double mx = st[ncell + t], my = st[2 * ncell + t], mz = st[3 * ncell + t];
+        double fv = st[5 * ncell + t];
+        if (!PLAIN) fv = signbit(fv) ? 1.0 + fv : fv;
+        tot[0] += rho;
+        tot[1] += mx;
+        tot[2] += my;
+        tot[3] += mz;
+        tot[4] += E;
+        tot[5] += rho * fv;
+        tot[6] += fv;
+        const double u = mx / rho, v = my / rho, w = mz / rho;
+        const double ke = 0.5 * (mx * u + my * v + mz * w);
+        const double p = b.p0 + gm1 * ((E - b.p0 / gm1) - ke);
+        const double cs = sqrt(gam * p / rho);
+        const double spd = sqrt(u * u + v * v + w * w);
+        mmax = fmax(mmax, spd / cs);
+        if (nbins > 0) {
+            const double r = sqrt(xyz[0] * xyz[0] + xyz[1] * xyz[1] + xyz[2] * xyz[2]);
+            const int bin = (int)floor(r / rmax_ * nbins);
+            if (bin >= 0 && bin < nbins) {
+                const double ur = r > 0.0 ? (u * xyz[0] + v * xyz[1] + w * xyz[2]) / r : 0.0;
+                double *a = sbin + 6 * bin;
+                atomicAdd(a + 0, 1.0);
+                atomicAdd(a + 1, rho);
+                atomicAdd(a + 2, p);
+                atomicAdd(a + 3, fv);
+                atomicAdd(a + 4, spd);
+                atomicAdd(a + 5, ur * ur);
+            }
+        }
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    for (int m = 0; m < 7; ++m) {
+        double v = tot[m];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (l == 0) stot[m][w] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 7) {
+        double v = 0.0;
+        for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) v += stot[threadIdx.x][ww];
+        atomicAdd(acc + threadIdx.x, v);
+    }
+    for (int b = threadIdx.x; b < 6 * nbins; b += blockDim.x)
+        if (sbin[b] != 0.0) atomicAdd(acc + 8 + b, sbin[b]);
+    block_max_atomic(mmax, reinterpret_cast<unsigned long long *>(acc + 7));
+}
+
+int grid_for(long long n, int block) {
+    long long g = (n + block - 1) / block;
+    if (g > 152 * 16) g = 152 * 16;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+SweepArgs<double> args64(ppm_ctx *c) { return make_args<double>(c, 0); }
+
+int check_flags(ppm_ctx *c) {
+    int fl = 0;
+    CK(c, cudaMemcpyAsync(&fl, &c->ds_dev->flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (fl & FLAG_NONPHYS) {
+        CK(c, cudaMemsetAsync(&c->ds_dev->flags, 0, sizeof(int), c->stream));
+        return fail(c, PPM_ENONPHYS, "a pass produced rho<=0, p<=0 or a non-finite value");
+    }
+    return PPM_OK;
+}
+
+int region_io(ppm_ctx *c, const int lo[3], const int hi[3], double *const *arrs, int mem, bool to_dev) {
+    if (!c || !lo || !hi || !arrs) return fail(c, PPM_EINVAL, "null argument");
+    int b[3];
+    for (int d = 0; d < 3; ++d) {
+        if (lo[d] < 0 || hi[d] > c->n[d] || lo[d] >= hi[d])
+            return fail(c, PPM_EINVAL, "region [%d,%d) outside axis %d of extent %d", lo[d], hi[d], d, c->n[d]);
+        b[d] = hi[d] - lo[d];
+    }
+    for (int q = 0; q < NVAR; ++q)
+        if (!arrs[q]) return fail(c, PPM_EINVAL, "q[%d] is NULL", q);
+    if (mem != PPM_MEM_HOST && mem != PPM_MEM_DEVICE) return fail(c, PPM_EINVAL, "bad mem kind %d", mem);
+    const SweepArgs<double> A = args64(c);
+    const long long plane = (long long)b[0] * b[1];
+    // device pointer table (9 pointers) lives in the stage's header
+    double **ptab = reinterpret_cast<double **>(c->h_pinned + 8);
+    double **dptab = reinterpret_cast<double **>(c->diag_acc + 8 + 6 * MAX_BINS);
+    long long kchunk = (mem == PPM_MEM_DEVICE) ? b[2] : std::max(1LL, c->stage_cells / plane);
+    if (plane > c->stage_cells && mem == PPM_MEM_HOST) {
+        // one plane exceeds the stage: fall back to row chunks is not needed for
+        // grids up to stage size; reject explicitly
+        return fail(c, PPM_EINVAL, "region plane of %lld cells exceeds the staging buffer", plane);
+    }
+    for (long long k0 = 0; k0 < b[2]; k0 += kchunk) {
+        const long long nk = std::min(kchunk, (long long)b[2] - k0);
+        const long long cnt = plane * nk;
+        for (int q = 0; q < NVAR; ++q)
+            ptab[q] = (mem == PPM_MEM_DEVICE) ? arrs[q] + k0 * plane : c->stage + (long long)q * c->stage_cells;
+        CK(c, cudaMemcpyAsync(dptab, ptab, NVAR * sizeof(double *), cudaMemcpyHostToDevice, c->stream));
+        if (to_dev && mem == PPM_MEM_HOST)
+            for (int q = 0; q < NVAR; ++q)
+                CK(c, cudaMemcpyAsync(c->stage + (long long)q * c->stage_cells, arrs[q] + k0 * plane,
+                                      cnt * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        const int g = grid_for(cnt, 256);
+        const int lz = lo[2] + (int)k0;
+        if (to_dev) {
+            if (c->prec == PPM_FP32_DEVIATION)
+                set_region_kernel<float, false><<<g, 256, 0, c->stream>>>(A, (float *)c->state, c->ncell, c->n[0], c->n[1], lo[0], lo[1], lz, b[0], b[1], (int)nk, dptab, 0);
+            else
+                set_region_kernel<double, true><<<g, 256, 0, c->stream>>>(A, (double *)c->state, c->ncell, c->n[0], c->n[1], lo[0], lo[1], lz, b[0], b[1], (int)nk, dptab, 0);
+        } else {
+            if (c->prec == PPM_FP32_DEVIATION)
+                get_region_kernel<float, false><<<g, 256, 0, c->stream>>>(A, (const float *)c->state, c->ncell, c->n[0], c->n[1], lo[0], lo[1], lz, b[0], b[1], (int)nk, dptab, 0);
+            else
+                get_region_kernel<double, true><<<g, 256, 0, c->stream>>>(A, (const double *)c->state, c->ncell, c->n[0], c->n[1], lo[0], lo[1], lz, b[0], b[1], (int)nk, dptab, 0);
+        }
+        c->launches++;
+        CK(c, cudaGetLastError());
+        if (!to_dev && mem == PPM_MEM_HOST)
+            for (int q = 0; q < NVAR; ++q)
+                CK(c, cudaMemcpyAsync(arrs[q] + k0 * plane, c->stage + (long long)q * c->stage_cells,
+                                      cnt * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        // the pinned pointer table is reused by the next chunk
+        CK(c, cudaStreamSynchronize(c->stream));
+    }
+    if (to_dev) c->have_speed = false;
+    return PPM_OK;
+}
+
+void release(ppm_ctx *c) {
+    if (!c) return;
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    if (c->state) cudaFree(c->state);
+    if (c->t64) cudaFree(c->t64);
+    if (c->t32) cudaFree(c->t32);
+    if (c->ds_dev) cudaFree(c->ds_dev);
+    if (c->stage) cudaFree(c->stage);
+    if (c->diag_acc) cudaFree(c->diag_acc);
+    if (c->h_pinned) cudaFreeHost(c->h_pinned);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+int ppm_create(ppm_ctx **out, int nx, int ny, int nz, double gamma, const int bc[6],
+               const ppm_gravity *grav, const ppm_options *opt) {
+    if (!out || !bc || !grav || !opt) return fail(nullptr, PPM_EINVAL, "null argument");
+    *out = nullptr;
+    if (nx < 4 || ny < 4 || nz < 4) return fail(nullptr, PPM_EINVAL, "every extent must be >= 4 (got %d %d %d)", nx, ny, nz);
+    if (!(gamma > 1.0)) return fail(nullptr, PPM_EINVAL, "gamma must exceed 1");
+    for (int d = 0; d < 3; ++d) {
+        for (int s = 0; s < 2; ++s)
+            if (bc[2 * d + s] != PPM_BC_PERIODIC && bc[2 * d + s] != PPM_BC_REFLECT)
+                return fail(nullptr, PPM_EINVAL, "bad boundary kind on face %d", 2 * d + s);
+        if ((bc[2 * d] == PPM_BC_PERIODIC) != (bc[2 * d + 1] == PPM_BC_PERIODIC))
+            return fail(nullptr, PPM_EINVAL, "periodic faces must come in pairs (axis %d)", d);
+    }
+    if (grav->kind < 0 || grav->kind > 2) return fail(nullptr, PPM_EINVAL, "bad gravity kind");
+    if (grav->ntab < 2 || !grav->rho0 || !grav->p0 || !grav->g || !(grav->ds > 0.0))
+        return fail(nullptr, PPM_EINVAL, "base-state tables need ntab >= 2, ds > 0 and rho0, p0, g");
+    if (opt->precision != PPM_FP64_PLAIN && opt->precision != PPM_FP32_DEVIATION)
+        return fail(nullptr, PPM_EINVAL, "bad precision");
+    if (!(opt->dx > 0.0)) return fail(nullptr, PPM_EINVAL, "dx must be positive");
+    if (grav->kind == PPM_GRAV_NONE && (opt->heat || opt->damp))
+        return fail(nullptr, PPM_EINVAL, "heating/damping tables need a gravity coordinate (plane or central)");
+
+    ppm_ctx *c = new ppm_ctx();
+    c->n[0] = nx; c->n[1] = ny; c->n[2] = nz;
+    c->ncell = (long long)nx * ny * nz;
+    c->gamma = gamma;
+    for (int i = 0; i < 6; ++i) c->bc[i] = bc[i];
+    c->grav = grav->kind;
+    c->prec = opt->precision;
+    c->org[0] = opt->x0; c->org[1] = opt->y0; c->org[2] = opt->z0;
+    c->dx = opt->dx;
+    c->ntab = grav->ntab;
+    c->rho0c = grav->rho0[0];
+    c->p0c = grav->p0[0];
+    c->s0 = grav->s0;
+    c->ds = grav->ds;
+    c->has_heat = opt->heat != nullptr;
+    c->has_damp = opt->damp != nullptr;
+    c->device = opt->device;
+
+    auto bail = [&](int code) {
+        std::string m = c->err;
+        release(c);
+        delete c;
+        g_create_error = m;
+        return code;
+    };
+    cudaError_t e = cudaSetDevice(opt->device);
+    if (e != cudaSuccess) {
+        fail(c, PPM_ECUDA, "cudaSetDevice(%d): %s", opt->device, cudaGetErrorString(e));
+        return bail(PPM_ECUDA);
+    }
+    if (opt->stream) {
+        c->stream = (cudaStream_t)opt->stream;
+        c->own_stream = false;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            fail(c, PPM_ECUDA, "cudaStreamCreate failed");
+            return bail(PPM_ECUDA);
+        }
+        c->own_stream = true;
+    }
+    const size_t es = (c->prec == PPM_FP32_DEVIATION) ? sizeof(float) : sizeof(double);
+    const size_t sbytes = (size_t)NVAR * (size_t)c->ncell * es;
+    if (cudaMalloc(&c->state, sbytes) != cudaSuccess) {
+        cudaGetLastError();
+        fail(c, PPM_ENOMEM, "cannot allocate %zu bytes of state", sbytes);
+        return bail(PPM_ENOMEM);
+    }
+    const int nt = grav->ntab;
+    std::vector<double> h64((size_t)5 * nt, 0.0);
+    std::vector<float> h32((size_t)5 * nt, 0.0f);
+    for (int i = 0; i < nt; ++i) {
+        h64[i] = grav->rho0[i];
+        h64[nt + i] = grav->p0[i];
+        h64[2 * nt + i] = grav->g[i];
+        h64[3 * nt + i] = opt->heat ? opt->heat[i] : 0.0;
+        h64[4 * nt + i] = opt->damp ? opt->damp[i] : 0.0;
+    }
+    for (size_t i = 0; i < h64.size(); ++i) h32[i] = (float)h64[i];
+    // stage: up to 2^24 cells per variable (9 x 128 MiB), or the whole grid if smaller
+    c->stage_cells = std::min<long long>(c->ncell, 1LL << 24);
+    if (cudaMalloc(&c->t64, h64.size() * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->t32, h32.size() * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&c->ds_dev, sizeof(DevScal)) != cudaSuccess ||
+        cudaMalloc(&c->stage, (size_t)NVAR * c->stage_cells * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->diag_acc, (8 + 6 * MAX_BINS + 16) * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&c->h_pinned, 64 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        fail(c, PPM_ENOMEM, "cannot allocate tables / staging");
+        return bail(PPM_ENOMEM);
+    }
+    if (cudaMemcpy(c->t64, h64.data(), h64.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->t32, h32.data(), h32.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(c->ds_dev, 0, sizeof(DevScal)) != cudaSuccess ||
+        cudaMemset(c->state, 0, sbytes) != cudaSuccess) {
+        fail(c, PPM_ECUDA, "initialising device buffers failed");
+        return bail(PPM_ECUDA);
+    }
+    *out = c;
+    return PPM_OK;
+}
+
+int ppm_set_region(ppm_ctx *c, const int lo[3], const int hi[3], const double *const q[9], int mem) {
+    return region_io(c, lo, hi, const_cast<double *const *>(q), mem, true);
+}
+
+int ppm_get_region(ppm_ctx *c, const int lo[3], const int hi[3], double *const q[9], int mem) {
+    if (!c) return PPM_EINVAL;
+    int r = region_io(c, lo, hi, q, mem, false);
+    if (r != PPM_OK) return r;
+    return check_flags(c);
+}
+
+int ppm_set_state(ppm_ctx *c, const double *const q[9]) {
+    if (!c) return PPM_EINVAL;
+    const int lo[3] = {0, 0, 0};
+    return ppm_set_region(c, lo, c->n, q, PPM_MEM_HOST);
+}
+
+int ppm_get_state(ppm_ctx *c, double *const q[9]) {
+    if (!c) return PPM_EINVAL;
+    const int lo[3] = {0, 0, 0};
+    return ppm_get_region(c, lo, c->n, q, PPM_MEM_HOST);
+}
+
+int ppm_cfl_dt(ppm_ctx *c, double cfl, double *dt_out) {
+    if (!c) return PPM_EINVAL;
+    if (!(cfl > 0.0)) return fail(c, PPM_EINVAL, "cfl must be positive");
+    if (cfl > 1.0) return fail(c, PPM_ECFL, "cfl %.3g exceeds 1", cfl);
+    CK(c, cudaMemsetAsync(&c->ds_dev->smax, 0, sizeof(unsigned long long), c->stream));
+    set_scalar_kernel<<<1, 32, 0, c->stream>>>(&c->ds_dev->cfl, cfl);
+    c->launches++;
+    const int g = grid_for(c->ncell, 256);
+    if (c->prec == PPM_FP32_DEVIATION)
+        cfl_kernel<float, false><<<g, 256, 0, c->stream>>>(make_args<float>(c, 0), (const float *)c->state, c->ncell, c->n[0], c->n[1], &c->ds_dev->smax);
+    else
+        cfl_kernel<double, true><<<g, 256, 0, c->stream>>>(make_args<double>(c, 0), (const double *)c->state, c->ncell, c->n[0], c->n[1], &c->ds_dev->smax);
+    c->launches++;
+    CK(c, cudaGetLastError());
+    c->have_speed = true;
+    if (dt_out) {
+        int r = check_flags(c);
+        if (r != PPM_OK) return r;
+        unsigned long long bits = 0;
+        CK(c, cudaMemcpyAsync(&bits, &c->ds_dev->smax, sizeof(bits), cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+        double smax;
+        memcpy(&smax, &bits, sizeof(double));
+        if (!(smax > 0.0) || !std::isfinite(smax)) return fail(c, PPM_ENONPHYS, "max signal speed %g", smax);
+        *dt_out = cfl * c->dx / smax;
+    }
+    return PPM_OK;
+}
+
+static int capture_step(ppm_ctx *c) {
+    CK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    dt_kernel<<<1, 32, 0, c->stream>>>(c->ds_dev, c->dx, -1.0);
+    const int order[6] = {0, 1, 2, 2, 1, 0};
+    int rc = PPM_OK;
+    for (int s = 0; s < 6 && rc == PPM_OK; ++s) {
+        const int src = (s == 2 || s == 5) ? ((c->has_heat || c->has_damp) ? 1 : 0) : 0;
+        rc = launch_sweep(c, order[s], src, s == 5 ? 1 : 0);
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    c->launches -= 6;  // captured, not yet launched
+    if (rc != PPM_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(c, PPM_ECUDA, "stream capture: %s", cudaGetErrorString(e));
+    c->graph = g;
+    // the dt kernel is the only node without dependencies
+    size_t nn = 0;
+    CK(c, cudaGraphGetRootNodes(c->graph, nullptr, &nn));
+    if (nn != 1) return fail(c, PPM_ECUDA, "unexpected step graph shape (%zu roots)", nn);
+    CK(c, cudaGraphGetRootNodes(c->graph, &c->dt_node, &nn));
+    CK(c, cudaGraphInstantiate(&c->gexec, c->graph, 0));
+    return PPM_OK;
+}
+
+int ppm_step(ppm_ctx *c, double dt) {
+    if (!c) return PPM_EINVAL;
+    if (!(dt > 0.0) && !c->have_speed)
+        return fail(c, PPM_ESTATE, "ppm_step with dt <= 0 needs a device dt (call ppm_cfl_dt first)");
+    if (!std::isfinite(dt)) return fail(c, PPM_EINVAL, "dt is not finite");
+    if (!c->gexec) {
+        int r = capture_step(c);
+        if (r != PPM_OK) return r;
+    }
+    // the explicit dt travels as an argument of the graph's first kernel;
+    // updating it does not touch launches already in flight
+    {
+        DevScal *dsp = c->ds_dev;
+        double dxv = c->dx;
+        double dtu = dt > 0.0 ? dt : -1.0;
+        void *args[3] = {&dsp, &dxv, &dtu};
+        cudaKernelNodeParams kp;
+        memset(&kp, 0, sizeof(kp));
+        kp.func = (void *)dt_kernel;
+        kp.gridDim = dim3(1);
+        kp.blockDim = dim3(32);
+        kp.sharedMemBytes = 0;
+        kp.kernelParams = args;
+        CK(c, cudaGraphExecKernelNodeSetParams(c->gexec, c->dt_node, &kp));
+    }
+    CK(c, cudaGraphLaunch(c->gexec, c->stream));
+    c->launches += 7;
+    c->have_speed = true;
+    return PPM_OK;
+}
+
+int ppm_sweep(ppm_ctx *c, int axis, double dt, int sources) {
+    if (!c) return PPM_EINVAL;
+    if (axis < 0 || axis > 2) return fail(c, PPM_EINVAL, "axis must be 0, 1 or 2");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, PPM_EINVAL, "dt must be positive");
+    set_scalar_kernel<<<1, 32, 0, c->stream>>>(&c->ds_dev->dt, dt);
+    c->launches++;
+    CK(c, cudaGetLastError());
+    int r = launch_sweep(c, axis, sources && (c->has_heat || c->has_damp), 0);
+    c->have_speed = false;
+    return r;
+}
+
+int ppm_diagnostics(ppm_ctx *c, double totals[7], int nbins, double rmax, double *profiles, double *max_mach) {
+    if (!c || !totals) return fail(c, PPM_EINVAL, "null argument");
+    if (nbins < 0 || nbins > MAX_BINS) return fail(c, PPM_EINVAL, "nbins must be in [0, %d]", MAX_BINS);
+    if (nbins > 0 && (!profiles || !(rmax > 0.0))) return fail(c, PPM_EINVAL, "profiles need rmax > 0 and an output array");
+    const size_t nacc = 8 + 6 * (size_t)nbins;
+    CK(c, cudaMemsetAsync(c->diag_acc, 0, nacc * sizeof(double), c->stream));
+    const int g = grid_for(c->ncell, 256);
+    const size_t shm = 6 * (size_t)nbins * sizeof(double);
+    const SweepArgs<double> A = args64(c);
+    if (c->prec == PPM_FP32_DEVIATION) {
+        if (shm > 48 * 1024) CK(c, cudaFuncSetAttribute(diag_kernel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+        diag_kernel<float, false><<<g, 256, shm, c->stream>>>(A, (const float *)c->state, c->ncell, c->n[0], c->n[1], nbins, rmax, c->diag_acc);
+    } else {
+        if (shm > 48 * 1024) CK(c, cudaFuncSetAttribute(diag_kernel<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+        diag_kernel<double, true><<<g, 256, shm, c->stream>>>(A, (const double *)c->state, c->ncell, c->n[0], c->n[1], nbins, rmax, c->diag_acc);
+    }
+    c->launches++;
+    CK(c, cudaGetLastError());
+    std::vector<double> h(nacc);
+    CK(c, cudaMemcpyAsync(h.data(), c->diag_acc, nacc * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    const double dV = c->dx * c->dx * c->dx;
+    for (int m = 0; m < 7; ++m) totals[m] = h[m] * dV;
+    for (int b = 0; b < nbins; ++b) {
+        const double *a = &h[8 + 6 * b];
+        for (int m = 0; m < 5; ++m) profiles[5 * b + m] = a[0] > 0.0 ? a[1 + m] / a[0] : 0.0;
+    }
+    if (max_mach) *max_mach = h[7];
+    return check_flags(c);
+}
+
+int ppm_sync(ppm_ctx *c) {
+    if (!c) return PPM_EINVAL;
+    CK(c, cudaStreamSynchronize(c->stream));
+    return check_flags(c);
+}
+
+long long ppm_launch_count(const ppm_ctx *c) { return c ? c->launches : 0; }
+
+const char *ppm_last_error(const ppm_ctx *c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+void ppm_destroy(ppm_ctx *c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    release(c);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,786 @@
+// sweep.cuh -- the fused 1-D PPM + PPB pass (one kernel per axis and precision).
+//
+// One thread owns one grid pencil and marches along it cell by cell, keeping a
+// five-cell window of the state in registers, the way the paper keeps three
+// 32-word vectors per quantity on chip and barrel-shifts them (Sec. 4, Fig. 7):
+// every quantity of the pass is computed exactly once per cell, with no halo
+// recomputation.  Neighbouring threads own neighbouring pencils, so for the y
+// and z passes every load and store of a warp is one contiguous 128-byte
+// segment along x.
+//
+// At step c (the newest cell loaded is c) the pipeline does, with fixed lags:
+//   load + primitives            cell c                       (step a1)
+//   interface value              face (c-2)+1/2               (a2)
+//   detector, flattening,        cell c-2                     (a3, a4)
+//   parabola, characteristic
+//   tracing of both edges                                     (a5)
+//   Riemann solve and fluxes     face (c-3)+1/2               (a6, a7)
+//   hydro update                 cell c-3                     (a8)
+//   PPB profile                  cell c-2                     (a9)
+//   PPB transfers                face (c-3)+1/2
+//   FCT factors                  cell c-3; limit face (c-4)+1/2
+//   FV / moment update, sources, cell c-4 -> stored in place
+//   CFL maximum
+// so the cell written (c-4) is never read again by this pencil; the four
+// cells needed as high-side ghosts are kept in a per-thread stash before they
+// are overwritten.
+//
+// The formulas are the ones of the method description (perturbation form
+// about the hydrostatic base state, Sec. 1; fourth-order interface values,
+// Sec. 1; five-cell smoothness test, Sec. 1; Colella-Woodward parabolas,
+// flattening and tracing; acoustic + two-shock Riemann solver in difference
+// form; PPB advection of FV with three first moments and FCT to [0,1],
+// Sec. 1 and Sec. 4).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+namespace ppm {
+
+constexpr int G = 4;  // ghost width (Sec. 4: the difference stencil reaches 4 cells)
+
+// status flags (device int, OR-ed)
+constexpr int FLAG_NONPHYS = 1;
+
+template <typename R>
+struct SweepArgs {
+    R *q;                 // state: 9 arrays of ncell values, var stride vs
+    long long vs;
+    int n;                // cells along the pass
+    int nlane, nblk;      // pencils: lane index (fast) x block index
+    long long s_axis, s_lane, s_blk;  // element strides
+    int lane_dim, blk_dim;            // physical axis of lane / block index
+    int axis;
+    int bc_lo, bc_hi;     // 0 periodic, 1 reflect (along the pass)
+    int grav;             // 0 none, 1 plane z, 2 central
+    double org[3];
+    double dx;
+    // tables in precision R (FP64 plain: the FP64 tables themselves)
+    const R *t_rho0, *t_p0, *t_g, *t_heat, *t_damp;
+    int ntab;
+    double s0, ds;
+    R rho0_c, p0_c;       // uniform base (grav == 0)
+    double gamma;
+    const double *dt;     // device time step
+    int sources;          // apply heating/damping after the pass
+    int cfl;              // accumulate max(|u_d|)+c into *smax
+    unsigned long long *smax;
+    int *flags;
+};
+
+// ---------------------------------------------------------------------------
+// Exact (non-contracted) arithmetic for the base-state lookups, so that the
+// FP64 form reproduces the base state of the reference arithmetic bit for bit
+// and a state at rest stays at rest exactly.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double xadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double xsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double xmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double xdiv(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ double xsqrt(double a) { return __dsqrt_rn(a); }
+__device__ __forceinline__ float xadd(float a, float b) { return a + b; }
+__device__ __forceinline__ float xsub(float a, float b) { return a - b; }
+__device__ __forceinline__ float xmul(float a, float b) { return a * b; }
+__device__ __forceinline__ float xdiv(float a, float b) { return a / b; }
+__device__ __forceinline__ float xsqrt(float a) { return sqrtf(a); }
+
+__device__ __forceinline__ double rsq(double a) { return sqrt(a); }
+__device__ __forceinline__ float rsq(float a) { return sqrtf(a); }
+__device__ __forceinline__ double rabs(double a) { return fabs(a); }
+__device__ __forceinline__ float rabs(float a) { return fabsf(a); }
+__device__ __forceinline__ double rmax(double a, double b) { return a > b ? a : b; }
+__device__ __forceinline__ float rmax(float a, float b) { return a > b ? a : b; }
+__device__ __forceinline__ double rmin(double a, double b) { return a < b ? a : b; }
+__device__ __forceinline__ float rmin(float a, float b) { return a < b ? a : b; }
+template <typename R>
+__device__ __forceinline__ R rclamp(R x, R lo, R hi) { return rmin(rmax(x, lo), hi); }
+
+template <typename R>
+__device__ __forceinline__ R lerp_tab(const SweepArgs<R> &A, const R *__restrict__ tab, R s) {
+    const R u = xdiv(xsub(s, (R)A.s0), (R)A.ds);
+    R fl = floor(u);
+    int i = (int)rmin(rmax(fl, (R)0), (R)(A.ntab - 2));
+    const R w = xsub(u, (R)i);
+    const R t0 = __ldg(tab + i), t1 = __ldg(tab + i + 1);
+    return xadd(t0, xmul(w, xsub(t1, t0)));
+}
+
+template <typename R>
+struct Base {
+    R rho0, p0, g[3];
+};
+
+// Hydrostatic base state and gravity at a point (Sec. 1).
+template <typename R>
+__device__ __forceinline__ Base<R> base_at(const SweepArgs<R> &A, const R xyz[3]) {
+    Base<R> b;
+    b.g[0] = b.g[1] = b.g[2] = (R)0;
+    if (A.grav == 0) {
+        b.rho0 = A.rho0_c;
+        b.p0 = A.p0_c;
+    } else if (A.grav == 1) {
+        b.rho0 = lerp_tab(A, A.t_rho0, xyz[2]);
+        b.p0 = lerp_tab(A, A.t_p0, xyz[2]);
+        b.g[2] = lerp_tab(A, A.t_g, xyz[2]);
+    } else {
+        const R r = xsqrt(xadd(xadd(xmul(xyz[0], xyz[0]), xmul(xyz[1], xyz[1])), xmul(xyz[2], xyz[2])));
+        b.rho0 = lerp_tab(A, A.t_rho0, r);
+        b.p0 = lerp_tab(A, A.t_p0, r);
+        if (r > (R)0) {
+            const R gor = xdiv(lerp_tab(A, A.t_g, r), r);
+            b.g[0] = xmul(gor, xyz[0]);
+            b.g[1] = xmul(gor, xyz[1]);
+            b.g[2] = xmul(gor, xyz[2]);
+        }
+    }
+    return b;
+}
+
+template <typename R>
+__device__ __forceinline__ R coord(const SweepArgs<R> &A, int d, int idx) {
+    return xadd((R)A.org[d], xmul(xadd((R)idx, (R)0.5), (R)A.dx));
+}
+
+// ---------------------------------------------------------------------------
+// Pass building blocks (one cell / one face at a time)
+// ---------------------------------------------------------------------------
+
+// a2: fourth-order interface value between a1 and a2 (Sec. 1).
+template <typename R>
+__device__ __forceinline__ R iface(R a0, R a1, R a2, R a3) {
+    return ((R)7 * (a1 + a2) - (a0 + a3)) * (R)(1.0 / 12.0);
+}
+
+// a3: smoothness on the 5-cell stencil (Sec. 1); see the reading in the oracle.
+template <typename R>
+__device__ __forceinline__ bool smooth5(R am2, R am1, R a0, R ap1, R ap2, R scale) {
+    const R d1m2 = am1 - am2, d1m1 = a0 - am1, d10 = ap1 - a0, d1p1 = ap2 - ap1;
+    const R d2m = d1m1 - d1m2, d20 = d10 - d1m1, d2p = d1p1 - d10;
+    const R T = rmax(rabs(d20 - d2m), rabs(d2p - d20));
+    const R S = rmax(rmax(rabs(d1m1), rabs(d10)), rmax(rmax(rabs(d2m), rabs(d20)), rabs(d2p)));
+    return T <= (R)0.5 * S + (R)1e-9 * scale;
+}
+
+// a4: parabola of one variable; returns aL, aR, a6 (da = aR - aL).
+template <typename R>
+__device__ __forceinline__ void parabola(R am, R a, R ap, R aL, R aR, R f, bool smooth, R &oL, R &oR,
+                                         R &o6) {
+    if (f > (R)0) {
+        aL = aL + f * (a - aL);
+        aR = aR + f * (a - aR);
+    }
+    if (!smooth) {
+        aL = rclamp(aL, rmin(am, a), rmax(am, a));
+        aR = rclamp(aR, rmin(a, ap), rmax(a, ap));
+        if ((aR - a) * (a - aL) <= (R)0) {
+            aL = a;
+            aR = a;
+        } else {
+            const R da = aR - aL;
+            const R dm = a - (R)0.5 * (aL + aR);
+            const R d6 = da * da * (R)(1.0 / 6.0);
+            if (da * dm > d6)
+                aL = (R)3 * a - (R)2 * aR;
+            else if (-d6 > da * dm)
+                aR = (R)3 * a - (R)2 * aL;
+        }
+    }
+    oL = aL;
+    oR = aR;
+    o6 = (R)6 * (a - (R)0.5 * (aL + aR));
+}
+
+// Averages of the parabola over a domain of dependence of width s (cells)
+// at the right / left edge.
+template <typename R>
+__device__ __forceinline__ R fR(R aL, R aR, R a6, R s) {
+    return aR - (R)0.5 * s * ((aR - aL) - ((R)1 - (R)(2.0 / 3.0) * s) * a6);
+}
+template <typename R>
+__device__ __forceinline__ R fL(R aL, R aR, R a6, R s) {
+    return aL + (R)0.5 * s * ((aR - aL) + ((R)1 - (R)(2.0 / 3.0) * s) * a6);
+}
+
+// Error-free transforms for the compensated FP32 update.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
+    p = a * b;
+    e = fmaf(a, b, -p);
+}
+
+// Map a ghost index onto the pencil (periodic wrap or mirror).
+__device__ __forceinline__ int map_cell(int i, int n, int bl, int bh, bool &flip) {
+    flip = false;
+    if (i < 0) {
+        if (bl == 0) return i + n;
+        flip = true;
+        return -1 - i;
+    }
+    if (i >= n) {
+        if (bh == 0) return i - n;
+        flip = true;
+        return 2 * n - 1 - i;
+    }
+    return i;
+}
+__device__ __forceinline__ int map_face(int j, int n, int bl, int bh) {
+    int P = j + 1;
+    if (P < 0) return bl == 0 ? P + n : -P;
+    if (P > n) return bh == 0 ? P - n : 2 * n - P;
+    if (P == n && bh == 0) return 0;
+    return P;
+}
+
+__device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
+
+// FP32 storage of FV is folded: s = FV for FV <= 1/2 and s = FV - 1 (<= -0.0)
+// above, so both small concentrations and small complements (1 - FV) keep
+// their significant bits; updates act on s directly (FV + d <=> s + d).
+__device__ __forceinline__ float fv_unfold(float s) { return signbit(s) ? 1.0f + s : s; }
+__device__ __forceinline__ float fv_complement(float s) { return signbit(s) ? -s : 1.0f - s; }
+// s + d, clamped to FV in [0, 1] and refolded (all conversions are exact).
+__device__ __forceinline__ float fv_add(float s, float d) {
+    if (!signbit(s)) {
+        const float f = s + d;
+        if (!(f > 0.0f)) return 0.0f;
+        if (f <= 0.5f) return f;
+        if (f < 1.0f) return f - 1.0f;
+        return -0.0f;
+    }
+    const float t = s + d;
+    if (t >= 0.0f) return -0.0f;
+    if (t > -0.5f) return t;
+    if (t > -1.0f) return 1.0f + t;
+    return 0.0f;
+}
+// realisability bound of a first moment: 6 FV (1 - FV), from the folded value
+__device__ __forceinline__ float fv_moment_bound(float s) {
+    const float a = fabsf(s);
+    return 6.0f * a * (1.0f - a);
+}
+
+// ---------------------------------------------------------------------------
+// The kernel.  PLAIN: FP64 storage of full rho and E (subtracting the base
+// state on load and adding it back on store); otherwise deviation storage.
+// ---------------------------------------------------------------------------
+template <typename R, bool PLAIN>
+__global__ void __launch_bounds__(128) sweep_kernel(const SweepArgs<R> A) {
+    constexpr bool F32 = std::is_same<R, float>::value;
+    const int lane = blockIdx.x * blockDim.x + threadIdx.x;
+    const int blk = blockIdx.y;
+    // threads past the edge take part in the final warp reduction only
+    const bool active = (lane < A.nlane) && (blk < A.nblk);
+    R smax_local = 0;
+    bool bad = false;
+    if (active) {
+    const int n = A.n;
+    const int ax = A.axis, t1d = (ax + 1) % 3, t2d = (ax + 2) % 3;
+    R *__restrict__ q = A.q + (long long)lane * A.s_lane + (long long)blk * A.s_blk;
+    const long long vs = A.vs, sa = A.s_axis;
+
+    const R gam = (R)A.gamma, gm1 = (R)(A.gamma - 1.0);
+    const R kk = (R)((A.gamma + 1.0) / (2.0 * A.gamma));
+    const R gg1 = (R)(A.gamma / (A.gamma - 1.0));
+    const double dtd = *A.dt;
+    const R dt = (R)dtd;
+    const R dtdx = (R)(dtd / A.dx);
+    const R hdt = (R)0.5 * dt;
+
+    // transverse position of this pencil
+    int ijk[3];
+    ijk[A.lane_dim] = lane;
+    ijk[A.blk_dim] = blk;
+    R xyz[3];
+    xyz[t1d] = coord(A, t1d, ijk[t1d]);
+    xyz[t2d] = coord(A, t2d, ijk[t2d]);
+    const R lo = (R)A.org[ax];
+
+    // per-thread stash of the 4 cells that serve as high-side ghosts
+    R stash[4][9];
+
+    // ---- windows: slot s holds cell c-4+s --------------------------------
+    R wrd[5], wu[5], wv[5], ww[5], wpd[5];     // primitives for interpolation
+    R wfv[5], won[5], wo1[5], wo2[5];          // FV and moments
+    R wro[5];                                  // full old density
+    R wp0[5], wr0[5];                          // base state at the cell
+    R wg[5];                                   // gravity along the pass
+    R wmn[5], wm1[5], wm2[5], wed[5];          // conserved momenta and E'
+    R wfs[5];                                  // stored (FP32: folded) FV
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        wrd[s] = wu[s] = wv[s] = ww[s] = wpd[s] = (R)0;
+        wfv[s] = won[s] = wo1[s] = wo2[s] = (R)0;
+        wro[s] = wr0[s] = wp0[s] = (R)1;
+        wg[s] = wmn[s] = wm1[s] = wm2[s] = wed[s] = wfs[s] = (R)0;
+    }
+    // interface values of face (c-3)+1/2 (from the previous step)
+    R afp[5] = {0, 0, 0, 0, 0};
+    // traced left state of face (c-3)+1/2 (right edge of cell c-3)
+    R WLp[5] = {0, 0, 0, 0, 0};
+    // fluxes of face (c-4)+1/2
+    R Frp = 0, Frlp = 0, Fnp = 0, Ft1p = 0, Ft2p = 0, FEp = 0, FElp = 0;
+    // PPB: profile of cell c-3, face (c-4)+1/2 transfers, FCT factors of cell c-4
+    R me3 = 0, ae3 = 0;
+    R GLp = 0, Ap = 0, KLp = 0, KHp = 0, T1p = 0, T2p = 0, PHIp = 0, KMp = 0, sgp = 0;
+    R Rp4 = 0, Rm4 = 0;
+    // limited transfers of face (c-5)+1/2
+    R Gq = 0, Kq = 0, T1q = 0, T2q = 0, PHIq = 0, KMq = 0, sgq = 0;
+    // hydro update of cell c-4 (computed one step earlier)
+    R rdn4 = 0, mnn4 = 0, m1n4 = 0, m2n4 = 0, edn4 = 0;
+
+    for (int c = -G; c < n + G; ++c) {
+        // ================= a1: load cell c ==================================
+        R raw[9];
+        bool flip = false;
+        int m;
+        if (c >= n) {
+            m = map_cell(c, n, A.bc_lo, A.bc_hi, flip);
+            const int si = (A.bc_hi == 0) ? (c - n) : (n + 3 - c);
+#pragma unroll
+            for (int v = 0; v < 9; ++v) raw[v] = stash[si][v];
+        } else {
+            m = map_cell(c, n, A.bc_lo, A.bc_hi, flip);
+            const R *p = q + (long long)m * sa;
+#pragma unroll
+            for (int v = 0; v < 9; ++v) raw[v] = p[v * vs];
+            if (c >= 0) {
+                const int si = (A.bc_hi == 0) ? c : (c - (n - 4));
+                if (si >= 0 && si < 4) {
+#pragma unroll
+                    for (int v = 0; v < 9; ++v) stash[si][v] = raw[v];
+                }
+            }
+        }
+        R cx[3] = {xyz[0], xyz[1], xyz[2]};
+        cx[ax] = coord(A, ax, m);
+        const Base<R> b = base_at(A, cx);
+        const R sg = flip ? (R)-1 : (R)1;
+        // rotate into the pass frame and subtract the base state
+        const R rd = PLAIN ? xsub(raw[0], b.rho0) : raw[0];
+        const R mn = sg * raw[1 + ax];
+        const R m1 = raw[1 + t1d];
+        const R m2 = raw[1 + t2d];
+        const R ed = PLAIN ? xsub(raw[4], xdiv(b.p0, gm1)) : raw[4];
+        const R rho = b.rho0 + rd;
+        const R rinv = (R)1 / rho;
+        const R u = mn * rinv, v = m1 * rinv, w = m2 * rinv;
+        const R ke = (R)0.5 * (mn * u + (m1 * v + m2 * w));
+        const R pd = gm1 * (ed - ke);
+        // shift windows and insert cell c at slot 4
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            wrd[s] = wrd[s + 1]; wu[s] = wu[s + 1]; wv[s] = wv[s + 1]; ww[s] = ww[s + 1];
+            wpd[s] = wpd[s + 1]; wfv[s] = wfv[s + 1]; won[s] = won[s + 1]; wo1[s] = wo1[s + 1];
+            wo2[s] = wo2[s + 1]; wro[s] = wro[s + 1]; wp0[s] = wp0[s + 1]; wr0[s] = wr0[s + 1];
+            wg[s] = wg[s + 1]; wmn[s] = wmn[s + 1]; wm1[s] = wm1[s + 1]; wm2[s] = wm2[s + 1];
+            wed[s] = wed[s + 1]; wfs[s] = wfs[s + 1];
+        }
+        wrd[4] = rd; wu[4] = u; wv[4] = v; ww[4] = w; wpd[4] = pd;
+        if constexpr (F32) {
+            wfv[4] = fv_unfold(raw[5]);
+        } else {
+            wfv[4] = raw[5];
+        }
+        wfs[4] = raw[5];
+        won[4] = sg * raw[6 + ax];
+        wo1[4] = raw[6 + t1d];
+        wo2[4] = raw[6 + t2d];
+        wro[4] = rho; wp0[4] = b.p0; wr0[4] = b.rho0;
+        wg[4] = sg * b.g[ax];
+        wmn[4] = mn; wm1[4] = m1; wm2[4] = m2; wed[4] = ed;
+
+        // ================= a2: interface values of face (c-2)+1/2 ==========
+        R afn[5];
+        afn[0] = iface(wrd[1], wrd[2], wrd[3], wrd[4]);
+        afn[1] = iface(wu[1], wu[2], wu[3], wu[4]);
+        afn[2] = iface(wv[1], wv[2], wv[3], wv[4]);
+        afn[3] = iface(ww[1], ww[2], ww[3], ww[4]);
+        afn[4] = iface(wpd[1], wpd[2], wpd[3], wpd[4]);
+
+        // ================= a3-a5: cell c-2 (slot 2) ========================
+        R WLn[5], WRc[5];
+        {
+            const R rho2 = wro[2];
+            const R p2 = wp0[2] + wpd[2];
+            const R c2 = gam * p2 / rho2;
+            const R cs = rsq(c2);
+            // flattening coefficient
+            R f = (R)0;
+            {
+                const R dp1 = wpd[3] - wpd[1];
+                const R dp2 = wpd[4] - wpd[0];
+                const R pmin = rmin(wp0[3] + wpd[3], wp0[1] + wpd[1]);
+                if (rabs(dp1) > (R)0.33 * pmin && wu[1] - wu[3] > (R)0) {
+                    const R r = (dp2 != (R)0) ? dp1 / dp2 : (R)1;
+                    f = rclamp((R)10 * (r - (R)0.75), (R)0, (R)1);
+                }
+            }
+            // parabolas of the five variables
+            R aL[5], aR[5], a6[5];
+            {
+                const bool s0 = smooth5(wrd[0], wrd[1], wrd[2], wrd[3], wrd[4], rho2);
+                parabola(wrd[1], wrd[2], wrd[3], afp[0], afn[0], f, s0, aL[0], aR[0], a6[0]);
+                const bool s1 = smooth5(wu[0], wu[1], wu[2], wu[3], wu[4], cs);
+                parabola(wu[1], wu[2], wu[3], afp[1], afn[1], f, s1, aL[1], aR[1], a6[1]);
+                const bool s2 = smooth5(wv[0], wv[1], wv[2], wv[3], wv[4], cs);
+                parabola(wv[1], wv[2], wv[3], afp[2], afn[2], f, s2, aL[2], aR[2], a6[2]);
+                const bool s3 = smooth5(ww[0], ww[1], ww[2], ww[3], ww[4], cs);
+                parabola(ww[1], ww[2], ww[3], afp[3], afn[3], f, s3, aL[3], aR[3], a6[3]);
+                const bool s4 = smooth5(wpd[0], wpd[1], wpd[2], wpd[3], wpd[4], p2);
+                parabola(wpd[1], wpd[2], wpd[3], afp[4], afn[4], f, s4, aL[4], aR[4], a6[4]);
+            }
+            // characteristic tracing (waves u-c, u, u+c) + buoyancy
+            const R uc = wu[2];
+            const R C = rho2 * cs;
+            const R lm = uc - cs, l0 = uc, lp = uc + cs;
+            const R hg = hdt * ((wrd[2] / rho2) * wg[2]);
+            {   // right edge -> left state of face (c-2)+1/2
+                const R sp = rmax(lp, (R)0) * dtdx;
+                R st[5];
+#pragma unroll
+                for (int k = 0; k < 5; ++k) st[k] = fR(aL[k], aR[k], a6[k], sp);
+                const R rr = st[0], ru = st[1], rv = st[2], rw = st[3], rp = st[4];
+                if (l0 > (R)0) {
+                    const R s0 = l0 * dtdx;
+                    const R dr = rr - fR(aL[0], aR[0], a6[0], s0);
+                    const R dp = rp - fR(aL[4], aR[4], a6[4], s0);
+                    st[0] = st[0] - (dr - dp / c2);
+                    st[2] = st[2] - (rv - fR(aL[2], aR[2], a6[2], s0));
+                    st[3] = st[3] - (rw - fR(aL[3], aR[3], a6[3], s0));
+                }
+                if (lm > (R)0) {
+                    const R sm = lm * dtdx;
+                    const R du = ru - fR(aL[1], aR[1], a6[1], sm);
+                    const R dp = rp - fR(aL[4], aR[4], a6[4], sm);
+                    const R Aa = (R)0.5 * (dp - C * du);
+                    st[0] = st[0] - Aa / c2;
+                    st[1] = st[1] + Aa / C;
+                    st[4] = st[4] - Aa;
+                }
+                st[1] = st[1] + hg;
+#pragma unroll
+                for (int k = 0; k < 5; ++k) WLn[k] = st[k];
+            }
+            {   // left edge -> right state of face (c-3)+1/2
+                const R sm = rmax(-lm, (R)0) * dtdx;
+                R st[5];
+#pragma unroll
+                for (int k = 0; k < 5; ++k) st[k] = fL(aL[k], aR[k], a6[k], sm);
+                const R rr = st[0], ru = st[1], rv = st[2], rw = st[3], rp = st[4];
+                if (l0 < (R)0) {
+                    const R s0 = -l0 * dtdx;
+                    const R dr = rr - fL(aL[0], aR[0], a6[0], s0);
+                    const R dp = rp - fL(aL[4], aR[4], a6[4], s0);
+                    st[0] = st[0] - (dr - dp / c2);
+                    st[2] = st[2] - (rv - fL(aL[2], aR[2], a6[2], s0));
+                    st[3] = st[3] - (rw - fL(aL[3], aR[3], a6[3], s0));
+                }
+                if (lp < (R)0) {
+                    const R s1 = -lp * dtdx;
+                    const R du = ru - fL(aL[1], aR[1], a6[1], s1);
+                    const R dp = rp - fL(aL[4], aR[4], a6[4], s1);
+                    const R Aa = (R)0.5 * (dp + C * du);
+                    st[0] = st[0] - Aa / c2;
+                    st[1] = st[1] - Aa / C;
+                    st[4] = st[4] - Aa;
+                }
+                st[1] = st[1] + hg;
+#pragma unroll
+                for (int k = 0; k < 5; ++k) WRc[k] = st[k];
+            }
+        }
+
+        // ================= a6-a7: Riemann + fluxes at face (c-3)+1/2 =======
+        R Frc, Frlc, Fnc, Ft1c, Ft2c, FEc, FElc, usc;
+        {
+            const int j = c - 3;
+            R fx[3] = {xyz[0], xyz[1], xyz[2]};
+            fx[ax] = xadd(lo, xmul((R)map_face(j, n, A.bc_lo, A.bc_hi), (R)A.dx));
+            const Base<R> bf = base_at(A, fx);
+            const R r0 = bf.rho0, p0 = bf.p0;
+            const R rdL = WLp[0], uL = WLp[1], pdL = WLp[4];
+            const R rdR = WRc[0], uR = WRc[1], pdR = WRc[4];
+            const R rL = r0 + rdL, pL = p0 + pdL;
+            const R rR = r0 + rdR, pR = p0 + pdR;
+            const R CL = rsq(gam * pL * rL), CR = rsq(gam * pR * rR);
+            const R pfl = (R)1e-10 * rmin(pL, pR);
+            R den = CL + CR;
+            R pst = pdL + CL * (CR * (uL - uR) + (pdR - pdL)) / den;
+            R ust = uL + (CR * (uR - uL) + (pdL - pdR)) / den;
+            if (p0 + pst < pfl) pst = pfl - p0;
+            const R WLi = CL * rsq((R)1 + kk * (pst - pdL) / pL);
+            const R WRi = CR * rsq((R)1 + kk * (pst - pdR) / pR);
+            den = WLi + WRi;
+            pst = pdL + WLi * (WRi * (uL - uR) + (pdR - pdL)) / den;
+            ust = uL + (WRi * (uR - uL) + (pdL - pdR)) / den;
+            if (p0 + pst < pfl) pst = pfl - p0;
+            if ((j == -1 && A.bc_lo == 1) || (j == n - 1 && A.bc_hi == 1)) ust = (R)0;
+            const bool left = (ust >= (R)0);
+            const R rds = left ? rdL : rdR;
+            const R pds = left ? pdL : pdR;
+            const R rs = left ? rL : rR;
+            const R pss = left ? pL : pR;
+            const R vst = left ? WLp[2] : WRc[2];
+            const R wst = left ? WLp[3] : WRc[3];
+            const R dps = pst - pds;
+            const R rdst = rds + rs * dps / (gam * pss + (R)0.5 * gm1 * dps);
+            const R h0 = gg1 * p0;
+            const R kin = (R)0.5 * (ust * ust + (vst * vst + wst * wst));
+            if constexpr (F32) {
+                // mass and energy fluxes carry their large base-state parts
+                // (rho0 u*, h0 u*) as exact hi+lo pairs
+                float hi, e;
+                two_prod(r0, ust, hi, e);
+                Frc = hi;
+                Frlc = e + rdst * ust;
+                const float Fr = Frc + Frlc;
+                float hE, eE;
+                two_prod(ust, h0, hE, eE);
+                FEc = hE;
+                FElc = eE + (ust * (gg1 * pst) + kin * Fr);
+                Fnc = Fr * ust + pst;
+                Ft1c = Fr * vst;
+                Ft2c = Fr * wst;
+            } else {
+                const R Fr = (r0 + rdst) * ust;
+                Frc = Fr;
+                Frlc = 0;
+                Fnc = Fr * ust + pst;
+                Ft1c = Fr * vst;
+                Ft2c = Fr * wst;
+                FEc = ust * (gg1 * pst + h0) + kin * Fr;
+                FElc = 0;
+            }
+            usc = ust;
+        }
+
+        // ================= a8: hydro update of cell c-3 (slot 1) ===========
+        R rdn3, mnn3, m1n3, m2n3, edn3;
+        {
+            const R g = wg[1];
+            if constexpr (F32) {
+                float s, e;
+                two_sum(Frc, -Frp, s, e);
+                const float dFr = s + (e + (Frlc - Frlp));
+                rdn3 = wrd[1] - dtdx * dFr;
+                two_sum(FEc, -FEp, s, e);
+                const float dFE = s + (e + (FElc - FElp));
+                edn3 = wed[1] - dtdx * dFE + dt * g * ((R)0.5 * ((Frp + Frlp) + (Frc + Frlc)));
+            } else {
+                rdn3 = wrd[1] - dtdx * (Frc - Frp);
+                edn3 = wed[1] - dtdx * (FEc - FEp) + dt * g * ((R)0.5 * (Frp + Frc));
+            }
+            mnn3 = wmn[1] - dtdx * (Fnc - Fnp) + dt * g * ((R)0.5 * (wrd[1] + rdn3));
+            m1n3 = wm1[1] - dtdx * (Ft1c - Ft1p);
+            m2n3 = wm2[1] - dtdx * (Ft2c - Ft2p);
+        }
+        const R rnew3 = wr0[1] + rdn3;
+
+        // ================= a9: PPB ==========================================
+        // profile of cell c-2 (slot 2): f = FV + m xi + a2 (xi^2 - 1/12), bound-limited
+        R me2, ae2;
+        {
+            const R F = wfv[2], mm = won[2];
+            const R a2 = (R)0.25 * (won[3] - won[1]);
+            const R ep = (R)0.5 * mm + a2 * (R)(1.0 / 6.0);
+            const R em = a2 * (R)(1.0 / 6.0) - (R)0.5 * mm;
+            R gmax = rmax(ep, em), gmin = rmin(ep, em);
+            if (a2 != (R)0) {
+                const R xv = -mm / ((R)2 * a2);
+                if (rabs(xv) < (R)0.5) {
+                    const R gv = mm * xv + a2 * (xv * xv - (R)(1.0 / 12.0));
+                    gmax = rmax(gmax, gv);
+                    gmin = rmin(gmin, gv);
+                }
+            }
+            R th = (R)1;
+            if constexpr (F32) {
+                const float omf = fv_complement(wfs[2]);
+                if (gmax > omf) th = rmin(th, omf / gmax);
+                if (-gmin > F) th = rmin(th, F / (-gmin));
+            } else {
+                if (F + gmax > (R)1) th = rmin(th, ((R)1 - F) / gmax);
+                if (F + gmin < (R)0) th = rmin(th, F / (-gmin));
+            }
+            me2 = th * mm;
+            ae2 = th * a2;
+        }
+        // transfers across face (c-3)+1/2: donor c-3 (slot 1) or c-2 (slot 2)
+        R GLc, Ac, KLc, KHc, T1c, T2c, PHIc, KMc, sgc;
+        {
+            const R Fr = Frc + Frlc;
+            const R sig = usc * dtdx;
+            const R phi = dtdx * Fr;
+            const bool fromleft = (sig >= (R)0);
+            const R s = fromleft ? sig : -sig;
+            R M1 = (R)0.5 - (R)0.5 * s;
+            const R M2 = (R)0.25 - (R)0.5 * s + s * s * (R)(1.0 / 3.0);
+            R M3 = (R)0.125 - (R)0.375 * s + (R)0.5 * s * s - (R)0.25 * s * s * s;
+            if (!fromleft) {
+                M1 = -M1;
+                M3 = -M3;
+            }
+            const R F = fromleft ? wfv[1] : wfv[2];
+            const R me = fromleft ? me3 : me2;
+            const R ae = fromleft ? ae3 : ae2;
+            const R ot1 = fromleft ? wo1[1] : wo1[2];
+            const R ot2 = fromleft ? wo2[1] : wo2[2];
+            const R phibar = F + me * M1 + ae * (M2 - (R)(1.0 / 12.0));
+            const R psibar = F * M1 + me * M2 + ae * (M3 - M1 * (R)(1.0 / 12.0));
+            GLc = phi * F;
+            Ac = phi * phibar - GLc;
+            KLc = phi * F * M1;
+            KHc = phi * psibar;
+            T1c = phi * ot1;
+            T2c = phi * ot2;
+            PHIc = phi;
+            KMc = phi * M1;
+            sgc = sig;
+        }
+        // FCT factors of cell c-3 (slot 1), bounds [0,1]
+        R Rp3, Rm3;
+        {
+            const R rold = wro[1];
+            const R cL = rold * wfv[1] - (GLc - GLp);
+            const R FVL = cL / rnew3;
+            const R Pp = rmax((R)0, Ap) - rmin((R)0, Ac);
+            const R Pm = rmax((R)0, Ac) - rmin((R)0, Ap);
+            const R Qp = ((R)1 - FVL) * rnew3;
+            const R Qm = FVL * rnew3;
+            Rp3 = (Pp > (R)0) ? rclamp(Qp / Pp, (R)0, (R)1) : (R)0;
+            Rm3 = (Pm > (R)0) ? rclamp(Qm / Pm, (R)0, (R)1) : (R)0;
+        }
+        // limit face (c-4)+1/2 with the factors of cells c-4 and c-3
+        R Gc4, Kc4;
+        {
+            const R Cf = (Ap >= (R)0) ? rmin(Rp3, Rm4) : rmin(Rp4, Rm3);
+            Gc4 = GLp + Cf * Ap;
+            Kc4 = KLp + Cf * (KHp - KLp);
+        }
+
+        // ================= final update of cell c-4 (slot 0) ===============
+        if (c >= G) {
+            const int i = c - G;
+            const R rold = wro[0];
+            const R rnew = wr0[0] + rdn4;
+            const R sm = sgq, sp = sgp;
+            const R cold = rold * wfv[0];
+            R c_out = 0, z_out = 0, z_in = 0, m_out = 0, zr_out = 0, zr_in = 0;
+            if (sp >= (R)0) {
+                c_out = c_out + Gc4;
+                z_out = z_out + Kc4;
+                m_out = m_out + PHIp;
+                zr_out = zr_out + KMp;
+            } else {
+                const R sh = sp + (R)1;
+                z_in = z_in + (-Kc4 - Gc4 * sh);
+                zr_in = zr_in + (-KMp - PHIp * sh);
+            }
+            if (sm >= (R)0) {
+                const R sh = sm - (R)1;
+                z_in = z_in + (Kq + Gq * sh);
+                zr_in = zr_in + (KMq + PHIq * sh);
+            } else {
+                c_out = c_out - Gq;
+                z_out = z_out - Kq;
+                m_out = m_out - PHIq;
+                zr_out = zr_out - KMq;
+            }
+            const R sbar = (R)0.5 * (sm + sp);
+            const R dZc = (cold - c_out) * sbar + z_in - z_out;
+            const R Zr = (rold - m_out) * sbar + zr_in - zr_out;
+            const R dPhi = PHIp - PHIq;
+            const R dG = Gc4 - Gq;
+            const R rinvn = (R)1 / rnew;
+            R fvn, fvs, bnd;
+            if constexpr (F32) {
+                fvs = fv_add(wfs[0], (wfv[0] * dPhi - dG) * rinvn);
+                fvn = fv_unfold(fvs);
+                bnd = fv_moment_bound(fvs);
+            } else {
+                fvn = rclamp(wfv[0] + (wfv[0] * dPhi - dG) * rinvn, (R)0, (R)1);
+                fvs = fvn;
+                bnd = (R)6 * fvn * ((R)1 - fvn);
+            }
+            R onn = won[0] + (won[0] * dPhi + (R)12 * (dZc - fvn * Zr)) * rinvn;
+            R o1 = wo1[0] + (wo1[0] * dPhi - (T1p - T1q)) * rinvn;
+            R o2 = wo2[0] + (wo2[0] * dPhi - (T2p - T2q)) * rinvn;
+            onn = rclamp(onn, -bnd, bnd);
+            o1 = rclamp(o1, -bnd, bnd);
+            o2 = rclamp(o2, -bnd, bnd);
+
+            R rdo = rdn4, mno = mnn4, m1o = m1n4, m2o = m2n4, edo = edn4;
+            R cxo[3] = {xyz[0], xyz[1], xyz[2]};
+            cxo[ax] = coord(A, ax, i);
+            if (A.sources) {
+                const R s = (A.grav == 1) ? cxo[2]
+                                          : xsqrt(xadd(xadd(xmul(cxo[0], cxo[0]), xmul(cxo[1], cxo[1])),
+                                                       xmul(cxo[2], cxo[2])));
+                if (A.t_heat) edo = edo + dt * lerp_tab(A, A.t_heat, s);
+                if (A.t_damp) {
+                    const R kd = lerp_tab(A, A.t_damp, s);
+                    const R fd = rmax((R)0, (R)1 - dt * kd);
+                    const R kin = (R)0.5 * (mno * mno + (m1o * m1o + m2o * m2o)) / rnew;
+                    mno = mno * fd;
+                    m1o = m1o * fd;
+                    m2o = m2o * fd;
+                    edo = edo - ((R)1 - fd * fd) * kin;
+                }
+            }
+            // physical checks and CFL maximum on the final values
+            {
+                const R ri = (R)1 / rnew;
+                const R uu = mno * ri, vv = m1o * ri, wv_ = m2o * ri;
+                const R kin = (R)0.5 * (mno * uu + (m1o * vv + m2o * wv_));
+                const R pr = wp0[0] + gm1 * (edo - kin);
+                if (!(rnew > (R)0) || !(pr > (R)0)) bad = true;
+                if (A.cfl) {
+                    const R spd = rmax(rmax(rabs(uu), rabs(vv)), rabs(wv_)) + rsq(gam * pr * ri);
+                    smax_local = rmax(smax_local, spd);
+                }
+            }
+            R *p = q + (long long)i * sa;
+            p[0] = PLAIN ? xadd(wr0[0], rdo) : rdo;
+            p[(1 + ax) * vs] = mno;
+            p[(1 + t1d) * vs] = m1o;
+            p[(1 + t2d) * vs] = m2o;
+            p[4 * vs] = PLAIN ? xadd(xdiv(wp0[0], gm1), edo) : edo;
+            p[5 * vs] = fvs;
+            p[(6 + ax) * vs] = onn;
+            p[(6 + t1d) * vs] = o1;
+            p[(6 + t2d) * vs] = o2;
+        }
+
+        // ================= carry to the next step ===========================
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            afp[k] = afn[k];
+            WLp[k] = WLn[k];
+        }
+        Frp = Frc; Frlp = Frlc; Fnp = Fnc; Ft1p = Ft1c; Ft2p = Ft2c; FEp = FEc; FElp = FElc;
+        me3 = me2; ae3 = ae2;
+        Gq = Gc4; Kq = Kc4; T1q = T1p; T2q = T2p; PHIq = PHIp; KMq = KMp; sgq = sgp;
+        GLp = GLc; Ap = Ac; KLp = KLc; KHp = KHc; T1p = T1c; T2p = T2c; PHIp = PHIc; KMp = KMc; sgp = sgc;
+        Rp4 = Rp3; Rm4 = Rm3;
+        rdn4 = rdn3; mnn4 = mnn3; m1n4 = m1n3; m2n4 = m2n3; edn4 = edn3;
+    }
+    }  // active
+
+    if (bad) atomicOr(A.flags, FLAG_NONPHYS);
+    if (A.cfl) {
+        // warp max, then one atomic per warp (double bits of positive values
+        // order like unsigned integers)
+        double sm = (double)smax_local;
+        for (int o = 16; o > 0; o >>= 1) sm = fmax(sm, __shfl_xor_sync(0xffffffffu, sm, o));
+        if ((threadIdx.x & 31) == 0) atomicMax(A.smax, dbits(sm));
+    }
+}
+
+}  // namespace ppm

@@ -1,0 +1,297 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle.
+
+Same seeded inputs on both sides, the same explicit dt sequence (taken from
+the oracle), element by element:
+  * FP64 plain form: relative L-inf <= 1e-10 per variable after 20 double
+    steps (relative to the variable's largest magnitude);
+  * FP32 deviation form: relative L1 <= 1e-5 on rho and E, mean |dFV| <= 1e-7;
+  * exact states (uniform, hydrostatic) preserved bit for bit;
+  * full-size sampled parity: single passes of the 1024^3 sphere checked
+    pencil by pencil against the oracle's single-pencil pass.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1810_13416_gb300 as ppm
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+TOL_F64 = 1e-10
+TOL_F32_L1 = 1e-5
+TOL_F32_FV = 1e-7
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ppm.build()
+    oracle.build()
+
+
+def _relinf(a, b):
+    s = np.abs(b).max()
+    return np.abs(a - b).max() / (s if s > 0 else 1.0)
+
+
+def _run_pair(p, precision, steps, q0=None):
+    q = workloads.build(p) if q0 is None else [a.copy() for a in q0]
+    qo = [a.copy() for a in q]
+    o = oracle.Oracle(p)
+    ctx = ppm.Context.from_problem(p, precision=precision)
+    ctx.set_state(q)
+    for _ in range(steps):
+        dt = o.cfl_dt(qo, p.cfl)
+        o.double_step(qo, dt)
+        ctx.step(dt)
+    qg = ctx.get_state()
+    ctx.close()
+    return qg, qo
+
+
+def _assert_f64(qg, qo):
+    for v in range(9):
+        assert _relinf(qg[v], qo[v]) <= TOL_F64, (v, _relinf(qg[v], qo[v]))
+
+
+def _assert_f32(qg, qo):
+    for v in (0, 4):
+        l1 = np.abs(qg[v] - qo[v]).sum() / np.abs(qo[v]).sum()
+        assert l1 <= TOL_F32_L1, (v, l1)
+    fv = np.abs(qg[5] - qo[5]).mean()
+    assert fv <= TOL_F32_FV, fv
+    assert qg[5].min() >= 0.0 and qg[5].max() <= 1.0
+
+
+def test_periodic_box_fp64_20_steps():
+    p = workloads.periodic_box(32)
+    qg, qo = _run_pair(p, ppm.FP64_PLAIN, 20)
+    _assert_f64(qg, qo)
+
+
+def test_periodic_box_fp32_20_steps():
+    p = workloads.periodic_box(32)
+    qg, qo = _run_pair(p, ppm.FP32_DEVIATION, 20)
+    _assert_f32(qg, qo)
+
+
+def _strat_ragged():
+    # not a multiple of the 128-thread tile, several tiles along x
+    return workloads.strat_box(shape=(150, 20, 36))
+
+
+def _sphere_ragged():
+    return workloads.sphere(shape=(44, 36, 40))
+
+
+@pytest.mark.parametrize("maker", [_strat_ragged, _sphere_ragged])
+def test_gravity_problems_fp64(maker):
+    p = maker()
+    qg, qo = _run_pair(p, ppm.FP64_PLAIN, 8)
+    _assert_f64(qg, qo)
+
+
+@pytest.mark.parametrize("maker", [_strat_ragged, _sphere_ragged])
+def test_gravity_problems_fp32(maker):
+    p = maker()
+    qg, qo = _run_pair(p, ppm.FP32_DEVIATION, 8)
+    _assert_f32(qg, qo)
+
+
+@pytest.mark.parametrize("kind", ["sod", "lax"])
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_shock_tubes_fp64(kind, axis):
+    p = workloads.tube(kind, n=64, axis=axis, length=1.0 if kind == "sod" else 2.0)
+    p.cfl = 0.6
+    qg, qo = _run_pair(p, ppm.FP64_PLAIN, 15)
+    _assert_f64(qg, qo)
+
+
+@pytest.mark.parametrize("precision", [ppm.FP64_PLAIN, ppm.FP32_DEVIATION])
+def test_uniform_state_preserved_bitwise(precision):
+    p = workloads.periodic_box(shape=(8, 12, 16))
+    nz, ny, nx = 16, 12, 8
+    q = [np.zeros((nz, ny, nx)) for _ in range(9)]
+    q[0][:] = 1.0
+    vel = (0.25, -0.125, 0.375)
+    for d in range(3):
+        q[1 + d][:] = vel[d]
+    q[4][:] = 0.75 / (p.gamma - 1.0) + 0.5 * sum(v * v for v in vel)
+    q[5][:] = 1.0
+    ctx = ppm.Context.from_problem(p, precision=precision)
+    ctx.set_state(q)
+    q_in = ctx.get_state()
+    for _ in range(10):
+        ctx.step(ctx.cfl_dt(0.7))
+    q_out = ctx.get_state()
+    for v in range(9):
+        assert np.array_equal(q_in[v], q_out[v]), v
+
+
+@pytest.mark.parametrize("precision", [ppm.FP64_PLAIN, ppm.FP32_DEVIATION])
+@pytest.mark.parametrize("which", ["strat", "sphere"])
+def test_hydrostatic_state_preserved_bitwise(precision, which):
+    if which == "strat":
+        p = workloads.strat_box(shape=(8, 6, 24), noise=0.0)
+    else:
+        p = workloads.sphere(n=20, mach=0.0)
+    p.tables.heat = None
+    p.tables.damp = None
+    q = workloads.build(p)
+    ctx = ppm.Context.from_problem(p, precision=precision)
+    ctx.set_state(q)
+    q_in = ctx.get_state()
+    for _ in range(10):
+        ctx.step(ctx.cfl_dt(0.7))
+    q_out = ctx.get_state()
+    for v in range(9):
+        assert np.array_equal(q_in[v], q_out[v]), v
+    if precision == ppm.FP64_PLAIN:
+        for v in range(9):
+            assert np.array_equal(q_out[v], q[v]), v
+
+
+def test_graph_step_equals_six_passes():
+    p = workloads.sphere(shape=(24, 20, 28))
+    q = workloads.build(p)
+    a = ppm.Context.from_problem(p, precision=ppm.FP32_DEVIATION)
+    b = ppm.Context.from_problem(p, precision=ppm.FP32_DEVIATION)
+    a.set_state(q)
+    b.set_state(q)
+    dt = a.cfl_dt(0.7)
+    a.step(dt)
+    for axis, src in ((0, 0), (1, 0), (2, 1), (2, 0), (1, 0), (0, 1)):
+        b.sweep(axis, dt, sources=bool(src))
+    qa, qb = a.get_state(), b.get_state()
+    for v in range(9):
+        assert np.array_equal(qa[v], qb[v]), v
+
+
+def test_device_dt_path_matches_explicit_dt():
+    p = workloads.periodic_box(16)
+    q = workloads.build(p)
+    a = ppm.Context.from_problem(p, precision=ppm.FP64_PLAIN)
+    b = ppm.Context.from_problem(p, precision=ppm.FP64_PLAIN)
+    a.set_state(q)
+    b.set_state(q)
+    a.cfl_dt(0.7, fetch=False)
+    for _ in range(3):
+        a.step(0.0)                      # dt from the fused CFL maximum on the device
+        b.step(b.cfl_dt(0.7))            # dt fetched and passed back explicitly
+    qa, qb = a.get_state(), b.get_state()
+    for v in range(9):
+        assert _relinf(qa[v], qb[v]) <= 1e-14, v
+
+
+@pytest.mark.parametrize("precision", [ppm.FP64_PLAIN, ppm.FP32_DEVIATION])
+def test_cfl_and_diagnostics_match_oracle(precision):
+    p = workloads.sphere(shape=(32, 28, 36))
+    q = workloads.build(p)
+    o = oracle.Oracle(p)
+    ctx = ppm.Context.from_problem(p, precision=precision)
+    ctx.set_state(q)
+    qs = ctx.get_state()                 # what the GPU holds (FP32-rounded for FP32)
+    dt_o = o.cfl_dt(qs, 0.7)
+    dt_g = ctx.cfl_dt(0.7)
+    tol = 1e-13 if precision == ppm.FP64_PLAIN else 1e-6
+    assert abs(dt_g - dt_o) <= tol * dt_o
+    tg, pg, mg = ctx.diagnostics(16, 1.0)
+    to, po, mo = o.diagnostics(qs, 16, 1.0)
+    np.testing.assert_allclose(tg, to, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(pg, po, rtol=(1e-12 if precision == ppm.FP64_PLAIN else 1e-5), atol=1e-12)
+    assert abs(mg - mo) <= (1e-12 if precision == ppm.FP64_PLAIN else 1e-5) * mo
+
+
+def test_nonphysical_state_is_reported():
+    p = workloads.periodic_box(16)
+    q = workloads.build(p)
+    q[4][3, 4, 5] = -1.0                 # negative energy -> negative pressure
+    ctx = ppm.Context.from_problem(p, precision=ppm.FP32_DEVIATION)
+    ctx.set_state(q)
+    ctx.sweep(0, 1e-4)
+    with pytest.raises(ppm.PpmError) as e:
+        ctx.sync()
+    assert e.value.code == -4
+    ctx.sync()                           # flag cleared after the report
+
+
+def test_region_roundtrip_host_and_device():
+    p = workloads.sphere(shape=(20, 18, 22))
+    q = workloads.build(p)
+    ctx = ppm.Context.from_problem(p, precision=ppm.FP64_PLAIN)
+    ctx.set_state(q)
+    lo, hi = (3, 2, 5), (17, 11, 20)
+    sub = ctx.get_region(lo, hi)
+    for v in range(9):
+        assert np.array_equal(sub[v], q[v][lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]])
+    dev = [torch.tensor(s, device="cuda") for s in sub]
+    for t in dev:
+        t.mul_(1.0)
+    ctx.set_region(lo, hi, dev, device=True)
+    out = [torch.empty_like(t) for t in dev]
+    ctx.get_region(lo, hi, out, device=True)
+    torch.cuda.synchronize()
+    for v in range(9):
+        assert np.array_equal(out[v].cpu().numpy(), sub[v])
+
+
+# --------------------------------------------------------------------------
+# Full size (the 1024^3 sphere in FP32, launch configuration of the benchmark):
+# single passes checked pencil by pencil against the oracle.
+# --------------------------------------------------------------------------
+def _upload_sphere(ctx, p, slab=64):
+    nz = p.shape[2]
+    for z0 in range(0, nz, slab):
+        z1 = min(nz, z0 + slab)
+        qs = workloads.initial_state(p, device="cuda", z_lo=z0, z_hi=z1)
+        ctx.set_region((0, 0, z0), (p.shape[0], p.shape[1], z1), [t.contiguous() for t in qs], device=True)
+        del qs
+    torch.cuda.synchronize()
+
+
+def _pencil_box(p, axis, ja, jb):
+    lo, hi = [0, 0, 0], [0, 0, 0]
+    lo[axis], hi[axis] = 0, p.shape[axis]
+    for d, j in (((axis + 1) % 3, ja), ((axis + 2) % 3, jb)):
+        lo[d], hi[d] = j, j + 1
+    return lo, hi
+
+
+def test_full_size_sphere_sampled_pencils_fp32():
+    n = 1024
+    free, _ = torch.cuda.mem_get_info()
+    if free < 60e9:
+        pytest.skip("needs ~60 GB of device memory")
+    p = workloads.sphere(n=n)
+    o = oracle.Oracle(p)
+    ctx = ppm.Context.from_problem(p, precision=ppm.FP32_DEVIATION)
+    _upload_sphere(ctx, p)
+    dt = ctx.cfl_dt(0.7)
+    rng = np.random.default_rng(1810)
+    for axis in (0, 1, 2):
+        picks = [(int(rng.integers(0, n)), int(rng.integers(0, n))) for _ in range(6)]
+        picks.append((n // 2, n // 2))     # through the centre of the star
+        ins = []
+        for ja, jb in picks:
+            lo, hi = _pencil_box(p, axis, ja, jb)
+            ins.append([a.reshape(-1).copy() for a in ctx.get_region(lo, hi)])
+        ctx.sweep(axis, dt, sources=(axis == 2))
+        for (ja, jb), pin in zip(picks, ins):
+            lo, hi = _pencil_box(p, axis, ja, jb)
+            got = [a.reshape(-1) for a in ctx.get_region(lo, hi)]
+            ref = o.sweep_pencil(pin, axis, ja, jb, dt, sources=(axis == 2))
+            for v in (0, 4):
+                err = np.abs(got[v] - ref[v]).max() / np.abs(ref[v]).max()
+                assert err <= 1e-6, (axis, ja, jb, v, err)
+            for v in (1, 2, 3):
+                scale = max(np.abs(ref[v]).max(), 1e-30)
+                assert np.abs(got[v] - ref[v]).max() <= 1e-4 * scale + 1e-7 * np.abs(ref[0]).max(), (axis, v)
+            assert np.abs(got[5] - ref[5]).max() <= 1e-5, (axis, ja, jb)
+    tot, _, mm = ctx.diagnostics()
+    assert np.isfinite(tot).all() and 0 < mm < 1
+    ctx.close()

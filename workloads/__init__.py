@@ -349,7 +349,7 @@ def sphere(n: int = 1024, seed: int = 5810, xi_R: float = 3.0, gamma: float = 5.
     dx = L / nz
     alpha = 1.0 / xi_R
     r_max = math.sqrt(3.0) * 1.02
-    h = 1e-4
+    h = (r_max / alpha) / 8192.0
     xi, th, dth = lane_emden(3.0, r_max / alpha + 2 * h, h)
     r = xi * alpha
     # table on uniform r grid with spacing alpha*h
