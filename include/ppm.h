@@ -137,6 +137,37 @@ int ppm_sync(ppm_ctx *ctx);
 /* Number of kernel launches queued by this context so far (for accounting). */
 long long ppm_launch_count(const ppm_ctx *ctx);
 
+/* Largest nz accepted by ppm_totals_noalloc (size of its fixed scratch). */
+#define PPM_NOALLOC_MAX_PLANES 8192
+
+/* Conserved totals of a state the caller keeps on the device, without any
+ * device allocation.  The paper has no counterpart: this entry point exists
+ * for callers that cannot let a library call cudaMalloc -- a code whose own
+ * pool allocator owns (and budgets in advance) all device memory, or a step
+ * loop that cannot take the device-wide synchronisation an allocation may
+ * cause.  It does not need a context.
+ *   q_dev[9]   device pointers to the FP64 full variables (rho, rho*u, rho*v,
+ *              rho*w, E, FV, m_x, m_y, m_z; the moments are not read), each
+ *              nx*ny*nz with x fastest; read only.
+ *   dx         cell size; the totals are multiplied by dx^3.
+ *   totals_dev device pointer to 7 doubles written with (M, Px, Py, Pz, E,
+ *              sum rho*FV, sum FV) * dx^3, the same quantities as the
+ *              totals of ppm_diagnostics; plane sums are added in z order, so
+ *              repeated calls give identical results.
+ *   stream     cudaStream_t to queue on (NULL: the legacy default stream);
+ *              returns without waiting for the device.
+ * Limits: nz <= PPM_NOALLOC_MAX_PLANES (else EINVAL with a message from
+ * ppm_last_error(NULL)).  Scratch: a fixed static device array of
+ * PPM_NOALLOC_MAX_PLANES x 8 doubles (512 KiB), held by every GPU that loads
+ * the library until the process exits; each call overwrites the rows it uses
+ * (nothing carries over from one call to the next, so nothing needs
+ * clearing), and calls that overlap on the GPU race on it.  The first call on
+ * each device looks up the array's device address (a one-time set-up); make
+ * that first call before any stream capture.  Errors: EINVAL (NULL pointers,
+ * extents, nz too large), ECUDA (lookup or launch failed). */
+int ppm_totals_noalloc(const double *const q_dev[9], int nx, int ny, int nz, double dx,
+                       double *totals_dev, void *stream);
+
 /* Last error message of this context (or of the last failed ppm_create when
  * ctx is NULL). */
 const char *ppm_last_error(const ppm_ctx *ctx);

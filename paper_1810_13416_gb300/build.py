@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libppm.so")
 BUILD = os.path.join(HERE, "_build")
-UNITS = ["sweep_f32", "sweep_f64", "ppm_api"]
+UNITS = ["sweep_f32", "sweep_f64", "ppm_api", "noalloc"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 _lock = threading.Lock()

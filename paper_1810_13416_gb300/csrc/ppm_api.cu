@@ -40,6 +40,11 @@ thread_local std::string g_create_error;
 
 }  // namespace
 
+namespace ppm {
+// Message for calls that have no context (read back by ppm_last_error(NULL)).
+void set_global_error(const char *msg) { g_create_error = msg; }
+}  // namespace ppm
+
 struct ppm_ctx {
     int n[3];
     long long ncell;
