@@ -203,7 +203,7 @@ struct Pencil {
     std::vector<R> rho, cs, c2, pfull;
     std::vector<R> W[NH];                       // rho', u, v, w, p'
     std::vector<R> af[NH];                      // interface values
-    std::vector<char> smooth[NH];
+    std::vector<R> wgt[NH];                     // constraint weight, 0 = smooth
     std::vector<R> flat;
     std::vector<R> PL[NH], PR[NH], PD[NH], P6[NH];
     std::vector<R> WL[NH], WR[NH];              // traced states left/right of face j+1/2
@@ -227,7 +227,7 @@ struct Pencil {
         for (int k = 0; k < NH; ++k) {
             for (auto *v : {&W[k], &af[k], &PL[k], &PR[k], &PD[k], &P6[k], &WL[k], &WR[k]})
                 v->assign(m, R(0.0));
-            smooth[k].assign(m, 1);
+            wgt[k].assign(m, R(0.0));
         }
     }
     static int at(int i) { return i + G; }
@@ -315,10 +315,13 @@ void interface_values(Pencil<R> &P) {
 }
 
 // Step a3: smoothness on the 5-cell stencil centred on the cell (Sec. 1).
-// Reading: third differences T against first/second differences S;
-// smooth iff T <= C_SMOOTH * S + EPS_SMOOTH * scale, where scale is the
-// cell's full density (for rho'), sound speed (velocities) or full pressure
-// (p'), so that round-off noise on flat data counts as smooth.
+// Reading: third differences T against first/second differences S.  The
+// judgment is made continuous so that it does not amplify round-off: the
+// constraint weight is w = 0 where T <= C_SMOOTH*S + EPS_SMOOTH*scale (smooth:
+// no constraint at all), rising linearly to w = 1 (full constraints) at
+// T >= S + 2*EPS_SMOOTH*scale; scale is the cell's full density (for rho'),
+// sound speed (velocities) or full pressure (p'), so that round-off noise on
+// flat data counts as smooth.
 template <class R>
 void smoothness(Pencil<R> &P) {
     for (int v = 0; v < NH; ++v)
@@ -333,12 +336,16 @@ void smoothness(Pencil<R> &P) {
             R d2m = d1m1 - d1m2, d20 = d10 - d1m1, d2p = d1p1 - d10;
             R T = Max(Abs(d20 - d2m), Abs(d2p - d20));
             R S = Max(Max(Abs(d1m1), Abs(d10)), Max(Max(Abs(d2m), Abs(d20)), Abs(d2p)));
-            P.smooth[v][k] = (T <= R(C_SMOOTH) * S + R(EPS_SMOOTH) * scale) ? 1 : 0;
+            R fl = R(EPS_SMOOTH) * scale;
+            R x = T - R(C_SMOOTH) * S - fl;
+            R w = R(0.0);
+            if (x > R(0.0)) w = Min(R(1.0), x / (R(1.0 - C_SMOOTH) * S + fl));
+            P.wgt[v][k] = w;
         }
     for (int i = 0; i < P.n; ++i) {
         const int k = Pencil<R>::at(i);
         bool any = false;
-        for (int v = 0; v < NH; ++v) any = any || !P.smooth[v][k];
+        for (int v = 0; v < NH; ++v) any = any || (val(P.wgt[v][k]) > 0.0);
         if (any) ++P.c_nonsmooth;
     }
 }
@@ -365,7 +372,8 @@ void flattening(Pencil<R> &P) {
 }
 
 // Step a4: parabolas; constraints only where the detector found the cell
-// non-smooth (Sec. 1), in the form of Colella & Woodward (1984).
+// non-smooth (Sec. 1), in the form of Colella & Woodward (1984), blended in
+// with the detector's weight w (w = 1: fully constrained edges).
 template <class R>
 void parabolas(Pencil<R> &P) {
     for (int v = 0; v < NH; ++v)
@@ -379,21 +387,24 @@ void parabolas(Pencil<R> &P) {
                 aL = aL + f * (a - aL);
                 aR = aR + f * (a - aR);
             }
-            if (!P.smooth[v][k]) {
-                aL = Clamp(aL, Min(A[k - 1], a), Max(A[k - 1], a));
-                aR = Clamp(aR, Min(a, A[k + 1]), Max(a, A[k + 1]));
-                if ((aR - a) * (a - aL) <= R(0.0)) {
-                    aL = a;
-                    aR = a;
+            const R w = P.wgt[v][k];
+            if (w > R(0.0)) {
+                R cL = Clamp(aL, Min(A[k - 1], a), Max(A[k - 1], a));
+                R cR = Clamp(aR, Min(a, A[k + 1]), Max(a, A[k + 1]));
+                if ((cR - a) * (a - cL) <= R(0.0)) {
+                    cL = a;
+                    cR = a;
                 } else {
-                    R da = aR - aL;
-                    R dm = a - R(0.5) * (aL + aR);
+                    R da = cR - cL;
+                    R dm = a - R(0.5) * (cL + cR);
                     R d6 = da * da * R(1.0 / 6.0);
                     if (da * dm > d6)
-                        aL = R(3.0) * a - R(2.0) * aR;
+                        cL = R(3.0) * a - R(2.0) * cR;
                     else if (-d6 > da * dm)
-                        aR = R(3.0) * a - R(2.0) * aL;
+                        cR = R(3.0) * a - R(2.0) * cL;
                 }
+                aL = aL + w * (cL - aL);
+                aR = aR + w * (cR - aR);
             }
             P.PL[v][k] = aL;
             P.PR[v][k] = aR;

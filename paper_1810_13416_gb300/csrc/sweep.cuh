@@ -154,39 +154,49 @@ __device__ __forceinline__ R iface(R a0, R a1, R a2, R a3) {
     return ((R)7 * (a1 + a2) - (a0 + a3)) * (R)(1.0 / 12.0);
 }
 
-// a3: smoothness on the 5-cell stencil (Sec. 1); see the reading in the oracle.
+// a3: smoothness on the 5-cell stencil (Sec. 1).  Returns the constraint
+// weight: 0 where T <= S/2 + 1e-9 scale (smooth: no constraint), rising
+// linearly to 1 at T >= S + 2e-9 scale, with T the largest third difference
+// and S the largest first or second difference of the stencil.
 template <typename R>
-__device__ __forceinline__ bool smooth5(R am2, R am1, R a0, R ap1, R ap2, R scale) {
+__device__ __forceinline__ R smooth5(R am2, R am1, R a0, R ap1, R ap2, R scale) {
     const R d1m2 = am1 - am2, d1m1 = a0 - am1, d10 = ap1 - a0, d1p1 = ap2 - ap1;
     const R d2m = d1m1 - d1m2, d20 = d10 - d1m1, d2p = d1p1 - d10;
     const R T = rmax(rabs(d20 - d2m), rabs(d2p - d20));
     const R S = rmax(rmax(rabs(d1m1), rabs(d10)), rmax(rmax(rabs(d2m), rabs(d20)), rabs(d2p)));
-    return T <= (R)0.5 * S + (R)1e-9 * scale;
+    const R fl = (R)1e-9 * scale;
+    const R x = T - (R)0.5 * S - fl;
+    R w = (R)0;
+    if (x > (R)0) w = rmin((R)1, x / ((R)0.5 * S + fl));
+    return w;
 }
 
-// a4: parabola of one variable; returns aL, aR, a6 (da = aR - aL).
+// a4: parabola of one variable; returns aL, aR, a6 (da = aR - aL).  The
+// Colella-Woodward constraints are blended in with the detector weight w.
 template <typename R>
-__device__ __forceinline__ void parabola(R am, R a, R ap, R aL, R aR, R f, bool smooth, R &oL, R &oR,
+__device__ __forceinline__ void parabola(R am, R a, R ap, R aL, R aR, R f, R w, R &oL, R &oR,
                                          R &o6) {
     if (f > (R)0) {
         aL = aL + f * (a - aL);
         aR = aR + f * (a - aR);
     }
-    if (!smooth) {
-        aL = rclamp(aL, rmin(am, a), rmax(am, a));
-        aR = rclamp(aR, rmin(a, ap), rmax(a, ap));
-        if ((aR - a) * (a - aL) <= (R)0) {
-            aL = a;
-            aR = a;
+    if (w > (R)0) {
+        R cL = rclamp(aL, rmin(am, a), rmax(am, a));
+        R cR = rclamp(aR, rmin(a, ap), rmax(a, ap));
+        if ((cR - a) * (a - cL) <= (R)0) {
+            cL = a;
+            cR = a;
         } else {
-            const R da = aR - aL;
-            const R dm = a - (R)0.5 * (aL + aR);
+            const R da = cR - cL;
+            const R dm = a - (R)0.5 * (cL + cR);
             const R d6 = da * da * (R)(1.0 / 6.0);
             if (da * dm > d6)
-                aL = (R)3 * a - (R)2 * aR;
+                cL = (R)3 * a - (R)2 * cR;
             else if (-d6 > da * dm)
-                aR = (R)3 * a - (R)2 * aL;
+                cR = (R)3 * a - (R)2 * cL;
         }
+        aL = aL + w * (cL - aL);
+        aR = aR + w * (cR - aR);
     }
     oL = aL;
     oR = aR;
@@ -270,8 +280,12 @@ __device__ __forceinline__ float fv_moment_bound(float s) {
 // The kernel.  PLAIN: FP64 storage of full rho and E (subtracting the base
 // state on load and adding it back on store); otherwise deviation storage.
 // ---------------------------------------------------------------------------
+#ifndef PPM_SWEEP_MINB
+#define PPM_SWEEP_MINB 1
+#endif
+
 template <typename R, bool PLAIN>
-__global__ void __launch_bounds__(128) sweep_kernel(const SweepArgs<R> A) {
+__global__ void __launch_bounds__(128, PPM_SWEEP_MINB) sweep_kernel(const SweepArgs<R> A) {
     constexpr bool F32 = std::is_same<R, float>::value;
     const int lane = blockIdx.x * blockDim.x + threadIdx.x;
     const int blk = blockIdx.y;
@@ -425,15 +439,15 @@ __global__ void __launch_bounds__(128) sweep_kernel(const SweepArgs<R> A) {
             // parabolas of the five variables
             R aL[5], aR[5], a6[5];
             {
-                const bool s0 = smooth5(wrd[0], wrd[1], wrd[2], wrd[3], wrd[4], rho2);
+                const R s0 = smooth5(wrd[0], wrd[1], wrd[2], wrd[3], wrd[4], rho2);
                 parabola(wrd[1], wrd[2], wrd[3], afp[0], afn[0], f, s0, aL[0], aR[0], a6[0]);
-                const bool s1 = smooth5(wu[0], wu[1], wu[2], wu[3], wu[4], cs);
+                const R s1 = smooth5(wu[0], wu[1], wu[2], wu[3], wu[4], cs);
                 parabola(wu[1], wu[2], wu[3], afp[1], afn[1], f, s1, aL[1], aR[1], a6[1]);
-                const bool s2 = smooth5(wv[0], wv[1], wv[2], wv[3], wv[4], cs);
+                const R s2 = smooth5(wv[0], wv[1], wv[2], wv[3], wv[4], cs);
                 parabola(wv[1], wv[2], wv[3], afp[2], afn[2], f, s2, aL[2], aR[2], a6[2]);
-                const bool s3 = smooth5(ww[0], ww[1], ww[2], ww[3], ww[4], cs);
+                const R s3 = smooth5(ww[0], ww[1], ww[2], ww[3], ww[4], cs);
                 parabola(ww[1], ww[2], ww[3], afp[3], afn[3], f, s3, aL[3], aR[3], a6[3]);
-                const bool s4 = smooth5(wpd[0], wpd[1], wpd[2], wpd[3], wpd[4], p2);
+                const R s4 = smooth5(wpd[0], wpd[1], wpd[2], wpd[3], wpd[4], p2);
                 parabola(wpd[1], wpd[2], wpd[3], afp[4], afn[4], f, s4, aL[4], aR[4], a6[4]);
             }
             // characteristic tracing (waves u-c, u, u+c) + buoyancy

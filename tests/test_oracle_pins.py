@@ -394,3 +394,25 @@ def test_flop_census_is_plausible():
     o = oracle.Oracle(p)
     fl, sel = o.count_flops(q, 0, o.cfl_dt(q))
     assert 200 < fl < 3000 and sel > 0
+
+
+def test_roundoff_sized_perturbations_stay_small():
+    """A 1e-7 relative perturbation of the inputs (the size of FP32 storage
+    rounding) must not be amplified by switching constraints on and off: the
+    smoothness judgment is continuous, so after 20 double steps of the
+    periodic box the momentum moves by less than 1e-5 of its maximum and FV
+    by less than 1e-7 on average."""
+    p = workloads.periodic_box(32)
+    q = workloads.build(p)
+    rng = np.random.default_rng(0)
+    qa = [a.copy() for a in q]
+    qb = [a * (1 + 1e-7 * rng.standard_normal(a.shape)) for a in q]
+    qb[5] = np.clip(qb[5], 0.0, 1.0)
+    o = oracle.Oracle(p)
+    for _ in range(20):
+        dt = o.cfl_dt(qa)
+        o.double_step(qa, dt)
+        o.double_step(qb, dt)
+    for d in range(3):
+        assert np.abs(qa[1 + d] - qb[1 + d]).max() <= 1e-5 * np.abs(qa[1 + d]).max()
+    assert np.abs(qa[5] - qb[5]).mean() <= 1e-7
