@@ -18,6 +18,8 @@ BUILD = os.path.join(HERE, "_build")
 UNITS = ["sweep_f32", "sweep_f64", "ppm_api", "noalloc"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE]
+# per-unit flags: the FP32 pass uses approximate division and square root
+UNIT_FLAGS = {"sweep_f32": ["-prec-div=false", "-prec-sqrt=false"]}
 _lock = threading.Lock()
 
 
@@ -52,7 +54,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
         procs = []
         for u in UNITS:
             obj = os.path.join(BUILD, u + ".o")
-            cmd = [nvcc, *ARCH, *FLAGS, *extra, "-Xptxas", "-v", "-c", os.path.join(CSRC, u + ".cu"), "-o", obj]
+            cmd = [nvcc, *ARCH, *FLAGS, *UNIT_FLAGS.get(u, []), *extra, "-Xptxas", "-v", "-c",
+                   os.path.join(CSRC, u + ".cu"), "-o", obj]
             procs.append((u, cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
         logs = []
         for u, cmd, p in procs:

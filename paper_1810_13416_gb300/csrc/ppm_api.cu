@@ -16,6 +16,8 @@
 namespace ppm {
 void launch_sweep_f32(const SweepArgs<float> &a, dim3 grid, dim3 block, cudaStream_t st);
 void launch_sweep_f64(const SweepArgs<double> &a, dim3 grid, dim3 block, cudaStream_t st);
+cudaError_t prepare_sweep_f32();
+cudaError_t prepare_sweep_f64();
 }  // namespace ppm
 
 using namespace ppm;
@@ -63,6 +65,9 @@ struct ppm_ctx {
     void *state;               // 9 * ncell values (float or double)
     double *t64;               // FP64 tables: rho0, p0, g, heat, damp (5 * ntab)
     float *t32;                // FP32 copies
+    float4 *t4;                // FP32 AoS tables for the passes: base[ntab4], sources[ntab4]
+    int ntab4;
+    float s4_0, inv_ds4;
     DevScal *ds_dev;
     double *h_pinned;          // 8 doubles of pinned host scratch
     double *stage;             // FP64 staging for host regions
@@ -131,6 +136,12 @@ SweepArgs<R> make_args(ppm_ctx *c, int axis) {
     a.t_heat = c->has_heat ? t + 3 * c->ntab : nullptr;
     a.t_damp = c->has_damp ? t + 4 * c->ntab : nullptr;
     a.ntab = c->ntab;
+    a.t4_base = c->t4;
+    a.t4_src = c->t4 + c->ntab4;
+    a.ntab4 = c->ntab4;
+    a.s4_0 = c->s4_0;
+    a.inv_ds4 = c->inv_ds4;
+    a.vec_x = (std::is_same<R, float>::value && axis == 0 && (c->n[0] % 4) == 0) ? 1 : 0;
     a.rho0_c = (R)c->rho0c;
     a.p0_c = (R)c->p0c;
     a.s0 = c->s0;
@@ -212,9 +223,9 @@ __global__ void set_region_kernel(SweepArgs<double> A64, R *st, long long ncell,
             for (int q = 0; q < 5; ++q) st[q * ncell + cidx] = (R)v[q];
             st[5 * ncell + cidx] = (R)s;
             for (int q = 6; q < 9; ++q) st[q * ncell + cidx] = (R)fminf(fmaxf((float)v[q], -bnd), bnd);
-            continue;
+        } else {
+            for (int q = 0; q < NVAR; ++q) st[q * ncell + cidx] = (R)v[q];
         }
-        for (int q = 0; q < NVAR; ++q) st[q * ncell + cidx] = (R)v[q];
     }
 }
 
@@ -436,6 +447,7 @@ void release(ppm_ctx *c) {
     if (c->state) cudaFree(c->state);
     if (c->t64) cudaFree(c->t64);
     if (c->t32) cudaFree(c->t32);
+    if (c->t4) cudaFree(c->t4);
     if (c->ds_dev) cudaFree(c->ds_dev);
     if (c->stage) cudaFree(c->stage);
     if (c->diag_acc) cudaFree(c->diag_acc);
@@ -527,9 +539,50 @@ int ppm_create(ppm_ctx **out, int nx, int ny, int nz, double gamma, const int bc
         h64[4 * nt + i] = opt->damp ? opt->damp[i] : 0.0;
     }
     for (size_t i = 0; i < h64.size(); ++i) h32[i] = (float)h64[i];
+    // FP32 pass tables, one float4 per point: {rho0, p0, g, 0} and {heat, damp, 0, 0}
+    // on the z grid (plane-parallel) or on a uniform grid in r^2 (central; g/r
+    // stored, so a pass needs neither a square root nor a division)
+    std::vector<float4> h4;
+    {
+        auto lerp = [&](const double *t, double s) {
+            const double u = (s - grav->s0) / grav->ds;
+            const double fl = std::min(std::max(std::floor(u), 0.0), (double)(nt - 2));
+            const int i = (int)fl;
+            const double w = u - fl;
+            return t[i] + w * (t[i + 1] - t[i]);
+        };
+        const double *heat = opt->heat, *damp = opt->damp;
+        if (grav->kind == PPM_GRAV_CENTRAL) {
+            const int n4 = 16384;
+            const double r_end = grav->s0 + (nt - 1) * grav->ds;
+            const double ds4 = r_end * r_end / (n4 - 1);
+            c->ntab4 = n4;
+            c->s4_0 = 0.0f;
+            c->inv_ds4 = (float)(1.0 / ds4);
+            h4.resize(2 * (size_t)n4);
+            for (int j = 0; j < n4; ++j) {
+                const double r = std::sqrt(j * ds4);
+                const double rr = (j == 0) ? std::sqrt(ds4) : r;
+                h4[j] = make_float4((float)lerp(grav->rho0, r), (float)lerp(grav->p0, r),
+                                    (float)(lerp(grav->g, rr) / rr), 0.0f);
+                h4[n4 + j] = make_float4(heat ? (float)lerp(heat, r) : 0.0f, damp ? (float)lerp(damp, r) : 0.0f,
+                                         0.0f, 0.0f);
+            }
+        } else {
+            c->ntab4 = nt;
+            c->s4_0 = (float)grav->s0;
+            c->inv_ds4 = (float)(1.0 / grav->ds);
+            h4.resize(2 * (size_t)nt);
+            for (int j = 0; j < nt; ++j) {
+                h4[j] = make_float4((float)grav->rho0[j], (float)grav->p0[j], (float)grav->g[j], 0.0f);
+                h4[nt + j] = make_float4(heat ? (float)heat[j] : 0.0f, damp ? (float)damp[j] : 0.0f, 0.0f, 0.0f);
+            }
+        }
+    }
     // stage: up to 2^24 cells per variable (9 x 128 MiB), or the whole grid if smaller
     c->stage_cells = std::min<long long>(c->ncell, 1LL << 24);
     if (cudaMalloc(&c->t64, h64.size() * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->t4, h4.size() * sizeof(float4)) != cudaSuccess ||
         cudaMalloc(&c->t32, h32.size() * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&c->ds_dev, sizeof(DevScal)) != cudaSuccess ||
         cudaMalloc(&c->stage, (size_t)NVAR * c->stage_cells * sizeof(double)) != cudaSuccess ||
@@ -541,6 +594,8 @@ int ppm_create(ppm_ctx **out, int nx, int ny, int nz, double gamma, const int bc
     }
     if (cudaMemcpy(c->t64, h64.data(), h64.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(c->t32, h32.data(), h32.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->t4, h4.data(), h4.size() * sizeof(float4), cudaMemcpyHostToDevice) != cudaSuccess ||
+        prepare_sweep_f32() != cudaSuccess || prepare_sweep_f64() != cudaSuccess ||
         cudaMemset(c->ds_dev, 0, sizeof(DevScal)) != cudaSuccess ||
         cudaMemset(c->state, 0, sbytes) != cudaSuccess) {
         fail(c, PPM_ECUDA, "initialising device buffers failed");

@@ -63,6 +63,12 @@ struct SweepArgs {
     int ntab;
     double s0, ds;
     R rho0_c, p0_c;       // uniform base (grav == 0)
+    // FP32 form: AoS tables {rho0, p0, g (plane) or g/r (central), 0} and
+    // {heat, damp, 0, 0} on s_j = s4_0 + j*ds4, s = z (plane) or r^2 (central)
+    const float4 *t4_base, *t4_src;
+    int ntab4;
+    float s4_0, inv_ds4;
+    int vec_x;            // x pass with 16-byte copies (n % 4 == 0)
     double gamma;
     const double *dt;     // device time step
     int sources;          // apply heating/damping after the pass
@@ -248,6 +254,33 @@ __device__ __forceinline__ int map_face(int j, int n, int bl, int bh) {
     return P;
 }
 
+// ---------------------------------------------------------------------------
+// Asynchronous global -> shared copies (each thread copies and later reads
+// only its own data, so a per-thread wait is enough: no block barrier).
+// ---------------------------------------------------------------------------
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// FP32 table lookup: one index for all four columns.
+__device__ __forceinline__ float4 tab4(const float4 *__restrict__ t, int ntab, float s0, float inv_ds, float s) {
+    const float u = (s - s0) * inv_ds;
+    const float fl = fminf(fmaxf(floorf(u), 0.0f), (float)(ntab - 2));
+    const int i = (int)fl;
+    const float w = u - fl;
+    const float4 a = __ldg(t + i), b = __ldg(t + i + 1);
+    return make_float4(fmaf(w, b.x - a.x, a.x), fmaf(w, b.y - a.y, a.y), fmaf(w, b.z - a.z, a.z),
+                       fmaf(w, b.w - a.w, a.w));
+}
+
 __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
 
 // FP32 storage of FV is folded: s = FV for FV <= 1/2 and s = FV - 1 (<= -0.0)
@@ -284,9 +317,30 @@ __device__ __forceinline__ float fv_moment_bound(float s) {
 #define PPM_SWEEP_MINB 1
 #endif
 
-template <typename R, bool PLAIN>
-__global__ void __launch_bounds__(128, PPM_SWEEP_MINB) sweep_kernel(const SweepArgs<R> A) {
+constexpr int SWEEP_NB = 128;   // threads per block
+constexpr int RING = 8;         // scalar prefetch ring slots per thread
+constexpr int PREF = 4;         // scalar prefetch distance (cells)
+
+// Dynamic shared memory of one block of the pass.
+template <typename R, bool VEC>
+constexpr int sweep_smem_bytes() {
+    return VEC ? (4 * 9 * SWEEP_NB * 16 + 2 * 9 * SWEEP_NB * 16) : (RING * 9 * SWEEP_NB * (int)sizeof(R));
+}
+
+// ---------------------------------------------------------------------------
+// The kernel.  PLAIN: FP64 storage of full rho and E (subtracting the base
+// state on load and adding it back on store); otherwise deviation storage.
+// VEC (FP32 x pass, n % 4 == 0): each thread copies 4 consecutive cells of
+// its row per variable with one 16-byte asynchronous copy, and writes its
+// results back 4 cells at a time, instead of 9 scalar accesses per cell that
+// touch 32 different cache lines per warp.
+// ---------------------------------------------------------------------------
+template <typename R, bool PLAIN, bool VEC>
+__global__ void __launch_bounds__(SWEEP_NB, PPM_SWEEP_MINB) sweep_kernel(const SweepArgs<R> A) {
     constexpr bool F32 = std::is_same<R, float>::value;
+    static_assert(!VEC || F32, "vector path is FP32 only");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int tid = threadIdx.x;
     const int lane = blockIdx.x * blockDim.x + threadIdx.x;
     const int blk = blockIdx.y;
     // threads past the edge take part in the final warp reduction only
@@ -316,8 +370,62 @@ __global__ void __launch_bounds__(128, PPM_SWEEP_MINB) sweep_kernel(const SweepA
     xyz[t2d] = coord(A, t2d, ijk[t2d]);
     const R lo = (R)A.org[ax];
 
+    // FP32 base state: squared transverse radius, and the base state of a
+    // pencil on which it does not vary (plane-parallel gravity, x/y pass)
+    const float rt2 = F32 ? (float)(xyz[t1d] * xyz[t1d] + xyz[t2d] * xyz[t2d]) : 0.0f;
+    float4 bconst = make_float4(0.f, 0.f, 0.f, 0.f);
+    if constexpr (F32) {
+        if (A.grav == 0) bconst = make_float4((float)A.rho0_c, (float)A.p0_c, 0.f, 0.f);
+        else if (A.grav == 1 && ax != 2) {
+            bconst = tab4(A.t4_base, A.ntab4, A.s4_0, A.inv_ds4, (float)xyz[2]);
+            bconst.z = 0.0f;  // vertical gravity has no component along x or y
+        }
+    }
+    // base (rho0, p0, g along +s) at coordinate xa along the pass (FP32)
+    auto base32 = [&](float xa) -> float4 {
+        if (A.grav == 0 || (A.grav == 1 && ax != 2)) return bconst;
+        if (A.grav == 1) return tab4(A.t4_base, A.ntab4, A.s4_0, A.inv_ds4, xa);
+        float4 t = tab4(A.t4_base, A.ntab4, A.s4_0, A.inv_ds4, fmaf(xa, xa, rt2));
+        t.z *= xa;  // (g/r) * x_axis
+        return t;
+    };
+
     // per-thread stash of the 4 cells that serve as high-side ghosts
     R stash[4][9];
+
+    // prefetch rings (shared memory, private to each thread)
+    R *ring = reinterpret_cast<R *>(smem_raw);
+    float *ringv = reinterpret_cast<float *>(smem_raw);
+    float *outv = reinterpret_cast<float *>(smem_raw) + 4 * 9 * SWEEP_NB * 4;
+    auto fetch = [&](int cf) {
+        if (cf < n) {
+            bool fl;
+            const int mm = map_cell(cf, n, A.bc_lo, A.bc_hi, fl);
+            const R *src = q + (long long)mm * sa;
+            R *dst = ring + ((cf + G) & (RING - 1)) * 9 * SWEEP_NB + tid;
+#pragma unroll
+            for (int v = 0; v < 9; ++v) cp_async<(int)sizeof(R)>(dst + v * SWEEP_NB, src + v * vs);
+        }
+        cp_commit();
+    };
+    auto fetchg = [&](int g) {  // group of cells 4g-G .. 4g-G+3 (x pass, FP32)
+        const int c0 = 4 * g - G;
+        if (c0 < n) {
+            const int m0 = (c0 < 0) ? ((A.bc_lo == 0) ? n - 4 : 0) : c0;
+            const float *src = reinterpret_cast<const float *>(q) + m0;
+            float *dst = ringv + (((g & 3) * 9) * SWEEP_NB + tid) * 4;
+#pragma unroll
+            for (int v = 0; v < 9; ++v) cp_async<16>(dst + v * SWEEP_NB * 4, src + v * vs);
+        }
+        cp_commit();
+    };
+    if constexpr (VEC) {
+        fetchg(0);
+        fetchg(1);
+    } else {
+#pragma unroll
+        for (int k = 0; k < PREF; ++k) fetch(-G + k);
+    }
 
     // ---- windows: slot s holds cell c-4+s --------------------------------
     R wrd[5], wu[5], wv[5], ww[5], wpd[5];     // primitives for interpolation
@@ -351,19 +459,34 @@ __global__ void __launch_bounds__(128, PPM_SWEEP_MINB) sweep_kernel(const SweepA
 
     for (int c = -G; c < n + G; ++c) {
         // ================= a1: load cell c ==================================
+        if constexpr (VEC) {
+            if (((c + G) & 3) == 0) {
+                fetchg(((c + G) >> 2) + 2);
+                cp_wait<2>();
+            }
+        } else {
+            fetch(c + PREF);
+            cp_wait<PREF>();
+        }
         R raw[9];
         bool flip = false;
-        int m;
+        const int m = map_cell(c, n, A.bc_lo, A.bc_hi, flip);
         if (c >= n) {
-            m = map_cell(c, n, A.bc_lo, A.bc_hi, flip);
             const int si = (A.bc_hi == 0) ? (c - n) : (n + 3 - c);
 #pragma unroll
             for (int v = 0; v < 9; ++v) raw[v] = stash[si][v];
         } else {
-            m = map_cell(c, n, A.bc_lo, A.bc_hi, flip);
-            const R *p = q + (long long)m * sa;
+            if constexpr (VEC) {
+                const int sub = (c + G) & 3;
+                const int idx = (c < 0 && A.bc_lo == 1) ? 3 - sub : sub;
+                const float *src = ringv + ((((c + G) >> 2) & 3) * 9 * SWEEP_NB + tid) * 4 + idx;
 #pragma unroll
-            for (int v = 0; v < 9; ++v) raw[v] = p[v * vs];
+                for (int v = 0; v < 9; ++v) raw[v] = src[v * SWEEP_NB * 4];
+            } else {
+                const R *src = ring + ((c + G) & (RING - 1)) * 9 * SWEEP_NB + tid;
+#pragma unroll
+                for (int v = 0; v < 9; ++v) raw[v] = src[v * SWEEP_NB];
+            }
             if (c >= 0) {
                 const int si = (A.bc_hi == 0) ? c : (c - (n - 4));
                 if (si >= 0 && si < 4) {
@@ -372,17 +495,28 @@ __global__ void __launch_bounds__(128, PPM_SWEEP_MINB) sweep_kernel(const SweepA
                 }
             }
         }
-        R cx[3] = {xyz[0], xyz[1], xyz[2]};
-        cx[ax] = coord(A, ax, m);
-        const Base<R> b = base_at(A, cx);
+        R b_rho0, b_p0, b_g;
+        if constexpr (F32) {
+            const float4 bb = base32(coord(A, ax, m));
+            b_rho0 = bb.x;
+            b_p0 = bb.y;
+            b_g = bb.z;
+        } else {
+            R cx[3] = {xyz[0], xyz[1], xyz[2]};
+            cx[ax] = coord(A, ax, m);
+            const Base<R> b = base_at(A, cx);
+            b_rho0 = b.rho0;
+            b_p0 = b.p0;
+            b_g = b.g[ax];
+        }
         const R sg = flip ? (R)-1 : (R)1;
         // rotate into the pass frame and subtract the base state
-        const R rd = PLAIN ? xsub(raw[0], b.rho0) : raw[0];
+        const R rd = PLAIN ? xsub(raw[0], b_rho0) : raw[0];
         const R mn = sg * raw[1 + ax];
         const R m1 = raw[1 + t1d];
         const R m2 = raw[1 + t2d];
-        const R ed = PLAIN ? xsub(raw[4], xdiv(b.p0, gm1)) : raw[4];
-        const R rho = b.rho0 + rd;
+        const R ed = PLAIN ? xsub(raw[4], xdiv(b_p0, gm1)) : raw[4];
+        const R rho = b_rho0 + rd;
         const R rinv = (R)1 / rho;
         const R u = mn * rinv, v = m1 * rinv, w = m2 * rinv;
         const R ke = (R)0.5 * (mn * u + (m1 * v + m2 * w));
@@ -406,8 +540,8 @@ __global__ void __launch_bounds__(128, PPM_SWEEP_MINB) sweep_kernel(const SweepA
         won[4] = sg * raw[6 + ax];
         wo1[4] = raw[6 + t1d];
         wo2[4] = raw[6 + t2d];
-        wro[4] = rho; wp0[4] = b.p0; wr0[4] = b.rho0;
-        wg[4] = sg * b.g[ax];
+        wro[4] = rho; wp0[4] = b_p0; wr0[4] = b_rho0;
+        wg[4] = sg * b_g;
         wmn[4] = mn; wm1[4] = m1; wm2[4] = m2; wed[4] = ed;
 
         // ================= a2: interface values of face (c-2)+1/2 ==========
@@ -515,10 +649,19 @@ __global__ void __launch_bounds__(128, PPM_SWEEP_MINB) sweep_kernel(const SweepA
         R Frc, Frlc, Fnc, Ft1c, Ft2c, FEc, FElc, usc;
         {
             const int j = c - 3;
-            R fx[3] = {xyz[0], xyz[1], xyz[2]};
-            fx[ax] = xadd(lo, xmul((R)map_face(j, n, A.bc_lo, A.bc_hi), (R)A.dx));
-            const Base<R> bf = base_at(A, fx);
-            const R r0 = bf.rho0, p0 = bf.p0;
+            R r0, p0;
+            const R xf = xadd(lo, xmul((R)map_face(j, n, A.bc_lo, A.bc_hi), (R)A.dx));
+            if constexpr (F32) {
+                const float4 bf = base32(xf);
+                r0 = bf.x;
+                p0 = bf.y;
+            } else {
+                R fx[3] = {xyz[0], xyz[1], xyz[2]};
+                fx[ax] = xf;
+                const Base<R> bf = base_at(A, fx);
+                r0 = bf.rho0;
+                p0 = bf.p0;
+            }
             const R rdL = WLp[0], uL = WLp[1], pdL = WLp[4];
             const R rdR = WRc[0], uR = WRc[1], pdR = WRc[4];
             const R rL = r0 + rdL, pL = p0 + pdL;
@@ -734,12 +877,21 @@ __global__ void __launch_bounds__(128, PPM_SWEEP_MINB) sweep_kernel(const SweepA
             R cxo[3] = {xyz[0], xyz[1], xyz[2]};
             cxo[ax] = coord(A, ax, i);
             if (A.sources) {
-                const R s = (A.grav == 1) ? cxo[2]
-                                          : xsqrt(xadd(xadd(xmul(cxo[0], cxo[0]), xmul(cxo[1], cxo[1])),
-                                                       xmul(cxo[2], cxo[2])));
-                if (A.t_heat) edo = edo + dt * lerp_tab(A, A.t_heat, s);
+                R heat = 0, kd = 0;
+                if constexpr (F32) {
+                    const float s = (A.grav == 1) ? (float)cxo[2] : fmaf((float)cxo[ax], (float)cxo[ax], rt2);
+                    const float4 hs = tab4(A.t4_src, A.ntab4, A.s4_0, A.inv_ds4, s);
+                    heat = hs.x;
+                    kd = hs.y;
+                } else {
+                    const R s = (A.grav == 1) ? cxo[2]
+                                              : xsqrt(xadd(xadd(xmul(cxo[0], cxo[0]), xmul(cxo[1], cxo[1])),
+                                                           xmul(cxo[2], cxo[2])));
+                    if (A.t_heat) heat = lerp_tab(A, A.t_heat, s);
+                    if (A.t_damp) kd = lerp_tab(A, A.t_damp, s);
+                }
+                if (A.t_heat) edo = edo + dt * heat;
                 if (A.t_damp) {
-                    const R kd = lerp_tab(A, A.t_damp, s);
                     const R fd = rmax((R)0, (R)1 - dt * kd);
                     const R kin = (R)0.5 * (mno * mno + (m1o * m1o + m2o * m2o)) / rnew;
                     mno = mno * fd;
@@ -760,16 +912,33 @@ __global__ void __launch_bounds__(128, PPM_SWEEP_MINB) sweep_kernel(const SweepA
                     smax_local = rmax(smax_local, spd);
                 }
             }
-            R *p = q + (long long)i * sa;
-            p[0] = PLAIN ? xadd(wr0[0], rdo) : rdo;
-            p[(1 + ax) * vs] = mno;
-            p[(1 + t1d) * vs] = m1o;
-            p[(1 + t2d) * vs] = m2o;
-            p[4 * vs] = PLAIN ? xadd(xdiv(wp0[0], gm1), edo) : edo;
-            p[5 * vs] = fvs;
-            p[(6 + ax) * vs] = onn;
-            p[(6 + t1d) * vs] = o1;
-            p[(6 + t2d) * vs] = o2;
+            R outc[9];
+            outc[0] = PLAIN ? xadd(wr0[0], rdo) : rdo;
+            outc[1 + ax] = mno;
+            outc[1 + t1d] = m1o;
+            outc[1 + t2d] = m2o;
+            outc[4] = PLAIN ? xadd(xdiv(wp0[0], gm1), edo) : edo;
+            outc[5] = fvs;
+            outc[6 + ax] = onn;
+            outc[6 + t1d] = o1;
+            outc[6 + t2d] = o2;
+            if constexpr (VEC) {
+                // stage 4 cells, then one 16-byte store per variable
+                float *st = outv + ((((i >> 2) & 1) * 9) * SWEEP_NB + tid) * 4 + (i & 3);
+#pragma unroll
+                for (int vv = 0; vv < 9; ++vv) st[vv * SWEEP_NB * 4] = outc[vv];
+                if ((i & 3) == 3) {
+                    const float4 *sv = reinterpret_cast<const float4 *>(outv) + (((i >> 2) & 1) * 9) * SWEEP_NB + tid;
+                    float *g = reinterpret_cast<float *>(q) + (i - 3);
+#pragma unroll
+                    for (int vv = 0; vv < 9; ++vv)
+                        *reinterpret_cast<float4 *>(g + vv * vs) = sv[vv * SWEEP_NB];
+                }
+            } else {
+                R *p = q + (long long)i * sa;
+#pragma unroll
+                for (int vv = 0; vv < 9; ++vv) p[vv * vs] = outc[vv];
+            }
         }
 
         // ================= carry to the next step ===========================

@@ -2,7 +2,12 @@
 #include "sweep.cuh"
 
 namespace ppm {
+cudaError_t prepare_sweep_f64() {
+    return cudaFuncSetAttribute(sweep_kernel<double, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                sweep_smem_bytes<double, false>());
+}
+
 void launch_sweep_f64(const SweepArgs<double> &a, dim3 grid, dim3 block, cudaStream_t st) {
-    sweep_kernel<double, true><<<grid, block, 0, st>>>(a);
+    sweep_kernel<double, true, false><<<grid, block, sweep_smem_bytes<double, false>(), st>>>(a);
 }
 }  // namespace ppm
