@@ -25,7 +25,7 @@ using namespace ppm;
 namespace {
 
 constexpr int NVAR = 9;
-constexpr int SWEEP_BLOCK = 128;
+constexpr int SWEEP_BLOCK = ppm::SWEEP_NB;
 constexpr int MAX_BINS = 1024;
 
 // Device scalars shared by the kernels of one context.
@@ -141,7 +141,7 @@ SweepArgs<R> make_args(ppm_ctx *c, int axis) {
     a.ntab4 = c->ntab4;
     a.s4_0 = c->s4_0;
     a.inv_ds4 = c->inv_ds4;
-    a.vec_x = (std::is_same<R, float>::value && axis == 0 && (c->n[0] % 4) == 0) ? 1 : 0;
+    a.vec_x = (std::is_same<R, float>::value && axis == 0 && (c->n[0] % 8) == 0) ? 1 : 0;
     a.rho0_c = (R)c->rho0c;
     a.p0_c = (R)c->p0c;
     a.s0 = c->s0;

@@ -317,23 +317,31 @@ __device__ __forceinline__ float fv_moment_bound(float s) {
 #define PPM_SWEEP_MINB 1
 #endif
 
-constexpr int SWEEP_NB = 128;   // threads per block
+#ifndef PPM_SWEEP_NB
+#define PPM_SWEEP_NB 128
+#endif
+constexpr int SWEEP_NB = PPM_SWEEP_NB;   // threads per block
 constexpr int RING = 8;         // scalar prefetch ring slots per thread
 constexpr int PREF = 4;         // scalar prefetch distance (cells)
 
 // Dynamic shared memory of one block of the pass.
 template <typename R, bool VEC>
 constexpr int sweep_smem_bytes() {
-    return VEC ? (4 * 9 * SWEEP_NB * 16 + 2 * 9 * SWEEP_NB * 16) : (RING * 9 * SWEEP_NB * (int)sizeof(R));
+    return VEC ? (4 * 9 * SWEEP_NB * 16 + 9 * SWEEP_NB * 32) : (RING * 9 * SWEEP_NB * (int)sizeof(R));
 }
+
+#ifndef PPM_SWEEP_UNROLL
+#define PPM_SWEEP_UNROLL 1
+#endif
+constexpr int SWEEP_UNROLL = PPM_SWEEP_UNROLL;  // unroll factor of the march loop
 
 // ---------------------------------------------------------------------------
 // The kernel.  PLAIN: FP64 storage of full rho and E (subtracting the base
 // state on load and adding it back on store); otherwise deviation storage.
-// VEC (FP32 x pass, n % 4 == 0): each thread copies 4 consecutive cells of
+// VEC (FP32 x pass, n % 8 == 0): each thread copies 4 consecutive cells of
 // its row per variable with one 16-byte asynchronous copy, and writes its
-// results back 4 cells at a time, instead of 9 scalar accesses per cell that
-// touch 32 different cache lines per warp.
+// results back 8 cells (one whole 32-byte sector) at a time, instead of 9
+// scalar accesses per cell that touch 32 different cache lines per warp.
 // ---------------------------------------------------------------------------
 template <typename R, bool PLAIN, bool VEC>
 __global__ void __launch_bounds__(SWEEP_NB, PPM_SWEEP_MINB) sweep_kernel(const SweepArgs<R> A) {
@@ -381,17 +389,56 @@ __global__ void __launch_bounds__(SWEEP_NB, PPM_SWEEP_MINB) sweep_kernel(const S
             bconst.z = 0.0f;  // vertical gravity has no component along x or y
         }
     }
-    // base (rho0, p0, g along +s) at coordinate xa along the pass (FP32)
-    auto base32 = [&](float xa) -> float4 {
-        if (A.grav == 0 || (A.grav == 1 && ax != 2)) return bconst;
-        if (A.grav == 1) return tab4(A.t4_base, A.ntab4, A.s4_0, A.inv_ds4, xa);
-        float4 t = tab4(A.t4_base, A.ntab4, A.s4_0, A.inv_ds4, fmaf(xa, xa, rt2));
-        t.z *= xa;  // (g/r) * x_axis
+    // FP32 base state (rho0, p0, g along the pass) at coordinate xa along the
+    // pass.  Where it varies along the pencil the two table rows are fetched
+    // one step before they are needed (issue / finish), so the table load
+    // latency is off the step's dependency chain.
+    const float orgf = (float)A.org[ax], dxf = (float)A.dx;
+    const bool bvar = F32 && (A.grav == 2 || (A.grav == 1 && ax == 2));
+    struct TabFetch {
+        float4 a, b;
+        float w, xa;
+    };
+    auto tab_issue = [&](float xa) -> TabFetch {
+        TabFetch t;
+        t.xa = xa;
+        if (!bvar) {
+            t.a = t.b = bconst;
+            t.w = 0.0f;
+            return t;
+        }
+        const float sv = (A.grav == 1) ? xa : fmaf(xa, xa, rt2);
+        const float u = (sv - A.s4_0) * A.inv_ds4;
+        const float fl = fminf(fmaxf(floorf(u), 0.0f), (float)(A.ntab4 - 2));
+        const int i = (int)fl;
+        t.a = __ldg(A.t4_base + i);
+        t.b = __ldg(A.t4_base + i + 1);
+        t.w = u - fl;
         return t;
     };
+    auto tab_finish = [&](const TabFetch &t) -> float4 {
+        if (!bvar) return bconst;
+        float4 r = make_float4(fmaf(t.w, t.b.x - t.a.x, t.a.x), fmaf(t.w, t.b.y - t.a.y, t.a.y),
+                               fmaf(t.w, t.b.z - t.a.z, t.a.z), 0.0f);
+        if (A.grav == 2) r.z *= t.xa;  // (g/r) * x_axis
+        return r;
+    };
+    auto xcell32 = [&](int mm) { return orgf + ((float)mm + 0.5f) * dxf; };
+    auto xface32 = [&](int j) { return orgf + (float)map_face(j, n, A.bc_lo, A.bc_hi) * dxf; };
+    TabFetch cell_next, face_next;
+    if constexpr (F32) {
+        bool fl0;
+        cell_next = tab_issue(xcell32(map_cell(-G, n, A.bc_lo, A.bc_hi, fl0)));
+        face_next = tab_issue(xface32(-G - 3));
+    }
 
     // per-thread stash of the 4 cells that serve as high-side ghosts
     R stash[4][9];
+#pragma unroll
+    for (int a_ = 0; a_ < 4; ++a_)
+#pragma unroll
+        for (int b_ = 0; b_ < 9; ++b_) stash[a_][b_] = (R)0;
+    auto stash_index = [&](int cc) { return (A.bc_hi == 0) ? (cc - n) : (n + 3 - cc); };
 
     // prefetch rings (shared memory, private to each thread)
     R *ring = reinterpret_cast<R *>(smem_raw);
@@ -419,6 +466,17 @@ __global__ void __launch_bounds__(SWEEP_NB, PPM_SWEEP_MINB) sweep_kernel(const S
         }
         cp_commit();
     };
+    // raw stored value of variable v of cell cc (still in the ring or stash)
+    auto raw_at = [&](int cc, int v) -> R {
+        if (cc >= n) return stash[stash_index(cc)][v];
+        if constexpr (VEC) {
+            const int sub = (cc + G) & 3;
+            const int idx = (cc < 0 && A.bc_lo == 1) ? 3 - sub : sub;
+            return ringv[((((cc + G) >> 2) & 3) * 9 * SWEEP_NB + tid) * 4 + idx + v * SWEEP_NB * 4];
+        } else {
+            return ring[((cc + G) & (RING - 1)) * 9 * SWEEP_NB + tid + v * SWEEP_NB];
+        }
+    };
     if constexpr (VEC) {
         fetchg(0);
         fetchg(1);
@@ -433,14 +491,13 @@ __global__ void __launch_bounds__(SWEEP_NB, PPM_SWEEP_MINB) sweep_kernel(const S
     R wro[5];                                  // full old density
     R wp0[5], wr0[5];                          // base state at the cell
     R wg[5];                                   // gravity along the pass
-    R wmn[5], wm1[5], wm2[5], wed[5];          // conserved momenta and E'
     R wfs[5];                                  // stored (FP32: folded) FV
 #pragma unroll
     for (int s = 0; s < 5; ++s) {
         wrd[s] = wu[s] = wv[s] = ww[s] = wpd[s] = (R)0;
         wfv[s] = won[s] = wo1[s] = wo2[s] = (R)0;
         wro[s] = wr0[s] = wp0[s] = (R)1;
-        wg[s] = wmn[s] = wm1[s] = wm2[s] = wed[s] = wfs[s] = (R)0;
+        wg[s] = wfs[s] = (R)0;
     }
     // interface values of face (c-3)+1/2 (from the previous step)
     R afp[5] = {0, 0, 0, 0, 0};
@@ -457,6 +514,7 @@ __global__ void __launch_bounds__(SWEEP_NB, PPM_SWEEP_MINB) sweep_kernel(const S
     // hydro update of cell c-4 (computed one step earlier)
     R rdn4 = 0, mnn4 = 0, m1n4 = 0, m2n4 = 0, edn4 = 0;
 
+#pragma unroll SWEEP_UNROLL
     for (int c = -G; c < n + G; ++c) {
         // ================= a1: load cell c ==================================
         if constexpr (VEC) {
@@ -472,7 +530,7 @@ __global__ void __launch_bounds__(SWEEP_NB, PPM_SWEEP_MINB) sweep_kernel(const S
         bool flip = false;
         const int m = map_cell(c, n, A.bc_lo, A.bc_hi, flip);
         if (c >= n) {
-            const int si = (A.bc_hi == 0) ? (c - n) : (n + 3 - c);
+            const int si = stash_index(c);
 #pragma unroll
             for (int v = 0; v < 9; ++v) raw[v] = stash[si][v];
         } else {
@@ -497,10 +555,12 @@ __global__ void __launch_bounds__(SWEEP_NB, PPM_SWEEP_MINB) sweep_kernel(const S
         }
         R b_rho0, b_p0, b_g;
         if constexpr (F32) {
-            const float4 bb = base32(coord(A, ax, m));
+            const float4 bb = tab_finish(cell_next);
             b_rho0 = bb.x;
             b_p0 = bb.y;
             b_g = bb.z;
+            bool fln;
+            cell_next = tab_issue(xcell32(map_cell(c + 1, n, A.bc_lo, A.bc_hi, fln)));
         } else {
             R cx[3] = {xyz[0], xyz[1], xyz[2]};
             cx[ax] = coord(A, ax, m);
@@ -527,8 +587,7 @@ __global__ void __launch_bounds__(SWEEP_NB, PPM_SWEEP_MINB) sweep_kernel(const S
             wrd[s] = wrd[s + 1]; wu[s] = wu[s + 1]; wv[s] = wv[s + 1]; ww[s] = ww[s + 1];
             wpd[s] = wpd[s + 1]; wfv[s] = wfv[s + 1]; won[s] = won[s + 1]; wo1[s] = wo1[s + 1];
             wo2[s] = wo2[s + 1]; wro[s] = wro[s + 1]; wp0[s] = wp0[s + 1]; wr0[s] = wr0[s + 1];
-            wg[s] = wg[s + 1]; wmn[s] = wmn[s + 1]; wm1[s] = wm1[s + 1]; wm2[s] = wm2[s + 1];
-            wed[s] = wed[s + 1]; wfs[s] = wfs[s + 1];
+            wg[s] = wg[s + 1]; wfs[s] = wfs[s + 1];
         }
         wrd[4] = rd; wu[4] = u; wv[4] = v; ww[4] = w; wpd[4] = pd;
         if constexpr (F32) {
@@ -542,7 +601,6 @@ __global__ void __launch_bounds__(SWEEP_NB, PPM_SWEEP_MINB) sweep_kernel(const S
         wo2[4] = raw[6 + t2d];
         wro[4] = rho; wp0[4] = b_p0; wr0[4] = b_rho0;
         wg[4] = sg * b_g;
-        wmn[4] = mn; wm1[4] = m1; wm2[4] = m2; wed[4] = ed;
 
         // ================= a2: interface values of face (c-2)+1/2 ==========
         R afn[5];
@@ -650,12 +708,13 @@ __global__ void __launch_bounds__(SWEEP_NB, PPM_SWEEP_MINB) sweep_kernel(const S
         {
             const int j = c - 3;
             R r0, p0;
-            const R xf = xadd(lo, xmul((R)map_face(j, n, A.bc_lo, A.bc_hi), (R)A.dx));
             if constexpr (F32) {
-                const float4 bf = base32(xf);
+                const float4 bf = tab_finish(face_next);
                 r0 = bf.x;
                 p0 = bf.y;
+                face_next = tab_issue(xface32(j + 1));
             } else {
+                const R xf = xadd(lo, xmul((R)map_face(j, n, A.bc_lo, A.bc_hi), (R)A.dx));
                 R fx[3] = {xyz[0], xyz[1], xyz[2]};
                 fx[ax] = xf;
                 const Base<R> bf = base_at(A, fx);
@@ -722,6 +781,13 @@ __global__ void __launch_bounds__(SWEEP_NB, PPM_SWEEP_MINB) sweep_kernel(const S
         R rdn3, mnn3, m1n3, m2n3, edn3;
         {
             const R g = wg[1];
+            // conserved values of cell c-3, re-read from the ring / stash
+            bool fl3;
+            map_cell(c - 3, n, A.bc_lo, A.bc_hi, fl3);
+            const R mn3 = (fl3 ? (R)-1 : (R)1) * raw_at(c - 3, 1 + ax);
+            const R m13 = raw_at(c - 3, 1 + t1d);
+            const R m23 = raw_at(c - 3, 1 + t2d);
+            const R ed3 = PLAIN ? xsub(raw_at(c - 3, 4), xdiv(wp0[1], gm1)) : raw_at(c - 3, 4);
             if constexpr (F32) {
                 float s, e;
                 two_sum(Frc, -Frp, s, e);
@@ -729,14 +795,14 @@ __global__ void __launch_bounds__(SWEEP_NB, PPM_SWEEP_MINB) sweep_kernel(const S
                 rdn3 = wrd[1] - dtdx * dFr;
                 two_sum(FEc, -FEp, s, e);
                 const float dFE = s + (e + (FElc - FElp));
-                edn3 = wed[1] - dtdx * dFE + dt * g * ((R)0.5 * ((Frp + Frlp) + (Frc + Frlc)));
+                edn3 = ed3 - dtdx * dFE + dt * g * ((R)0.5 * ((Frp + Frlp) + (Frc + Frlc)));
             } else {
                 rdn3 = wrd[1] - dtdx * (Frc - Frp);
-                edn3 = wed[1] - dtdx * (FEc - FEp) + dt * g * ((R)0.5 * (Frp + Frc));
+                edn3 = ed3 - dtdx * (FEc - FEp) + dt * g * ((R)0.5 * (Frp + Frc));
             }
-            mnn3 = wmn[1] - dtdx * (Fnc - Fnp) + dt * g * ((R)0.5 * (wrd[1] + rdn3));
-            m1n3 = wm1[1] - dtdx * (Ft1c - Ft1p);
-            m2n3 = wm2[1] - dtdx * (Ft2c - Ft2p);
+            mnn3 = mn3 - dtdx * (Fnc - Fnp) + dt * g * ((R)0.5 * (wrd[1] + rdn3));
+            m1n3 = m13 - dtdx * (Ft1c - Ft1p);
+            m2n3 = m23 - dtdx * (Ft2c - Ft2p);
         }
         const R rnew3 = wr0[1] + rdn3;
 
@@ -875,7 +941,10 @@ __global__ void __launch_bounds__(SWEEP_NB, PPM_SWEEP_MINB) sweep_kernel(const S
 
             R rdo = rdn4, mno = mnn4, m1o = m1n4, m2o = m2n4, edo = edn4;
             R cxo[3] = {xyz[0], xyz[1], xyz[2]};
-            cxo[ax] = coord(A, ax, i);
+            if constexpr (F32)
+                cxo[ax] = xcell32(i);
+            else
+                cxo[ax] = coord(A, ax, i);
             if (A.sources) {
                 R heat = 0, kd = 0;
                 if constexpr (F32) {
@@ -923,16 +992,19 @@ __global__ void __launch_bounds__(SWEEP_NB, PPM_SWEEP_MINB) sweep_kernel(const S
             outc[6 + t1d] = o1;
             outc[6 + t2d] = o2;
             if constexpr (VEC) {
-                // stage 4 cells, then one 16-byte store per variable
-                float *st = outv + ((((i >> 2) & 1) * 9) * SWEEP_NB + tid) * 4 + (i & 3);
+                // stage 8 cells, then one whole 32-byte sector per variable
+                float *st = outv + (size_t)tid * 8 + (i & 7);
 #pragma unroll
-                for (int vv = 0; vv < 9; ++vv) st[vv * SWEEP_NB * 4] = outc[vv];
-                if ((i & 3) == 3) {
-                    const float4 *sv = reinterpret_cast<const float4 *>(outv) + (((i >> 2) & 1) * 9) * SWEEP_NB + tid;
-                    float *g = reinterpret_cast<float *>(q) + (i - 3);
+                for (int vv = 0; vv < 9; ++vv) st[vv * SWEEP_NB * 8] = outc[vv];
+                if ((i & 7) == 7) {
+                    const float4 *sv = reinterpret_cast<const float4 *>(outv) + (size_t)tid * 2;
+                    float *g = reinterpret_cast<float *>(q) + (i - 7);
 #pragma unroll
-                    for (int vv = 0; vv < 9; ++vv)
-                        *reinterpret_cast<float4 *>(g + vv * vs) = sv[vv * SWEEP_NB];
+                    for (int vv = 0; vv < 9; ++vv) {
+                        float4 *d = reinterpret_cast<float4 *>(g + vv * vs);
+                        d[0] = sv[vv * SWEEP_NB * 2];
+                        d[1] = sv[vv * SWEEP_NB * 2 + 1];
+                    }
                 }
             } else {
                 R *p = q + (long long)i * sa;
