@@ -168,6 +168,63 @@ long long ppm_launch_count(const ppm_ctx *ctx);
 int ppm_totals_noalloc(const double *const q_dev[9], int nx, int ny, int nz, double dx,
                        double *totals_dev, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Ensembles: many independent boxes of uneven shapes advanced together, one
+ * kernel launch per pass for all boxes (a work list of pencil blocks, longest
+ * pencils first), the whole double step captured as one CUDA graph.  Each
+ * box keeps its own time step from its own CFL maximum.  This is the batched
+ * form of the same passes (Sec. 4, "a large number of grid pencil updates that
+ * are, pretty much, independent").
+ * ------------------------------------------------------------------------- */
+typedef struct ppm_ens ppm_ens;
+
+typedef struct {
+    int n[3];              /* nx, ny, nz >= 4 */
+    int bc[6];             /* as for ppm_create */
+    ppm_gravity grav;      /* this box's base-state tables */
+    double x0, y0, z0, dx; /* low corner and cell size */
+    const double *heat;    /* optional source tables on grav's grid (NULL) */
+    const double *damp;
+} ppm_box;
+
+/* Create nbox (1..4096) boxes sharing gamma, precision, device and stream
+ * (NULL: private stream).  Each box is a ppm_ctx internally; EINVAL names the
+ * offending box. */
+int ppm_ensemble_create(ppm_ens **out, int nbox, const ppm_box *boxes, double gamma, int precision,
+                        void *stream, int device);
+/* Per-box state transfers (same layout and semantics as ppm_set_state etc.). */
+int ppm_ensemble_set_state(ppm_ens *e, int box, const double *const q[9]);
+int ppm_ensemble_set_region(ppm_ens *e, int box, const int lo[3], const int hi[3], const double *const q[9],
+                            int mem);
+int ppm_ensemble_get_state(ppm_ens *e, int box, double *const q[9]);
+/* CFL time step of every box (dt_out: nbox doubles, or NULL to keep them on
+ * the device). */
+int ppm_ensemble_cfl_dt(ppm_ens *e, double cfl, double *dt_out);
+/* One Strang double step of every box as one graph launch; dt > 0: that dt
+ * for all boxes; dt <= 0: each box's device dt (ESTATE before any cfl). */
+int ppm_ensemble_step(ppm_ens *e, double dt);
+/* FP64 totals and max Mach of one box (as ppm_diagnostics). */
+int ppm_ensemble_diagnostics(ppm_ens *e, int box, double totals[7], double *max_mach);
+/* Wait for the ensemble's work; ENONPHYS if any box flagged a bad cell. */
+int ppm_ensemble_sync(ppm_ens *e);
+/* Tile configuration per axis: block = pencils per block (64 or 128; FP64:
+ * 128), persistent != 0: a resident grid takes work items from a counter
+ * instead of one block per item; vec (axis 0 only): 16-byte x-pass copies for
+ * boxes with nx % 8 == 0 (FP32). */
+int ppm_ensemble_set_config(ppm_ens *e, int axis, int block, int persistent, int vec);
+/* cfg[7] = {block_x, persistent_x, block_y, persistent_y, block_z, persistent_z, vec}. */
+int ppm_ensemble_get_config(const ppm_ens *e, int cfg[7]);
+/* Autotuner: times every configuration of each axis on the current states
+ * (saved and restored around the timing, so they are unchanged) and keeps the
+ * fastest.  cache_path (may be NULL): text file of "signature	config" lines,
+ * signature = GPU name, precision and the sorted box shapes; a matching line
+ * is used without timing (*from_cache = 1).  Needs valid states; the device
+ * time steps must be recomputed afterwards (ppm_ensemble_cfl_dt). */
+int ppm_ensemble_tune(ppm_ens *e, const char *cache_path, int *from_cache);
+long long ppm_ensemble_launch_count(const ppm_ens *e);
+const char *ppm_ensemble_last_error(const ppm_ens *e);
+void ppm_ensemble_destroy(ppm_ens *e);
+
 /* Last error message of this context (or of the last failed ppm_create when
  * ctx is NULL). */
 const char *ppm_last_error(const ppm_ctx *ctx);

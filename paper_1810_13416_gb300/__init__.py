@@ -26,7 +26,7 @@ import numpy as np
 
 from . import build as _build_mod
 
-__all__ = ["Context", "PpmError", "build", "library_path", "FP64_PLAIN", "FP32_DEVIATION",
+__all__ = ["Context", "Ensemble", "PpmError", "build", "library_path", "FP64_PLAIN", "FP32_DEVIATION",
            "BC_PERIODIC", "BC_REFLECT", "GRAV_NONE", "GRAV_PLANE_Z", "GRAV_CENTRAL"]
 
 FP64_PLAIN = 0
@@ -61,6 +61,11 @@ class _Options(C.Structure):
     _fields_ = [("x0", C.c_double), ("y0", C.c_double), ("z0", C.c_double), ("dx", C.c_double),
                 ("precision", C.c_int), ("heat", _DP), ("damp", _DP), ("stream", C.c_void_p),
                 ("device", C.c_int)]
+
+
+class _Box(C.Structure):
+    _fields_ = [("n", C.c_int * 3), ("bc", C.c_int * 6), ("grav", _Gravity), ("x0", C.c_double),
+                ("y0", C.c_double), ("z0", C.c_double), ("dx", C.c_double), ("heat", _DP), ("damp", _DP)]
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -99,6 +104,24 @@ def _load():
     lib.ppm_last_error.restype = C.c_char_p
     lib.ppm_destroy.argtypes = [P]
     lib.ppm_destroy.restype = None
+    lib.ppm_ensemble_create.argtypes = [C.POINTER(P), C.c_int, C.POINTER(_Box), C.c_double, C.c_int, C.c_void_p,
+                                        C.c_int]
+    lib.ppm_ensemble_set_state.argtypes = [P, C.c_int, Q]
+    lib.ppm_ensemble_set_region.argtypes = [P, C.c_int, I3, I3, Q, C.c_int]
+    lib.ppm_ensemble_get_state.argtypes = [P, C.c_int, Q]
+    lib.ppm_ensemble_cfl_dt.argtypes = [P, C.c_double, _DP]
+    lib.ppm_ensemble_step.argtypes = [P, C.c_double]
+    lib.ppm_ensemble_diagnostics.argtypes = [P, C.c_int, _DP, _DP]
+    lib.ppm_ensemble_sync.argtypes = [P]
+    lib.ppm_ensemble_set_config.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int]
+    lib.ppm_ensemble_get_config.argtypes = [P, C.POINTER(C.c_int)]
+    lib.ppm_ensemble_tune.argtypes = [P, C.c_char_p, C.POINTER(C.c_int)]
+    lib.ppm_ensemble_launch_count.argtypes = [P]
+    lib.ppm_ensemble_launch_count.restype = C.c_longlong
+    lib.ppm_ensemble_last_error.argtypes = [P]
+    lib.ppm_ensemble_last_error.restype = C.c_char_p
+    lib.ppm_ensemble_destroy.argtypes = [P]
+    lib.ppm_ensemble_destroy.restype = None
     _lib = lib
     return lib
 
@@ -251,3 +274,128 @@ class Context:
     @property
     def launch_count(self) -> int:
         return int(self.lib.ppm_launch_count(self.h))
+
+
+class Ensemble:
+    """Independent boxes advanced together (a ``ppm_ens``): one launch per
+    pass for all boxes, one graph per double step, tile configuration chosen
+    by the library's autotuner."""
+
+    def __init__(self, problems, precision: int = FP32_DEVIATION, stream=None, device: int = 0):
+        self.lib = _load()
+        self._keep = []
+        boxes = (_Box * len(problems))()
+        gammas = {float(p.gamma) for p in problems}
+        if len(gammas) != 1:
+            raise ValueError("all boxes of an ensemble share gamma")
+        for i, p in enumerate(problems):
+            t = p.tables
+            arrs = [_f64(t.rho0), _f64(t.p0), _f64(t.g)]
+            self._keep.extend(arrs)
+            b = boxes[i]
+            for d in range(3):
+                b.n[d] = int(p.shape[d])
+            for f in range(6):
+                b.bc[f] = int(p.bc[f])
+            b.grav = _Gravity(int(p.grav), int(arrs[0].size), float(t.s0), float(t.ds),
+                              arrs[0].ctypes.data_as(_DP), arrs[1].ctypes.data_as(_DP), arrs[2].ctypes.data_as(_DP))
+            b.x0, b.y0, b.z0 = (float(v) for v in p.origin)
+            b.dx = float(p.dx)
+            for name in ("heat", "damp"):
+                a = getattr(t, name, None)
+                if a is not None:
+                    a = _f64(a)
+                    self._keep.append(a)
+                    setattr(b, name, a.ctypes.data_as(_DP))
+        sptr = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+        h = C.c_void_p()
+        rc = self.lib.ppm_ensemble_create(C.byref(h), len(problems), boxes, gammas.pop(), int(precision), sptr,
+                                          int(device))
+        if rc != 0:
+            raise PpmError(rc, self.lib.ppm_ensemble_last_error(None).decode())
+        self.h = h
+        self.nbox = len(problems)
+        self.shapes = [tuple(int(v) for v in p.shape) for p in problems]
+
+    def _check(self, rc: int):
+        if rc != 0:
+            raise PpmError(rc, self.lib.ppm_ensemble_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ppm_ensemble_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_state(self, box: int, q):
+        arrs = [_f64(a) for a in q]
+        self._check(self.lib.ppm_ensemble_set_state(self.h, int(box), _ptrs(arrs)))
+
+    def set_region(self, box: int, lo, hi, q, device: bool = False):
+        if device:
+            Context._sync_torch()
+            ptrs = (_DP * 9)(*[C.cast(C.c_void_p(int(t.data_ptr())), _DP) for t in q])
+        else:
+            q = [_f64(a) for a in q]
+            ptrs = _ptrs(q)
+        self._check(self.lib.ppm_ensemble_set_region(self.h, int(box), (C.c_int * 3)(*lo), (C.c_int * 3)(*hi),
+                                                     ptrs, MEM_DEVICE if device else MEM_HOST))
+
+    def get_state(self, box: int):
+        nx, ny, nz = self.shapes[box]
+        out = [np.empty((nz, ny, nx)) for _ in range(9)]
+        self._check(self.lib.ppm_ensemble_get_state(self.h, int(box), _ptrs(out)))
+        return out
+
+    def cfl_dt(self, cfl: float, fetch: bool = True):
+        if fetch:
+            out = np.zeros(self.nbox)
+            self._check(self.lib.ppm_ensemble_cfl_dt(self.h, float(cfl), out.ctypes.data_as(_DP)))
+            return out
+        self._check(self.lib.ppm_ensemble_cfl_dt(self.h, float(cfl), None))
+        return None
+
+    def step(self, dt: float = 0.0):
+        self._check(self.lib.ppm_ensemble_step(self.h, float(dt)))
+
+    def diagnostics(self, box: int):
+        tot = np.zeros(7)
+        mm = C.c_double()
+        self._check(self.lib.ppm_ensemble_diagnostics(self.h, int(box), tot.ctypes.data_as(_DP), C.byref(mm)))
+        return tot, mm.value
+
+    def sync(self):
+        self._check(self.lib.ppm_ensemble_sync(self.h))
+
+    def set_config(self, axis: int, block: int, persistent: bool, vec: bool = True):
+        self._check(self.lib.ppm_ensemble_set_config(self.h, int(axis), int(block), int(bool(persistent)),
+                                                     int(bool(vec))))
+
+    def config(self):
+        c = (C.c_int * 7)()
+        self._check(self.lib.ppm_ensemble_get_config(self.h, c))
+        v = list(c)
+        return {"x": (v[0], bool(v[1])), "y": (v[2], bool(v[3])), "z": (v[4], bool(v[5])), "vec_x": bool(v[6])}
+
+    def tune(self, cache_path: Optional[str] = None) -> bool:
+        """Run the autotuner; returns True when the configuration came from
+        the cache file."""
+        fc = C.c_int(0)
+        path = cache_path.encode() if cache_path else None
+        self._check(self.lib.ppm_ensemble_tune(self.h, path, C.byref(fc)))
+        return bool(fc.value)
+
+    @property
+    def launch_count(self) -> int:
+        return int(self.lib.ppm_ensemble_launch_count(self.h))

@@ -15,11 +15,12 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libppm.so")
 BUILD = os.path.join(HERE, "_build")
-UNITS = ["sweep_f32", "sweep_f64", "ppm_api", "noalloc"]
+UNITS = ["sweep_f32", "sweep_f64", "sweep_ens", "ppm_api", "noalloc"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 # per-unit flags: the FP32 pass uses approximate division and square root
-UNIT_FLAGS = {"sweep_f32": ["-prec-div=false", "-prec-sqrt=false"]}
+UNIT_FLAGS = {"sweep_f32": ["-prec-div=false", "-prec-sqrt=false"],
+              "sweep_ens": ["-prec-div=false", "-prec-sqrt=false"]}
 _lock = threading.Lock()
 
 

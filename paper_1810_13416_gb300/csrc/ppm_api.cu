@@ -18,6 +18,10 @@ void launch_sweep_f32(const SweepArgs<float> &a, dim3 grid, dim3 block, cudaStre
 void launch_sweep_f64(const SweepArgs<double> &a, dim3 grid, dim3 block, cudaStream_t st);
 cudaError_t prepare_sweep_f32();
 cudaError_t prepare_sweep_f64();
+cudaError_t prepare_sweep_ensemble();
+int ensemble_blocks_per_sm(int f32, int vec, int nb);
+void launch_sweep_ensemble(int f32, int vec, int nb, const void *args, const WorkItem *work, int nwork,
+                           int *counter, int persistent, int grid, cudaStream_t st);
 }  // namespace ppm
 
 using namespace ppm;
@@ -399,6 +403,13 @@ int region_io(ppm_ctx *c, const int lo[3], const int hi[3], double *const *arrs,
     double **ptab = reinterpret_cast<double **>(c->h_pinned + 8);
     double **dptab = reinterpret_cast<double **>(c->diag_acc + 8 + 6 * MAX_BINS);
     long long kchunk = (mem == PPM_MEM_DEVICE) ? b[2] : std::max(1LL, c->stage_cells / plane);
+    if (mem == PPM_MEM_HOST && !c->stage) {
+        if (cudaMalloc(&c->stage, (size_t)NVAR * c->stage_cells * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            c->stage = nullptr;
+            return fail(c, PPM_ENOMEM, "cannot allocate the host-transfer staging buffer");
+        }
+    }
     if (plane > c->stage_cells && mem == PPM_MEM_HOST) {
         // one plane exceeds the stage: fall back to row chunks is not needed for
         // grids up to stage size; reject explicitly
@@ -579,13 +590,13 @@ int ppm_create(ppm_ctx **out, int nx, int ny, int nz, double gamma, const int bc
             }
         }
     }
-    // stage: up to 2^24 cells per variable (9 x 128 MiB), or the whole grid if smaller
+    // stage (allocated on the first host transfer): up to 2^24 cells per
+    // variable (9 x 128 MiB), or the whole grid if smaller
     c->stage_cells = std::min<long long>(c->ncell, 1LL << 24);
     if (cudaMalloc(&c->t64, h64.size() * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&c->t4, h4.size() * sizeof(float4)) != cudaSuccess ||
         cudaMalloc(&c->t32, h32.size() * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&c->ds_dev, sizeof(DevScal)) != cudaSuccess ||
-        cudaMalloc(&c->stage, (size_t)NVAR * c->stage_cells * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&c->diag_acc, (8 + 6 * MAX_BINS + 16) * sizeof(double)) != cudaSuccess ||
         cudaMallocHost(&c->h_pinned, 64 * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
@@ -596,6 +607,7 @@ int ppm_create(ppm_ctx **out, int nx, int ny, int nz, double gamma, const int bc
         cudaMemcpy(c->t32, h32.data(), h32.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(c->t4, h4.data(), h4.size() * sizeof(float4), cudaMemcpyHostToDevice) != cudaSuccess ||
         prepare_sweep_f32() != cudaSuccess || prepare_sweep_f64() != cudaSuccess ||
+        prepare_sweep_ensemble() != cudaSuccess ||
         cudaMemset(c->ds_dev, 0, sizeof(DevScal)) != cudaSuccess ||
         cudaMemset(c->state, 0, sbytes) != cudaSuccess) {
         fail(c, PPM_ECUDA, "initialising device buffers failed");
@@ -773,6 +785,553 @@ void ppm_destroy(ppm_ctx *c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     release(c);
     delete c;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Ensembles of independent boxes (one launch per pass for all boxes)
+// ===========================================================================
+struct ppm_ens {
+    int nbox = 0;
+    int prec = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<ppm_ctx *> box;
+    void *d_args = nullptr;         // SweepArgs<R>[6 passes][nbox]
+    size_t args_bytes = 0;
+    WorkItem *d_work = nullptr;     // work lists, [axis][variant] slices
+    int work_off[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+    int nwork[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+    int *d_counters = nullptr;      // [6 passes][2 variants]
+    DevScal **d_ds = nullptr;
+    double *d_dx = nullptr;
+    int cfg_nb[3] = {128, 128, 128};
+    int cfg_pers[3] = {1, 1, 1};
+    int cfg_vec = 1;
+    int bps[3] = {1, 1, 1};         // resident blocks per SM: scalar 64, scalar 128, vec 128
+    int nsm = 152;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    cudaGraphNode_t dt_node = nullptr;
+    bool have_speed = false;
+    long long launches = 0;
+    std::string err;
+};
+
+namespace {
+
+constexpr int ENS_PASS_AXIS[6] = {0, 1, 2, 2, 1, 0};
+
+int efail(ppm_ens *e, int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (e)
+        e->err = buf;
+    else
+        g_create_error = buf;
+    return code;
+}
+
+#define ECK(ens, call)                                                                         \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return efail((ens), PPM_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_),     \
+                         __FILE__, __LINE__);                                                  \
+    } while (0)
+
+// dt of every box for the next step, clearing the running maxima and the
+// work counters of the persistent passes.
+__global__ void ens_dt_kernel(DevScal *const *ds, const double *dx, int nbox, int *counters, int ncounters,
+                              double dt_user) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbox; b += gridDim.x * blockDim.x) {
+        DevScal *s = ds[b];
+        const double smax = __longlong_as_double((long long)s->smax);
+        s->dt = (dt_user > 0.0) ? dt_user : s->cfl * dx[b] / smax;
+        s->smax = 0ull;
+    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncounters; i += gridDim.x * blockDim.x) counters[i] = 0;
+}
+
+__global__ void zero_ints_kernel(int *p, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = 0;
+}
+
+int pencils_along(const ppm_ctx *c, int axis, int *nlane, int *nblk) {
+    if (axis == 0) {
+        *nlane = c->n[1];
+        *nblk = c->n[2];
+    } else if (axis == 1) {
+        *nlane = c->n[0];
+        *nblk = c->n[2];
+    } else {
+        *nlane = c->n[0];
+        *nblk = c->n[1];
+    }
+    return c->n[axis];
+}
+
+bool box_vec_ok(const ppm_ens *e, int b) { return e->prec == PPM_FP32_DEVIATION && (e->box[b]->n[0] % 8) == 0; }
+
+// Work lists for the current configuration: longest pencils first.
+int build_work(ppm_ens *e) {
+    std::vector<WorkItem> all;
+    for (int a = 0; a < 3; ++a) {
+        for (int var = 0; var < 2; ++var) {
+            std::vector<WorkItem> items;
+            for (int b = 0; b < e->nbox; ++b) {
+                const bool v = (a == 0) && e->cfg_vec && box_vec_ok(e, b);
+                if ((var == 1) != v) continue;
+                const int nb = v ? 128 : e->cfg_nb[a];
+                int nlane, nblk;
+                pencils_along(e->box[b], a, &nlane, &nblk);
+                const int nlb = (nlane + nb - 1) / nb;
+                for (int k = 0; k < nblk; ++k)
+                    for (int l = 0; l < nlb; ++l) items.push_back(WorkItem{b, l, k, 0});
+            }
+            std::stable_sort(items.begin(), items.end(), [&](const WorkItem &x, const WorkItem &y) {
+                return e->box[x.box]->n[a] > e->box[y.box]->n[a];
+            });
+            e->work_off[a][var] = (int)all.size();
+            e->nwork[a][var] = (int)items.size();
+            all.insert(all.end(), items.begin(), items.end());
+        }
+    }
+    if (e->d_work) cudaFree(e->d_work);
+    e->d_work = nullptr;
+    ECK(e, cudaMalloc(&e->d_work, std::max<size_t>(1, all.size()) * sizeof(WorkItem)));
+    ECK(e, cudaMemcpy(e->d_work, all.data(), all.size() * sizeof(WorkItem), cudaMemcpyHostToDevice));
+    if (e->gexec) cudaGraphExecDestroy(e->gexec);
+    if (e->graph) cudaGraphDestroy(e->graph);
+    e->gexec = nullptr;
+    e->graph = nullptr;
+    return PPM_OK;
+}
+
+// Launch one pass (both variants) of every box.
+int ens_launch_pass(ppm_ens *e, int pass) {
+    const int a = ENS_PASS_AXIS[pass];
+    const int f32 = e->prec == PPM_FP32_DEVIATION;
+    const size_t asz = f32 ? sizeof(SweepArgs<float>) : sizeof(SweepArgs<double>);
+    const void *args = static_cast<const char *>(e->d_args) + (size_t)pass * e->nbox * asz;
+    for (int var = 1; var >= 0; --var) {
+        const int nw = e->nwork[a][var];
+        if (nw == 0) continue;
+        const int vec = var;
+        const int nb = vec ? 128 : (f32 ? e->cfg_nb[a] : 128);
+        const int pers = e->cfg_pers[a];
+        int grid = nw;
+        if (pers) grid = std::min(nw, e->nsm * e->bps[vec ? 2 : (nb == 64 ? 0 : 1)]);
+        launch_sweep_ensemble(f32, vec, nb, args, e->d_work + e->work_off[a][var], nw, e->d_counters + pass * 2 + var,
+                              pers, grid, e->stream);
+        e->launches++;
+        ECK(e, cudaGetLastError());
+    }
+    return PPM_OK;
+}
+
+int ens_capture(ppm_ens *e) {
+    ECK(e, cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal));
+    ens_dt_kernel<<<1, 256, 0, e->stream>>>(e->d_ds, e->d_dx, e->nbox, e->d_counters, 12, -1.0);
+    int rc = PPM_OK;
+    const long long l0 = e->launches;
+    for (int s = 0; s < 6 && rc == PPM_OK; ++s) rc = ens_launch_pass(e, s);
+    e->launches = l0;
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(e->stream, &g);
+    if (rc != PPM_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (ce != cudaSuccess) return efail(e, PPM_ECUDA, "stream capture: %s", cudaGetErrorString(ce));
+    e->graph = g;
+    size_t nn = 0;
+    ECK(e, cudaGraphGetRootNodes(e->graph, nullptr, &nn));
+    if (nn != 1) return efail(e, PPM_ECUDA, "unexpected ensemble graph shape (%zu roots)", nn);
+    ECK(e, cudaGraphGetRootNodes(e->graph, &e->dt_node, &nn));
+    ECK(e, cudaGraphInstantiate(&e->gexec, e->graph, 0));
+    return PPM_OK;
+}
+
+int graph_launches_per_step(const ppm_ens *e) {
+    int n = 1;
+    for (int s = 0; s < 6; ++s)
+        for (int var = 0; var < 2; ++var) n += e->nwork[ENS_PASS_AXIS[s]][var] > 0 ? 1 : 0;
+    return n;
+}
+
+void ens_release(ppm_ens *e) {
+    if (e->stream) cudaStreamSynchronize(e->stream);
+    if (e->gexec) cudaGraphExecDestroy(e->gexec);
+    if (e->graph) cudaGraphDestroy(e->graph);
+    for (ppm_ctx *c : e->box) ppm_destroy(c);
+    e->box.clear();
+    if (e->d_args) cudaFree(e->d_args);
+    if (e->d_work) cudaFree(e->d_work);
+    if (e->d_counters) cudaFree(e->d_counters);
+    if (e->d_ds) cudaFree(e->d_ds);
+    if (e->d_dx) cudaFree(e->d_dx);
+    if (e->own_stream && e->stream) cudaStreamDestroy(e->stream);
+}
+
+std::string ens_signature(const ppm_ens *e) {
+    cudaDeviceProp prop;
+    cudaGetDeviceProperties(&prop, e->device);
+    std::vector<std::string> shapes;
+    for (const ppm_ctx *c : e->box) {
+        char b[64];
+        snprintf(b, sizeof(b), "%dx%dx%d", c->n[0], c->n[1], c->n[2]);
+        shapes.push_back(b);
+    }
+    std::sort(shapes.begin(), shapes.end());
+    std::string key = std::string(prop.name) + "|prec" + std::to_string(e->prec) + "|";
+    for (size_t i = 0; i < shapes.size(); ++i) key += (i ? "," : "") + shapes[i];
+    for (char &ch : key)
+        if (ch == ' ' || ch == '\t') ch = '_';
+    return key;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ppm_ensemble_create(ppm_ens **out, int nbox, const ppm_box *boxes, double gamma, int precision, void *stream,
+                        int device) {
+    if (!out || !boxes) return efail(nullptr, PPM_EINVAL, "null argument");
+    *out = nullptr;
+    if (nbox < 1 || nbox > 4096) return efail(nullptr, PPM_EINVAL, "nbox must be in [1, 4096]");
+    if (precision != PPM_FP64_PLAIN && precision != PPM_FP32_DEVIATION)
+        return efail(nullptr, PPM_EINVAL, "bad precision");
+    ppm_ens *e = new ppm_ens();
+    e->nbox = nbox;
+    e->prec = precision;
+    e->device = device;
+    auto bail = [&](int code) {
+        std::string m = e->err;
+        ens_release(e);
+        delete e;
+        g_create_error = m;
+        return code;
+    };
+    if (cudaSetDevice(device) != cudaSuccess) {
+        efail(e, PPM_ECUDA, "cudaSetDevice(%d) failed", device);
+        return bail(PPM_ECUDA);
+    }
+    if (stream) {
+        e->stream = (cudaStream_t)stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            efail(e, PPM_ECUDA, "cudaStreamCreate failed");
+            return bail(PPM_ECUDA);
+        }
+        e->own_stream = true;
+    }
+    for (int b = 0; b < nbox; ++b) {
+        const ppm_box &B = boxes[b];
+        ppm_options opt;
+        memset(&opt, 0, sizeof(opt));
+        opt.x0 = B.x0;
+        opt.y0 = B.y0;
+        opt.z0 = B.z0;
+        opt.dx = B.dx;
+        opt.precision = precision;
+        opt.heat = B.heat;
+        opt.damp = B.damp;
+        opt.stream = e->stream;
+        opt.device = device;
+        ppm_ctx *c = nullptr;
+        const int rc = ppm_create(&c, B.n[0], B.n[1], B.n[2], gamma, B.bc, &B.grav, &opt);
+        if (rc != PPM_OK) {
+            efail(e, rc, "box %d: %s", b, g_create_error.c_str());
+            return bail(rc);
+        }
+        e->box.push_back(c);
+    }
+    // per-pass argument arrays
+    const int f32 = precision == PPM_FP32_DEVIATION;
+    const size_t asz = f32 ? sizeof(SweepArgs<float>) : sizeof(SweepArgs<double>);
+    std::vector<char> h((size_t)6 * nbox * asz);
+    for (int s = 0; s < 6; ++s)
+        for (int b = 0; b < nbox; ++b) {
+            ppm_ctx *c = e->box[b];
+            const int src = (s == 2 || s == 5) ? ((c->has_heat || c->has_damp) ? 1 : 0) : 0;
+            char *dst = h.data() + ((size_t)s * nbox + b) * asz;
+            if (f32) {
+                SweepArgs<float> a = make_args<float>(c, ENS_PASS_AXIS[s]);
+                a.sources = src;
+                a.cfl = (s == 5);
+                memcpy(dst, &a, asz);
+            } else {
+                SweepArgs<double> a = make_args<double>(c, ENS_PASS_AXIS[s]);
+                a.sources = src;
+                a.cfl = (s == 5);
+                memcpy(dst, &a, asz);
+            }
+        }
+    std::vector<DevScal *> hds(nbox);
+    std::vector<double> hdx(nbox);
+    for (int b = 0; b < nbox; ++b) {
+        hds[b] = e->box[b]->ds_dev;
+        hdx[b] = e->box[b]->dx;
+    }
+    if (cudaMalloc(&e->d_args, h.size()) != cudaSuccess || cudaMalloc(&e->d_counters, 12 * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&e->d_ds, nbox * sizeof(DevScal *)) != cudaSuccess ||
+        cudaMalloc(&e->d_dx, nbox * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        efail(e, PPM_ENOMEM, "cannot allocate ensemble tables");
+        return bail(PPM_ENOMEM);
+    }
+    e->args_bytes = h.size();
+    if (cudaMemcpy(e->d_args, h.data(), h.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(e->d_ds, hds.data(), nbox * sizeof(DevScal *), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(e->d_dx, hdx.data(), nbox * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(e->d_counters, 0, 12 * sizeof(int)) != cudaSuccess) {
+        efail(e, PPM_ECUDA, "initialising ensemble tables failed");
+        return bail(PPM_ECUDA);
+    }
+    {
+        int nsm = 0;
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
+        e->nsm = nsm > 0 ? nsm : 152;
+        e->bps[0] = ensemble_blocks_per_sm(f32, 0, 64);
+        e->bps[1] = ensemble_blocks_per_sm(f32, 0, 128);
+        e->bps[2] = ensemble_blocks_per_sm(f32, 1, 128);
+    }
+    const int rc = build_work(e);
+    if (rc != PPM_OK) return bail(rc);
+    *out = e;
+    return PPM_OK;
+}
+
+int ppm_ensemble_set_state(ppm_ens *e, int b, const double *const q[9]) {
+    if (!e || b < 0 || b >= e->nbox) return efail(e, PPM_EINVAL, "bad ensemble or box index");
+    const int rc = ppm_set_state(e->box[b], q);
+    if (rc != PPM_OK) return efail(e, rc, "box %d: %s", b, e->box[b]->err.c_str());
+    e->have_speed = false;
+    return PPM_OK;
+}
+
+int ppm_ensemble_set_region(ppm_ens *e, int b, const int lo[3], const int hi[3], const double *const q[9], int mem) {
+    if (!e || b < 0 || b >= e->nbox) return efail(e, PPM_EINVAL, "bad ensemble or box index");
+    const int rc = ppm_set_region(e->box[b], lo, hi, q, mem);
+    if (rc != PPM_OK) return efail(e, rc, "box %d: %s", b, e->box[b]->err.c_str());
+    e->have_speed = false;
+    return PPM_OK;
+}
+
+int ppm_ensemble_get_state(ppm_ens *e, int b, double *const q[9]) {
+    if (!e || b < 0 || b >= e->nbox) return efail(e, PPM_EINVAL, "bad ensemble or box index");
+    const int rc = ppm_get_state(e->box[b], q);
+    if (rc != PPM_OK) return efail(e, rc, "box %d: %s", b, e->box[b]->err.c_str());
+    return PPM_OK;
+}
+
+int ppm_ensemble_cfl_dt(ppm_ens *e, double cfl, double *dt_out) {
+    if (!e) return PPM_EINVAL;
+    for (int b = 0; b < e->nbox; ++b) {
+        const int rc = ppm_cfl_dt(e->box[b], cfl, dt_out ? dt_out + b : nullptr);
+        if (rc != PPM_OK) return efail(e, rc, "box %d: %s", b, e->box[b]->err.c_str());
+        e->launches += 2;
+    }
+    e->have_speed = true;
+    return PPM_OK;
+}
+
+int ppm_ensemble_step(ppm_ens *e, double dt) {
+    if (!e) return PPM_EINVAL;
+    if (!(dt > 0.0) && !e->have_speed)
+        return efail(e, PPM_ESTATE, "ppm_ensemble_step with dt <= 0 needs device dts (call ppm_ensemble_cfl_dt)");
+    if (!std::isfinite(dt)) return efail(e, PPM_EINVAL, "dt is not finite");
+    if (!e->gexec) {
+        const int rc = ens_capture(e);
+        if (rc != PPM_OK) return rc;
+    }
+    DevScal **dsp = e->d_ds;
+    const double *dxp = e->d_dx;
+    int nb = e->nbox, *ctr = e->d_counters, nctr = 12;
+    double dtu = dt > 0.0 ? dt : -1.0;
+    void *args[6] = {&dsp, &dxp, &nb, &ctr, &nctr, &dtu};
+    cudaKernelNodeParams kp;
+    memset(&kp, 0, sizeof(kp));
+    kp.func = (void *)ens_dt_kernel;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(256);
+    kp.kernelParams = args;
+    ECK(e, cudaGraphExecKernelNodeSetParams(e->gexec, e->dt_node, &kp));
+    ECK(e, cudaGraphLaunch(e->gexec, e->stream));
+    e->launches += graph_launches_per_step(e);
+    e->have_speed = true;
+    return PPM_OK;
+}
+
+int ppm_ensemble_diagnostics(ppm_ens *e, int b, double totals[7], double *max_mach) {
+    if (!e || b < 0 || b >= e->nbox) return efail(e, PPM_EINVAL, "bad ensemble or box index");
+    const int rc = ppm_diagnostics(e->box[b], totals, 0, 1.0, nullptr, max_mach);
+    if (rc != PPM_OK) return efail(e, rc, "box %d: %s", b, e->box[b]->err.c_str());
+    e->launches += 1;
+    return PPM_OK;
+}
+
+int ppm_ensemble_sync(ppm_ens *e) {
+    if (!e) return PPM_EINVAL;
+    for (int b = 0; b < e->nbox; ++b) {
+        const int rc = ppm_sync(e->box[b]);
+        if (rc != PPM_OK) return efail(e, rc, "box %d: %s", b, e->box[b]->err.c_str());
+    }
+    return PPM_OK;
+}
+
+int ppm_ensemble_set_config(ppm_ens *e, int axis, int block, int persistent, int vec) {
+    if (!e || axis < 0 || axis > 2) return efail(e, PPM_EINVAL, "bad axis");
+    if (block != 64 && block != 128) return efail(e, PPM_EINVAL, "block must be 64 or 128");
+    if (e->prec != PPM_FP32_DEVIATION && block != 128) return efail(e, PPM_EINVAL, "FP64 passes use 128-thread blocks");
+    e->cfg_nb[axis] = block;
+    e->cfg_pers[axis] = persistent ? 1 : 0;
+    if (axis == 0) e->cfg_vec = vec ? 1 : 0;
+    return build_work(e);
+}
+
+int ppm_ensemble_get_config(const ppm_ens *e, int cfg[7]) {
+    if (!e || !cfg) return PPM_EINVAL;
+    for (int a = 0; a < 3; ++a) {
+        cfg[2 * a] = e->cfg_nb[a];
+        cfg[2 * a + 1] = e->cfg_pers[a];
+    }
+    cfg[6] = e->cfg_vec;
+    return PPM_OK;
+}
+
+int ppm_ensemble_tune(ppm_ens *e, const char *cache_path, int *from_cache) {
+    if (!e) return PPM_EINVAL;
+    if (from_cache) *from_cache = 0;
+    const std::string key = ens_signature(e);
+    if (cache_path) {
+        FILE *f = fopen(cache_path, "r");
+        if (f) {
+            char line[8192];
+            while (fgets(line, sizeof(line), f)) {
+                char *tab = strchr(line, '\t');
+                if (!tab) continue;
+                *tab = 0;
+                if (key != line) continue;
+                int v[7];
+                if (sscanf(tab + 1, "%d %d %d %d %d %d %d", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6]) == 7) {
+                    fclose(f);
+                    for (int a = 0; a < 3; ++a) {
+                        e->cfg_nb[a] = v[2 * a];
+                        e->cfg_pers[a] = v[2 * a + 1];
+                    }
+                    e->cfg_vec = v[6];
+                    if (from_cache) *from_cache = 1;
+                    return build_work(e);
+                }
+            }
+            fclose(f);
+        }
+    }
+    // snapshot the states, time every candidate on the real data, restore
+    std::vector<void *> snap(e->nbox, nullptr);
+    size_t total = 0;
+    for (ppm_ctx *c : e->box) total += (size_t)NVAR * c->ncell * (e->prec == PPM_FP32_DEVIATION ? 4 : 8);
+    char *scratch = nullptr;
+    ECK(e, cudaMalloc(&scratch, total));
+    auto copy_all = [&](bool save) -> int {
+        size_t off = 0;
+        for (ppm_ctx *c : e->box) {
+            const size_t bytes = (size_t)NVAR * c->ncell * (e->prec == PPM_FP32_DEVIATION ? 4 : 8);
+            ECK(e, cudaMemcpyAsync(save ? scratch + off : c->state, save ? c->state : scratch + off, bytes,
+                                   cudaMemcpyDeviceToDevice, e->stream));
+            off += bytes;
+        }
+        return PPM_OK;
+    };
+    int rc = copy_all(true);
+    // a valid dt for every box: half the CFL-0.5 step of the current state
+    for (int b = 0; b < e->nbox && rc == PPM_OK; ++b) {
+        double dtb = 0.0;
+        if (ppm_cfl_dt(e->box[b], 0.5, &dtb) != PPM_OK) rc = efail(e, PPM_ENONPHYS, "box %d has no valid state to tune on", b);
+        else set_scalar_kernel<<<1, 32, 0, e->stream>>>(&e->box[b]->ds_dev->dt, 0.5 * dtb);
+    }
+    const bool f32 = e->prec == PPM_FP32_DEVIATION;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    if (rc == PPM_OK && (cudaEventCreate(&t0) != cudaSuccess || cudaEventCreate(&t1) != cudaSuccess))
+        rc = efail(e, PPM_ECUDA, "cudaEventCreate failed");
+    for (int a = 0; a < 3 && rc == PPM_OK; ++a) {
+        float best = 1e30f;
+        int bnb = 128, bpers = 1, bvec = e->cfg_vec;
+        const int nbs[2] = {64, 128};
+        for (int vec = (a == 0 && f32) ? 1 : e->cfg_vec; vec >= 0 && rc == PPM_OK; --vec) {
+            for (int ib = (f32 ? 0 : 1); ib < 2 && rc == PPM_OK; ++ib) {
+                for (int pers = 0; pers < 2 && rc == PPM_OK; ++pers) {
+                    e->cfg_nb[a] = nbs[ib];
+                    e->cfg_pers[a] = pers;
+                    if (a == 0) e->cfg_vec = vec;
+                    if ((rc = build_work(e)) != PPM_OK) break;
+                    const int pass = a;  // passes 0, 1, 2 are x, y, z
+                    float ms = 0.0f;
+                    for (int rep = 0; rep < 3 && rc == PPM_OK; ++rep) {
+                        zero_ints_kernel<<<1, 32, 0, e->stream>>>(e->d_counters, 12);
+                        cudaEventRecord(t0, e->stream);
+                        rc = ens_launch_pass(e, pass);
+                        cudaEventRecord(t1, e->stream);
+                        if (rc == PPM_OK) rc = copy_all(false);
+                        if (cudaEventSynchronize(t1) != cudaSuccess) rc = efail(e, PPM_ECUDA, "event sync failed");
+                        float m = 0.0f;
+                        cudaEventElapsedTime(&m, t0, t1);
+                        if (rep > 0) ms += m;  // first repetition warms up
+                    }
+                    if (rc == PPM_OK && ms < best) {
+                        best = ms;
+                        bnb = nbs[ib];
+                        bpers = pers;
+                        bvec = (a == 0) ? vec : e->cfg_vec;
+                    }
+                }
+            }
+        }
+        e->cfg_nb[a] = bnb;
+        e->cfg_pers[a] = bpers;
+        if (a == 0) e->cfg_vec = bvec;
+    }
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    cudaStreamSynchronize(e->stream);
+    for (ppm_ctx *c : e->box) cudaMemsetAsync(&c->ds_dev->flags, 0, sizeof(int), e->stream);
+    cudaStreamSynchronize(e->stream);
+    cudaFree(scratch);
+    e->have_speed = false;
+    if (rc != PPM_OK) return rc;
+    rc = build_work(e);
+    if (rc != PPM_OK) return rc;
+    if (cache_path) {
+        FILE *f = fopen(cache_path, "a");
+        if (f) {
+            fprintf(f, "%s\t%d %d %d %d %d %d %d\n", key.c_str(), e->cfg_nb[0], e->cfg_pers[0], e->cfg_nb[1],
+                    e->cfg_pers[1], e->cfg_nb[2], e->cfg_pers[2], e->cfg_vec);
+            fclose(f);
+        }
+    }
+    return PPM_OK;
+}
+
+long long ppm_ensemble_launch_count(const ppm_ens *e) {
+    if (!e) return 0;
+    long long n = e->launches;
+    for (const ppm_ctx *c : e->box) n += c->launches;
+    return n;
+}
+
+const char *ppm_ensemble_last_error(const ppm_ens *e) { return e ? e->err.c_str() : g_create_error.c_str(); }
+
+void ppm_ensemble_destroy(ppm_ens *e) {
+    if (!e) return;
+    ens_release(e);
+    delete e;
 }
 
 }  // extern "C"

@@ -325,9 +325,9 @@ constexpr int RING = 8;         // scalar prefetch ring slots per thread
 constexpr int PREF = 4;         // scalar prefetch distance (cells)
 
 // Dynamic shared memory of one block of the pass.
-template <typename R, bool VEC>
+template <typename R, bool VEC, int NB = SWEEP_NB>
 constexpr int sweep_smem_bytes() {
-    return VEC ? (4 * 9 * SWEEP_NB * 16 + 9 * SWEEP_NB * 32) : (RING * 9 * SWEEP_NB * (int)sizeof(R));
+    return VEC ? (4 * 9 * NB * 16 + 9 * NB * 32) : (RING * 9 * NB * (int)sizeof(R));
 }
 
 #ifndef PPM_SWEEP_UNROLL
@@ -343,14 +343,16 @@ constexpr int SWEEP_UNROLL = PPM_SWEEP_UNROLL;  // unroll factor of the march lo
 // results back 8 cells (one whole 32-byte sector) at a time, instead of 9
 // scalar accesses per cell that touch 32 different cache lines per warp.
 // ---------------------------------------------------------------------------
-template <typename R, bool PLAIN, bool VEC>
-__global__ void __launch_bounds__(SWEEP_NB, PPM_SWEEP_MINB) sweep_kernel(const SweepArgs<R> A) {
+// One block of the pass: NB consecutive pencils (lane_block) of pencil row
+// blk.  Called by the single-grid kernel and by the work-list kernel.
+template <typename R, bool PLAIN, bool VEC, int NB>
+__device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block, int blk,
+                                           unsigned char *smem_raw) {
+    constexpr int SWEEP_NB = NB;
     constexpr bool F32 = std::is_same<R, float>::value;
     static_assert(!VEC || F32, "vector path is FP32 only");
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tid = threadIdx.x;
-    const int lane = blockIdx.x * blockDim.x + threadIdx.x;
-    const int blk = blockIdx.y;
+    const int lane = lane_block * NB + threadIdx.x;
     // threads past the edge take part in the final warp reduction only
     const bool active = (lane < A.nlane) && (blk < A.nblk);
     R smax_local = 0;
@@ -1035,6 +1037,49 @@ __global__ void __launch_bounds__(SWEEP_NB, PPM_SWEEP_MINB) sweep_kernel(const S
         double sm = (double)smax_local;
         for (int o = 16; o > 0; o >>= 1) sm = fmax(sm, __shfl_xor_sync(0xffffffffu, sm, o));
         if ((threadIdx.x & 31) == 0) atomicMax(A.smax, dbits(sm));
+    }
+}
+
+template <typename R, bool PLAIN, bool VEC>
+__global__ void __launch_bounds__(SWEEP_NB, PPM_SWEEP_MINB) sweep_kernel(const SweepArgs<R> A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    sweep_body<R, PLAIN, VEC, SWEEP_NB>(A, blockIdx.x, blockIdx.y, smem_raw);
+}
+
+// ---------------------------------------------------------------------------
+// Ensemble pass: one launch walks a work list of (box, lane block, pencil row)
+// items of many independent boxes; each box has its own arguments (shape,
+// tables, dt, CFL accumulator).  persistent != 0: a grid of resident blocks
+// takes items from a counter in list order (longest pencils first); else one
+// block per item.
+// ---------------------------------------------------------------------------
+struct WorkItem {
+    int box, lane_block, blk, pad;
+};
+
+template <typename R, bool PLAIN, bool VEC, int NB>
+__global__ void __launch_bounds__(NB, 1) sweep_ensemble_kernel(const SweepArgs<R> *__restrict__ args,
+                                                               const WorkItem *__restrict__ work, int nwork,
+                                                               int *counter, int persistent) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ SweepArgs<R> sA;
+    __shared__ int s_item;
+    int item = blockIdx.x;
+    if (persistent) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        item = s_item;
+    }
+    while (item < nwork) {
+        const WorkItem w = work[item];
+        if (threadIdx.x == 0) sA = args[w.box];
+        __syncthreads();
+        sweep_body<R, PLAIN, VEC, NB>(sA, w.lane_block, w.blk, smem_raw);
+        __syncthreads();
+        if (!persistent) break;
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        item = s_item;
     }
 }
 

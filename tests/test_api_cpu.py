@@ -75,3 +75,14 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(ppm, "_lib", None)
     with pytest.raises(ImportError):
         ppm._load()
+
+
+def test_ensemble_create_rejects_bad_arguments(lib):
+    h = C.c_void_p()
+    boxes = (ppm._Box * 1)()
+    assert lib.ppm_ensemble_create(C.byref(h), 0, boxes, 1.4, 1, None, 0) == -1
+    assert "nbox" in lib.ppm_ensemble_last_error(None).decode()
+    assert lib.ppm_ensemble_create(C.byref(h), 1, boxes, 1.4, 7, None, 0) == -1
+    assert lib.ppm_ensemble_step(None, 1.0) == -1
+    assert lib.ppm_ensemble_launch_count(None) == 0
+    lib.ppm_ensemble_destroy(None)

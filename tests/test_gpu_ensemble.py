@@ -1,0 +1,134 @@
+"""Batched ensembles (one launch per pass for many uneven boxes) on the GPU.
+
+* Every box of an ensemble evolves exactly (bit for bit) as the same box in
+  its own single-grid context, under every tile configuration the autotuner
+  can choose (64/128-thread blocks, persistent or one block per item, x-pass
+  vector path on or off), including a box whose x extent is not a multiple
+  of 8 and a box with periodic x/y.
+* Boxes agree with the oracle within the FP32 (and FP64) tolerances.
+* The autotuner leaves the states unchanged and reuses its cache.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1810_13416_gb300 as ppm
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ppm.build()
+    oracle.build()
+
+
+def _boxes():
+    shapes = [(48, 32, 40), (52, 36, 44), (64, 48, 32), (40, 40, 56), (32, 24, 24)]
+    rates = [1e-4, 3e-3, 1e-2, 5e-4, 2e-3]
+    return [workloads.strat_box(shape=s, seed=7000 + i, heat_rate=r) for i, (s, r) in enumerate(zip(shapes, rates))]
+
+
+CONFIGS = [
+    [(128, 1, 1), (128, 1, 1), (128, 1, 1)],
+    [(64, 0, 0), (64, 0, 0), (64, 0, 0)],
+    [(128, 0, 1), (64, 1, 0), (128, 0, 0)],
+    [(64, 1, 0), (128, 0, 0), (64, 1, 0)],
+]
+
+
+@pytest.mark.parametrize("cfg", CONFIGS)
+def test_ensemble_equals_single_contexts_bitwise(cfg):
+    probs = _boxes()
+    qs = [workloads.build(p) for p in probs]
+    ens = ppm.Ensemble(probs, precision=ppm.FP32_DEVIATION)
+    for axis, (nb, pers, vec) in enumerate(cfg):
+        ens.set_config(axis, nb, pers, vec)
+    for b, q in enumerate(qs):
+        ens.set_state(b, q)
+    ens.cfl_dt(0.7, fetch=False)
+    for _ in range(4):
+        ens.step(0.0)
+    ens.sync()
+    for b, (p, q) in enumerate(zip(probs, qs)):
+        with ppm.Context.from_problem(p, precision=ppm.FP32_DEVIATION) as ctx:
+            ctx.set_state(q)
+            ctx.cfl_dt(0.7, fetch=False)
+            for _ in range(4):
+                ctx.step(0.0)
+            ref = ctx.get_state()
+        got = ens.get_state(b)
+        for v in range(9):
+            assert np.array_equal(got[v], ref[v]), (b, v)
+    ens.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(ppm.FP32_DEVIATION, 1e-5), (ppm.FP64_PLAIN, 1e-10)])
+def test_ensemble_matches_oracle(precision, tol):
+    probs = _boxes()[:3]
+    qs = [workloads.build(p) for p in probs]
+    qo = [[a.copy() for a in q] for q in qs]
+    ens = ppm.Ensemble(probs, precision=precision)
+    for b, q in enumerate(qs):
+        ens.set_state(b, q)
+    os_ = [oracle.Oracle(p) for p in probs]
+    for _ in range(4):
+        dt = min(o.cfl_dt(q, 0.7) for o, q in zip(os_, qo))
+        for o, q in zip(os_, qo):
+            o.double_step(q, dt)
+        ens.step(dt)
+    for b in range(len(probs)):
+        got = ens.get_state(b)
+        ref = qo[b]
+        if precision == ppm.FP64_PLAIN:
+            for v in range(9):
+                s = np.abs(ref[v]).max()
+                assert np.abs(got[v] - ref[v]).max() <= tol * (s if s > 0 else 1.0), (b, v)
+        else:
+            for v in (0, 4):
+                assert np.abs(got[v] - ref[v]).sum() / np.abs(ref[v]).sum() <= tol, (b, v)
+            assert np.abs(got[5] - ref[5]).mean() <= 1e-7
+    ens.close()
+
+
+def test_tuner_keeps_states_and_uses_cache(tmp_path):
+    probs = _boxes()
+    qs = [workloads.build(p) for p in probs]
+    cache = str(tmp_path / "tune.txt")
+    ens = ppm.Ensemble(probs, precision=ppm.FP32_DEVIATION)
+    for b, q in enumerate(qs):
+        ens.set_state(b, q)
+    before = [ens.get_state(b) for b in range(len(probs))]
+    assert ens.tune(cache) is False
+    cfg = ens.config()
+    after = [ens.get_state(b) for b in range(len(probs))]
+    for b in range(len(probs)):
+        for v in range(9):
+            assert np.array_equal(before[b][v], after[b][v])
+    for ax in "xyz":
+        assert cfg[ax][0] in (64, 128)
+    ens.cfl_dt(0.7, fetch=False)
+    ens.step(0.0)
+    ens.sync()
+    ens.close()
+    ens2 = ppm.Ensemble(probs, precision=ppm.FP32_DEVIATION)
+    for b, q in enumerate(qs):
+        ens2.set_state(b, q)
+    assert ens2.tune(cache) is True
+    assert ens2.config() == cfg
+    ens2.close()
+
+
+def test_ensemble_step_needs_dt():
+    probs = _boxes()[:2]
+    ens = ppm.Ensemble(probs, precision=ppm.FP32_DEVIATION)
+    for b, p in enumerate(probs):
+        ens.set_state(b, workloads.build(p))
+    with pytest.raises(ppm.PpmError) as e:
+        ens.step(0.0)
+    assert e.value.code == -7
+    ens.close()

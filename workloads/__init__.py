@@ -368,6 +368,24 @@ def sphere(n: int = 1024, seed: int = 5810, xi_R: float = 3.0, gamma: float = 5.
                               nmodes=nmodes, kmax=kmax))
 
 
+def ensemble_boxes(nbox: int = 24, seed: int = 3810, sizes=tuple(range(48, 193, 16))) -> List[Problem]:
+    """Batched-ensemble workload: nbox stratified boxes whose three extents are
+    drawn independently from `sizes` (48..192 in steps of 16, so shapes such
+    as 64x128x96 occur), each with its own heating rate (log-uniform in
+    [1e-4, 1e-2]) and its own noise seed."""
+    rng = SplitMix64(seed)
+    out = []
+    for b in range(nbox):
+        shape = tuple(sizes[int(rng.uniform() * len(sizes))] for _ in range(3))
+        rate = 10.0 ** (-4.0 + 2.0 * rng.uniform())
+        p = strat_box(shape=shape, seed=seed * 1000 + b, heat_rate=rate)
+        p.name = "strat_box"
+        p.extra["box"] = b
+        p.extra["heat_rate"] = rate
+        out.append(p)
+    return out
+
+
 def tube(kind: str = "sod", n: int = 100, axis: int = 0, ntrans: int = 4,
          gamma: float = 1.4, length: float = 1.0) -> Problem:
     """Sod or Lax shock tube along `axis` on [0.5-L/2, 0.5+L/2] with n cells
