@@ -125,6 +125,27 @@ def _dist():
     return ws, rank, local
 
 
+def shard(n_items: int, rank: int, world: int):
+    """Independent units (ensemble boxes) owned by one rank: round robin, no
+    data-path communication between ranks."""
+    return [i for i in range(n_items) if i % world == rank]
+
+
+def reduce_max(x: float, dist=None, device="cpu") -> float:
+    """Slowest rank's time: the job's time."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job rate: units of all ranks over the slowest rank's time."""
+    return units_per_rank * world / seconds
+
+
 def _upload(ctx, p, torch, slab=64):
     import workloads
     nz = p.shape[2]
@@ -229,11 +250,7 @@ def run_ours(args):
             dist.barrier()
 
     def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(x, dist, "cuda")
 
     # ---------------- FP32 deviation form: the headline -----------------
     ctx = ppm.Context.from_problem(p, precision=ppm.FP32_DEVIATION, stream=stream, device=local)
@@ -258,7 +275,7 @@ def run_ours(args):
     passes = _time_passes(ctx, torch, stream, 0.5 * dt_now)
     tot, _, mach = ctx.diagnostics()
     ok_state = bool(np.isfinite(tot).all()) and 0.0 < mach < 1.0
-    value = 2.0 * ncell * args.steps * ws / t
+    value = job_throughput(2.0 * ncell * args.steps, ws, t)
     ms = 1e3 * t / args.steps
     # dominant kernel: the fused pass (6 of the 7 launches of a step; the
     # 7th is a one-thread dt kernel)
@@ -328,7 +345,7 @@ def run_ours(args):
     ens_out = None
     if not args.no_ensemble:
         boxes = workloads.ensemble_boxes(nbox=args.ens_boxes)
-        mine = [b for i, b in enumerate(boxes) if i % ws == rank]   # independent boxes shard over ranks
+        mine = [boxes[i] for i in shard(len(boxes), rank, ws)]   # independent boxes shard over ranks
         ens = ppm.Ensemble(mine, precision=ppm.FP32_DEVIATION, stream=stream, device=local)
         for i, bp in enumerate(mine):
             qs = workloads.initial_state(bp, device="cuda")

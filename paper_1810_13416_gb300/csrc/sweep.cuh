@@ -994,18 +994,20 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
             outc[6 + t1d] = o1;
             outc[6 + t2d] = o2;
             if constexpr (VEC) {
-                // stage 8 cells, then one whole 32-byte sector per variable
-                float *st = outv + (size_t)tid * 8 + (i & 7);
+                // stage 8 cells ([var][cell][thread]: conflict-free), then one
+                // whole 32-byte sector per variable
+                float *st = outv + (size_t)(i & 7) * SWEEP_NB + tid;
 #pragma unroll
                 for (int vv = 0; vv < 9; ++vv) st[vv * SWEEP_NB * 8] = outc[vv];
                 if ((i & 7) == 7) {
-                    const float4 *sv = reinterpret_cast<const float4 *>(outv) + (size_t)tid * 2;
                     float *g = reinterpret_cast<float *>(q) + (i - 7);
+                    const float *sv = outv + tid;
 #pragma unroll
                     for (int vv = 0; vv < 9; ++vv) {
+                        const float *r = sv + vv * SWEEP_NB * 8;
                         float4 *d = reinterpret_cast<float4 *>(g + vv * vs);
-                        d[0] = sv[vv * SWEEP_NB * 2];
-                        d[1] = sv[vv * SWEEP_NB * 2 + 1];
+                        d[0] = make_float4(r[0], r[SWEEP_NB], r[2 * SWEEP_NB], r[3 * SWEEP_NB]);
+                        d[1] = make_float4(r[4 * SWEEP_NB], r[5 * SWEEP_NB], r[6 * SWEEP_NB], r[7 * SWEEP_NB]);
                     }
                 }
             } else {
