@@ -56,15 +56,17 @@ def _src_hash() -> str:
 
 
 def _traffic_per_cell(prec: str):
-    """DRAM bytes per cell and pass of the sweep kernel from the committed ncu
-    summary, or None when absent or taken on a different kernel source."""
+    """DRAM bytes per cell and pass of the sweep kernel, averaged over the six
+    passes of a double step (two x passes, four y/z passes), from the
+    committed ncu summary; None when absent or taken on another kernel source."""
     try:
         with open(TRAFFIC_JSON) as f:
             d = json.load(f)
         e = d[prec]
         if e.get("sweep_src_sha256_16") != _src_hash():
             return None
-        return float(e["dram_bytes_per_cell_pass"])
+        b = e["dram_bytes_per_cell_pass"]
+        return (2.0 * float(b["x"]) + 4.0 * float(b["yz"])) / 6.0
     except Exception:
         return None
 

@@ -494,12 +494,14 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
     R wp0[5], wr0[5];                          // base state at the cell
     R wg[5];                                   // gravity along the pass
     R wfs[5];                                  // stored (FP32: folded) FV
+    R wmn[5], wm1[5], wm2[5], wed[5];          // conserved momenta and E'
 #pragma unroll
     for (int s = 0; s < 5; ++s) {
         wrd[s] = wu[s] = wv[s] = ww[s] = wpd[s] = (R)0;
         wfv[s] = won[s] = wo1[s] = wo2[s] = (R)0;
         wro[s] = wr0[s] = wp0[s] = (R)1;
         wg[s] = wfs[s] = (R)0;
+        wmn[s] = wm1[s] = wm2[s] = wed[s] = (R)0;
     }
     // interface values of face (c-3)+1/2 (from the previous step)
     R afp[5] = {0, 0, 0, 0, 0};
@@ -590,6 +592,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
             wpd[s] = wpd[s + 1]; wfv[s] = wfv[s + 1]; won[s] = won[s + 1]; wo1[s] = wo1[s + 1];
             wo2[s] = wo2[s + 1]; wro[s] = wro[s + 1]; wp0[s] = wp0[s + 1]; wr0[s] = wr0[s + 1];
             wg[s] = wg[s + 1]; wfs[s] = wfs[s + 1];
+            wmn[s] = wmn[s + 1]; wm1[s] = wm1[s + 1]; wm2[s] = wm2[s + 1]; wed[s] = wed[s + 1];
         }
         wrd[4] = rd; wu[4] = u; wv[4] = v; ww[4] = w; wpd[4] = pd;
         if constexpr (F32) {
@@ -603,6 +606,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
         wo2[4] = raw[6 + t2d];
         wro[4] = rho; wp0[4] = b_p0; wr0[4] = b_rho0;
         wg[4] = sg * b_g;
+        wmn[4] = mn; wm1[4] = m1; wm2[4] = m2; wed[4] = ed;
 
         // ================= a2: interface values of face (c-2)+1/2 ==========
         R afn[5];
@@ -783,13 +787,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
         R rdn3, mnn3, m1n3, m2n3, edn3;
         {
             const R g = wg[1];
-            // conserved values of cell c-3, re-read from the ring / stash
-            bool fl3;
-            map_cell(c - 3, n, A.bc_lo, A.bc_hi, fl3);
-            const R mn3 = (fl3 ? (R)-1 : (R)1) * raw_at(c - 3, 1 + ax);
-            const R m13 = raw_at(c - 3, 1 + t1d);
-            const R m23 = raw_at(c - 3, 1 + t2d);
-            const R ed3 = PLAIN ? xsub(raw_at(c - 3, 4), xdiv(wp0[1], gm1)) : raw_at(c - 3, 4);
+            const R mn3 = wmn[1], m13 = wm1[1], m23 = wm2[1], ed3 = wed[1];
             if constexpr (F32) {
                 float s, e;
                 two_sum(Frc, -Frp, s, e);
