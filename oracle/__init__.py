@@ -68,6 +68,7 @@ def _load():
         lib.oracle_cfl_dt.restype = C.c_double
         lib.oracle_sweep_pencil.argtypes = [P, C.c_int, C.c_int, C.c_int, Q, Q, C.c_double, C.c_int]
         lib.oracle_diagnostics.argtypes = [P, Q, _DP, C.c_int, C.c_double, _DP, _DP]
+        lib.oracle_sweep_z_slab.argtypes = [P, Q, C.c_int, C.c_int, C.c_double, C.c_int]
         lib.oracle_counters.argtypes = [C.POINTER(C.c_longlong)]
         lib.oracle_reset_counters.argtypes = []
         lib.oracle_count_flops.argtypes = [P, Q, C.c_int, C.c_double, _DP]
@@ -144,6 +145,15 @@ class Oracle:
                                      (_DP * 9)(*[_ptr(a) for a in pin]),
                                      (_DP * 9)(*[_ptr(a) for a in out]), dt, int(sources))
         return out
+
+    def sweep_z_slab(self, qloc, k0: int, nzl: int, dt: float, sources: bool = False):
+        """z pass of global planes [k0, k0+nzl) given with 4 halo planes on
+        each side (qloc: 9 arrays of shape (nzl+8, ny, nx))."""
+        nx, ny, _ = self.problem.shape
+        for a in qloc:
+            assert a.shape == (nzl + 8, ny, nx) and a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+        self.lib.oracle_sweep_z_slab(C.byref(self.s), (_DP * 9)(*[_ptr(a) for a in qloc]), int(k0), int(nzl),
+                                     dt, int(sources))
 
     def diagnostics(self, q, nbins: int = 0, rmax: float = 1.0):
         tot = np.zeros(7)

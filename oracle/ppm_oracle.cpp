@@ -934,6 +934,79 @@ void oracle_sweep_pencil(const oracle_problem *pb, int axis, int ja, int jb, dou
     flush_counters(P);
 }
 
+void oracle_sweep_z_slab(const oracle_problem *pb, double *q[9], int k0, int nzl, double dt, int with_sources) {
+    const int axis = 2, n = pb->nz;
+    const int bl = pb->bc[4], bh = pb->bc[5];
+    const double gm1 = pb->gamma - 1.0;
+    const long long plane = (long long)pb->nx * pb->ny;
+    const int src = with_sources && has_sources(pb);
+#pragma omp parallel num_threads(g_threads > 0 ? g_threads : omp_get_max_threads())
+    {
+        Pencil<double> P;
+        P.alloc(nzl);
+        P.axis = axis;
+#pragma omp for schedule(static)
+        for (long long pidx = 0; pidx < plane; ++pidx) {
+            const int ja = (int)(pidx % pb->nx), jb = (int)(pidx / pb->nx);  // (x, y) of the z pencil
+            P.ja = ja;
+            P.jb = jb;
+            P.c_nonsmooth = P.c_flat = P.c_theta = P.c_fct = P.c_clamp = 0;
+            P.wall_lo = (k0 == 0 && bl == 1);
+            P.wall_hi = (k0 + nzl == n && bh == 1);
+            for (int i = -G; i < nzl + G; ++i) {
+                const int kg = k0 + i;                 // global plane
+                bool flip;
+                const int m = map_cell(kg, n, bl, bh, &flip);
+                double xyz[3];
+                cell_position<double>(pb, axis, m, ja, jb, xyz);
+                BasePoint<double> b = base_at<double>(pb, xyz);
+                const int k = Pencil<double>::at(i);
+                const long long c = (long long)(i + G) * plane + pidx;
+                P.rho0c[k] = b.rho0;
+                P.p0c[k] = b.p0;
+                P.gn[k] = flip ? -b.g[axis] : b.g[axis];
+                P.rd[k] = q[0][c] - b.rho0;
+                P.mn[k] = flip ? -q[3][c] : q[3][c];
+                P.mt1[k] = q[1][c];
+                P.mt2[k] = q[2][c];
+                P.ed[k] = q[4][c] - b.p0 / gm1;
+                P.fv[k] = q[5][c];
+                P.on[k] = flip ? -q[8][c] : q[8][c];
+                P.ot1[k] = q[6][c];
+                P.ot2[k] = q[7][c];
+            }
+            const double lo = origin(pb, axis);
+            for (int j = -G; j < nzl + G; ++j) {
+                const int Pf = map_face(k0 + j, n, bl, bh);
+                double xyz[3];
+                cell_position<double>(pb, axis, 0, ja, jb, xyz);
+                xyz[axis] = lo + (double)Pf * pb->dx;
+                BasePoint<double> b = base_at<double>(pb, xyz);
+                P.rho0f[Pencil<double>::at(j)] = b.rho0;
+                P.p0f[Pencil<double>::at(j)] = b.p0;
+            }
+            // sources need the global position of each updated cell
+            oracle_problem sub = *pb;
+            sub.z0 = pb->z0 + k0 * pb->dx;
+            pass(&sub, P, dt, src);
+            for (int i = 0; i < nzl; ++i) {
+                const int k = Pencil<double>::at(i);
+                const long long c = (long long)(i + G) * plane + pidx;
+                q[0][c] = P.rho0c[k] + P.rdn[k];
+                q[3][c] = P.mnn[k];
+                q[1][c] = P.mt1n[k];
+                q[2][c] = P.mt2n[k];
+                q[4][c] = P.p0c[k] / gm1 + P.edn[k];
+                q[5][c] = P.fvn[k];
+                q[8][c] = P.onn[k];
+                q[6][c] = P.ot1n[k];
+                q[7][c] = P.ot2n[k];
+            }
+            flush_counters(P);
+        }
+    }
+}
+
 void oracle_diagnostics(const oracle_problem *pb, double *const q[9], double totals[7], int nbins,
                         double rmax, double *profiles, double *max_mach) {
     const double gam = pb->gamma, gm1 = pb->gamma - 1.0;

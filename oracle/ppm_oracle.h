@@ -60,6 +60,15 @@ double oracle_cfl_dt(const oracle_problem *pb, double *const q[9], double cfl);
 void oracle_sweep_pencil(const oracle_problem *pb, int axis, int ja, int jb,
                          double *const in[9], double *out[9], double dt, int sources);
 
+/* One z pass of the slab of global planes [k0, k0+nzl) of the grid of pb,
+ * for a domain decomposition into z slabs: q[v] holds nx*ny*(nzl+8) values,
+ * plane 0 = global plane k0-4, i.e. 4 halo planes on each side filled by the
+ * caller (neighbours' planes, or the wrapped / mirrored planes of the global
+ * boundary, raw: normal components are flipped here as for any ghost).
+ * Only planes 4 .. 4+nzl-1 are updated.  With correct halos the result is
+ * identical to the same planes of oracle_sweep over the whole grid. */
+void oracle_sweep_z_slab(const oracle_problem *pb, double *q[9], int k0, int nzl, double dt, int sources);
+
 /* Conserved totals (x dV) M, Px, Py, Pz, E, sum rho*FV, sum FV; spherical
  * shell averages (nbins bins of width rmax/nbins; per bin rho, p, FV, |u|,
  * u_r^2, volume-weighted; empty bins 0); max Mach number. */
