@@ -145,6 +145,32 @@ __device__ __forceinline__ Base<R> base_at(const SweepArgs<R> &A, const R xyz[3]
     return b;
 }
 
+// The same base state from the three coordinates as scalars, with gravity
+// only along the pass axis ax (no per-axis array in the pass kernel).
+template <typename R>
+struct BaseAx {
+    R rho0, p0, g;
+};
+template <typename R>
+__device__ __forceinline__ BaseAx<R> base_along(const SweepArgs<R> &A, R x, R y, R z, int ax) {
+    BaseAx<R> b;
+    b.g = (R)0;
+    if (A.grav == 0) {
+        b.rho0 = A.rho0_c;
+        b.p0 = A.p0_c;
+    } else if (A.grav == 1) {
+        b.rho0 = lerp_tab(A, A.t_rho0, z);
+        b.p0 = lerp_tab(A, A.t_p0, z);
+        if (ax == 2) b.g = lerp_tab(A, A.t_g, z);
+    } else {
+        const R r = xsqrt(xadd(xadd(xmul(x, x), xmul(y, y)), xmul(z, z)));
+        b.rho0 = lerp_tab(A, A.t_rho0, r);
+        b.p0 = lerp_tab(A, A.t_p0, r);
+        if (r > (R)0) b.g = xmul(xdiv(lerp_tab(A, A.t_g, r), r), ax == 0 ? x : (ax == 1 ? y : z));
+    }
+    return b;
+}
+
 template <typename R>
 __device__ __forceinline__ R coord(const SweepArgs<R> &A, int d, int idx) {
     return xadd((R)A.org[d], xmul(xadd((R)idx, (R)0.5), (R)A.dx));
@@ -359,9 +385,19 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
     bool bad = false;
     if (active) {
     const int n = A.n;
-    const int ax = A.axis, t1d = (ax + 1) % 3, t2d = (ax + 2) % 3;
+    const int ax = VEC ? 0 : A.axis, t1d = (ax + 1) % 3, t2d = (ax + 2) % 3;
     R *__restrict__ q = A.q + (long long)lane * A.s_lane + (long long)blk * A.s_blk;
     const long long vs = A.vs, sa = A.s_axis;
+    // Cells are held in the pass frame: slot k of a cell is stored variable
+    // vslot(k) (normal momentum and moment first, then the two transverse
+    // ones in cyclic order), so that no per-cell array is indexed by the
+    // run-time axis.
+    const int pn = 1 + ax, p1 = 1 + t1d, p2 = 1 + t2d;
+    auto voff = [&](int k) -> long long {
+        const int v = (k == 1) ? pn : (k == 2) ? p1 : (k == 3) ? p2
+                    : (k == 6) ? pn + 5 : (k == 7) ? p1 + 5 : (k == 8) ? p2 + 5 : k;
+        return (long long)v * vs;
+    };
 
     const R gam = (R)A.gamma, gm1 = (R)(A.gamma - 1.0);
     const R kk = (R)((A.gamma + 1.0) / (2.0 * A.gamma));
@@ -371,23 +407,28 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
     const R dtdx = (R)(dtd / A.dx);
     const R hdt = (R)0.5 * dt;
 
-    // transverse position of this pencil
-    int ijk[3];
-    ijk[A.lane_dim] = lane;
-    ijk[A.blk_dim] = blk;
-    R xyz[3];
-    xyz[t1d] = coord(A, t1d, ijk[t1d]);
-    xyz[t2d] = coord(A, t2d, ijk[t2d]);
+    // transverse position of this pencil (the lane and block indices run
+    // over the two transverse axes)
+    const bool lane_t1 = (A.lane_dim == t1d);
+    const R xt1 = coord(A, t1d, lane_t1 ? lane : blk);
+    const R xt2 = coord(A, t2d, lane_t1 ? blk : lane);
+    // physical coordinates of a point at coordinate `along` on the pencil
+    auto point = [&](R along, R &x, R &y, R &z) {
+        x = (ax == 0) ? along : (t1d == 0 ? xt1 : xt2);
+        y = (ax == 1) ? along : (t1d == 1 ? xt1 : xt2);
+        z = (ax == 2) ? along : (t1d == 2 ? xt1 : xt2);
+    };
+    const R zt = (t1d == 2) ? xt1 : xt2;  // z of the pencil when ax != 2
     const R lo = (R)A.org[ax];
 
     // FP32 base state: squared transverse radius, and the base state of a
     // pencil on which it does not vary (plane-parallel gravity, x/y pass)
-    const float rt2 = F32 ? (float)(xyz[t1d] * xyz[t1d] + xyz[t2d] * xyz[t2d]) : 0.0f;
+    const float rt2 = F32 ? (float)(xt1 * xt1 + xt2 * xt2) : 0.0f;
     float4 bconst = make_float4(0.f, 0.f, 0.f, 0.f);
     if constexpr (F32) {
         if (A.grav == 0) bconst = make_float4((float)A.rho0_c, (float)A.p0_c, 0.f, 0.f);
         else if (A.grav == 1 && ax != 2) {
-            bconst = tab4(A.t4_base, A.ntab4, A.s4_0, A.inv_ds4, (float)xyz[2]);
+            bconst = tab4(A.t4_base, A.ntab4, A.s4_0, A.inv_ds4, (float)zt);
             bconst.z = 0.0f;  // vertical gravity has no component along x or y
         }
     }
@@ -435,11 +476,8 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
     }
 
     // per-thread stash of the 4 cells that serve as high-side ghosts
+    // (every entry is written before it is read, since n >= 4)
     R stash[4][9];
-#pragma unroll
-    for (int a_ = 0; a_ < 4; ++a_)
-#pragma unroll
-        for (int b_ = 0; b_ < 9; ++b_) stash[a_][b_] = (R)0;
     auto stash_index = [&](int cc) { return (A.bc_hi == 0) ? (cc - n) : (n + 3 - cc); };
 
     // prefetch rings (shared memory, private to each thread)
@@ -453,7 +491,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
             const R *src = q + (long long)mm * sa;
             R *dst = ring + ((cf + G) & (RING - 1)) * 9 * SWEEP_NB + tid;
 #pragma unroll
-            for (int v = 0; v < 9; ++v) cp_async<(int)sizeof(R)>(dst + v * SWEEP_NB, src + v * vs);
+            for (int v = 0; v < 9; ++v) cp_async<(int)sizeof(R)>(dst + v * SWEEP_NB, src + voff(v));
         }
         cp_commit();
     };
@@ -467,17 +505,6 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
             for (int v = 0; v < 9; ++v) cp_async<16>(dst + v * SWEEP_NB * 4, src + v * vs);
         }
         cp_commit();
-    };
-    // raw stored value of variable v of cell cc (still in the ring or stash)
-    auto raw_at = [&](int cc, int v) -> R {
-        if (cc >= n) return stash[stash_index(cc)][v];
-        if constexpr (VEC) {
-            const int sub = (cc + G) & 3;
-            const int idx = (cc < 0 && A.bc_lo == 1) ? 3 - sub : sub;
-            return ringv[((((cc + G) >> 2) & 3) * 9 * SWEEP_NB + tid) * 4 + idx + v * SWEEP_NB * 4];
-        } else {
-            return ring[((cc + G) & (RING - 1)) * 9 * SWEEP_NB + tid + v * SWEEP_NB];
-        }
     };
     if constexpr (VEC) {
         fetchg(0);
@@ -566,19 +593,19 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
             bool fln;
             cell_next = tab_issue(xcell32(map_cell(c + 1, n, A.bc_lo, A.bc_hi, fln)));
         } else {
-            R cx[3] = {xyz[0], xyz[1], xyz[2]};
-            cx[ax] = coord(A, ax, m);
-            const Base<R> b = base_at(A, cx);
+            R cx, cy, cz;
+            point(coord(A, ax, m), cx, cy, cz);
+            const BaseAx<R> b = base_along(A, cx, cy, cz, ax);
             b_rho0 = b.rho0;
             b_p0 = b.p0;
-            b_g = b.g[ax];
+            b_g = b.g;
         }
         const R sg = flip ? (R)-1 : (R)1;
         // rotate into the pass frame and subtract the base state
         const R rd = PLAIN ? xsub(raw[0], b_rho0) : raw[0];
-        const R mn = sg * raw[1 + ax];
-        const R m1 = raw[1 + t1d];
-        const R m2 = raw[1 + t2d];
+        const R mn = sg * raw[1];
+        const R m1 = raw[2];
+        const R m2 = raw[3];
         const R ed = PLAIN ? xsub(raw[4], xdiv(b_p0, gm1)) : raw[4];
         const R rho = b_rho0 + rd;
         const R rinv = (R)1 / rho;
@@ -601,9 +628,9 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
             wfv[4] = raw[5];
         }
         wfs[4] = raw[5];
-        won[4] = sg * raw[6 + ax];
-        wo1[4] = raw[6 + t1d];
-        wo2[4] = raw[6 + t2d];
+        won[4] = sg * raw[6];
+        wo1[4] = raw[7];
+        wo2[4] = raw[8];
         wro[4] = rho; wp0[4] = b_p0; wr0[4] = b_rho0;
         wg[4] = sg * b_g;
         wmn[4] = mn; wm1[4] = m1; wm2[4] = m2; wed[4] = ed;
@@ -721,9 +748,9 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
                 face_next = tab_issue(xface32(j + 1));
             } else {
                 const R xf = xadd(lo, xmul((R)map_face(j, n, A.bc_lo, A.bc_hi), (R)A.dx));
-                R fx[3] = {xyz[0], xyz[1], xyz[2]};
-                fx[ax] = xf;
-                const Base<R> bf = base_at(A, fx);
+                R fx, fy, fz;
+                point(xf, fx, fy, fz);
+                const BaseAx<R> bf = base_along(A, fx, fy, fz, ax);
                 r0 = bf.rho0;
                 p0 = bf.p0;
             }
@@ -940,22 +967,19 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
             o2 = rclamp(o2, -bnd, bnd);
 
             R rdo = rdn4, mno = mnn4, m1o = m1n4, m2o = m2n4, edo = edn4;
-            R cxo[3] = {xyz[0], xyz[1], xyz[2]};
-            if constexpr (F32)
-                cxo[ax] = xcell32(i);
-            else
-                cxo[ax] = coord(A, ax, i);
             if (A.sources) {
                 R heat = 0, kd = 0;
                 if constexpr (F32) {
-                    const float s = (A.grav == 1) ? (float)cxo[2] : fmaf((float)cxo[ax], (float)cxo[ax], rt2);
+                    const float xa = xcell32(i);
+                    const float s = (A.grav == 1) ? (ax == 2 ? xa : (float)zt) : fmaf(xa, xa, rt2);
                     const float4 hs = tab4(A.t4_src, A.ntab4, A.s4_0, A.inv_ds4, s);
                     heat = hs.x;
                     kd = hs.y;
                 } else {
-                    const R s = (A.grav == 1) ? cxo[2]
-                                              : xsqrt(xadd(xadd(xmul(cxo[0], cxo[0]), xmul(cxo[1], cxo[1])),
-                                                           xmul(cxo[2], cxo[2])));
+                    R cx, cy, cz;
+                    point(coord(A, ax, i), cx, cy, cz);
+                    const R s = (A.grav == 1) ? cz
+                                              : xsqrt(xadd(xadd(xmul(cx, cx), xmul(cy, cy)), xmul(cz, cz)));
                     if (A.t_heat) heat = lerp_tab(A, A.t_heat, s);
                     if (A.t_damp) kd = lerp_tab(A, A.t_damp, s);
                 }
@@ -983,14 +1007,14 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
             }
             R outc[9];
             outc[0] = PLAIN ? xadd(wr0[0], rdo) : rdo;
-            outc[1 + ax] = mno;
-            outc[1 + t1d] = m1o;
-            outc[1 + t2d] = m2o;
+            outc[1] = mno;
+            outc[2] = m1o;
+            outc[3] = m2o;
             outc[4] = PLAIN ? xadd(xdiv(wp0[0], gm1), edo) : edo;
             outc[5] = fvs;
-            outc[6 + ax] = onn;
-            outc[6 + t1d] = o1;
-            outc[6 + t2d] = o2;
+            outc[6] = onn;
+            outc[7] = o1;
+            outc[8] = o2;
             if constexpr (VEC) {
                 // stage 8 cells ([var][cell][thread]: conflict-free), then one
                 // whole 32-byte sector per variable
@@ -1011,7 +1035,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
             } else {
                 R *p = q + (long long)i * sa;
 #pragma unroll
-                for (int vv = 0; vv < 9; ++vv) p[vv * vs] = outc[vv];
+                for (int vv = 0; vv < 9; ++vv) p[voff(vv)] = outc[vv];
             }
         }
 
