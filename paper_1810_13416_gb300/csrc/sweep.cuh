@@ -198,9 +198,7 @@ __device__ __forceinline__ R smooth5(R am2, R am1, R a0, R ap1, R ap2, R scale) 
     const R S = rmax(rmax(rabs(d1m1), rabs(d10)), rmax(rmax(rabs(d2m), rabs(d20)), rabs(d2p)));
     const R fl = (R)1e-9 * scale;
     const R x = T - (R)0.5 * S - fl;
-    R w = (R)0;
-    if (x > (R)0) w = rmin((R)1, x / ((R)0.5 * S + fl));
-    return w;
+    return rclamp(x / ((R)0.5 * S + fl), (R)0, (R)1);
 }
 
 // a4: parabola of one variable; returns aL, aR, a6 (da = aR - aL).  The
@@ -212,23 +210,25 @@ __device__ __forceinline__ void parabola(R am, R a, R ap, R aL, R aR, R f, R w, 
         aL = aL + f * (a - aL);
         aR = aR + f * (a - aR);
     }
-    if (w > (R)0) {
-        R cL = rclamp(aL, rmin(am, a), rmax(am, a));
-        R cR = rclamp(aR, rmin(a, ap), rmax(a, ap));
-        if ((cR - a) * (a - cL) <= (R)0) {
-            cL = a;
-            cR = a;
-        } else {
-            const R da = cR - cL;
-            const R dm = a - (R)0.5 * (cL + cR);
-            const R d6 = da * da * (R)(1.0 / 6.0);
-            if (da * dm > d6)
-                cL = (R)3 * a - (R)2 * cR;
-            else if (-d6 > da * dm)
-                cR = (R)3 * a - (R)2 * cL;
-        }
-        aL = aL + w * (cL - aL);
-        aR = aR + w * (cR - aR);
+    // Constrained edges, evaluated without branches (non-smooth cells are
+    // scattered, so a branch would diverge in almost every warp); w = 0
+    // leaves aL, aR unchanged.
+    {
+        const R cL = rclamp(aL, rmin(am, a), rmax(am, a));
+        const R cR = rclamp(aR, rmin(a, ap), rmax(a, ap));
+        const bool ext = (cR - a) * (a - cL) <= (R)0;   // local extremum: flat
+        const R da = cR - cL;
+        const R dm = a - (R)0.5 * (cL + cR);
+        const R d6 = da * da * (R)(1.0 / 6.0);
+        const R x = da * dm;
+        const bool fixL = x > d6;                        // overshoot on the left
+        const bool fixR = !fixL && (-d6 > x);            // overshoot on the right
+        R nL = fixL ? (R)3 * a - (R)2 * cR : cL;
+        R nR = fixR ? (R)3 * a - (R)2 * cL : cR;
+        nL = ext ? a : nL;
+        nR = ext ? a : nR;
+        aL = aL + w * (nL - aL);
+        aR = aR + w * (nR - aR);
     }
     oL = aL;
     oR = aR;
@@ -841,20 +841,23 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
             const R a2 = (R)0.25 * (won[3] - won[1]);
             const R ep = (R)0.5 * mm + a2 * (R)(1.0 / 6.0);
             const R em = a2 * (R)(1.0 / 6.0) - (R)0.5 * mm;
+            // (selects, not branches: bound-limited profiles are scattered)
             R gmax = rmax(ep, em), gmin = rmin(ep, em);
-            if (a2 != (R)0) {
-                const R xv = -mm / ((R)2 * a2);
-                if (rabs(xv) < (R)0.5) {
-                    const R gv = mm * xv + a2 * (xv * xv - (R)(1.0 / 12.0));
-                    gmax = rmax(gmax, gv);
-                    gmin = rmin(gmin, gv);
-                }
+            {
+                const bool nz = (a2 != (R)0);
+                const R xv = -mm / ((R)2 * (nz ? a2 : (R)1));   // interior extremum
+                const R gv = mm * xv + a2 * (xv * xv - (R)(1.0 / 12.0));
+                const bool in = nz && (rabs(xv) < (R)0.5);
+                gmax = in ? rmax(gmax, gv) : gmax;
+                gmin = in ? rmin(gmin, gv) : gmin;
             }
             R th = (R)1;
             if constexpr (F32) {
                 const float omf = fv_complement(wfs[2]);
-                if (gmax > omf) th = rmin(th, omf / gmax);
-                if (-gmin > F) th = rmin(th, F / (-gmin));
+                const bool hi = gmax > omf, lo = -gmin > F;
+                const float t1 = omf / (hi ? gmax : 1.0f), t2 = F / (lo ? -gmin : 1.0f);
+                th = hi ? rmin(th, t1) : th;
+                th = lo ? rmin(th, t2) : th;
             } else {
                 if (F + gmax > (R)1) th = rmin(th, ((R)1 - F) / gmax);
                 if (F + gmin < (R)0) th = rmin(th, F / (-gmin));
