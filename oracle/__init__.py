@@ -38,6 +38,7 @@ class _Problem(C.Structure):
         ("ntab", C.c_int),
         ("s0", C.c_double), ("ds", C.c_double),
         ("rho0", _DP), ("p0", _DP), ("g", _DP), ("heat", _DP), ("damp", _DP),
+        ("confine_r", C.c_double),
     ]
 
 
@@ -114,6 +115,7 @@ class Oracle:
         s.rho0, s.p0, s.g = _ptr(rho0), _ptr(p0), _ptr(g)
         s.heat = _ptr(heat) if heat is not None else None
         s.damp = _ptr(damp) if damp is not None else None
+        s.confine_r = float(getattr(p, "confine_r", 0.0) or 0.0)
         self.s = s
         self.problem = p
 
@@ -150,6 +152,8 @@ class Oracle:
         """z pass of global planes [k0, k0+nzl) given with 4 halo planes on
         each side (qloc: 9 arrays of shape (nzl+8, ny, nx))."""
         nx, ny, _ = self.problem.shape
+        if self.s.confine_r > 0.0:
+            raise ValueError("sweep_z_slab: no confining sphere")
         for a in qloc:
             assert a.shape == (nzl + 8, ny, nx) and a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
         self.lib.oracle_sweep_z_slab(C.byref(self.s), (_DP * 9)(*[_ptr(a) for a in qloc]), int(k0), int(nzl),

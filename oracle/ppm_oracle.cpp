@@ -31,6 +31,8 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -142,30 +144,36 @@ R source_coord(const oracle_problem *pb, const R xyz[3]) {
 inline int extent(const oracle_problem *pb, int a) { return a == 0 ? pb->nx : (a == 1 ? pb->ny : pb->nz); }
 inline double origin(const oracle_problem *pb, int a) { return a == 0 ? pb->x0 : (a == 1 ? pb->y0 : pb->z0); }
 
-// Ghost-cell index mapping along a pencil (periodic wrap or mirror).
+// Ghost-cell index mapping along a pencil (periodic wrap or mirror).  A
+// pencil with walls at both ends and its mirror images repeat with period 2n,
+// so a ghost deeper than n cells (a short fluid run inside a confining
+// sphere) is an image of an image: same orientation, no flip.
 inline int map_cell(int i, int n, int bc_lo, int bc_hi, bool *flip) {
     *flip = false;
-    if (i < 0) {
-        if (bc_lo == 0) return i + n;
-        *flip = true;
-        return -1 - i;
+    if (i >= 0 && i < n) return i;
+    if ((i < 0 && bc_lo == 0) || (i >= n && bc_hi == 0)) {
+        int k = i % n;
+        return k < 0 ? k + n : k;
     }
-    if (i >= n) {
-        if (bc_hi == 0) return i - n;
-        *flip = true;
-        return 2 * n - 1 - i;
-    }
-    return i;
+    int k = i % (2 * n);
+    if (k < 0) k += 2 * n;
+    if (k < n) return k;
+    *flip = true;
+    return 2 * n - 1 - k;
 }
 
 // Position (in cells from the low boundary) of face j+1/2 after mapping
-// through the boundary conditions.
+// through the boundary conditions (same images as map_cell).
 inline int map_face(int j, int n, int bc_lo, int bc_hi) {
-    int P = j + 1;
-    if (P < 0) return bc_lo == 0 ? P + n : -P;
-    if (P > n) return bc_hi == 0 ? P - n : 2 * n - P;
-    if (P == n && bc_hi == 0) return 0;
-    return P;
+    const int P = j + 1;
+    if (P >= 0 && P <= n) return (P == n && bc_hi == 0) ? 0 : P;
+    if ((P < 0 && bc_lo == 0) || (P > n && bc_hi == 0)) {
+        int k = P % n;
+        return k < 0 ? k + n : k;
+    }
+    int k = P % (2 * n);
+    if (k < 0) k += 2 * n;
+    return k <= n ? k : 2 * n - k;
 }
 
 inline size_t cell_index(const oracle_problem *pb, int axis, int i, int ja, int jb) {
@@ -185,6 +193,44 @@ void cell_position(const oracle_problem *pb, int axis, int i, int ja, int jb, R 
     for (int d = 0; d < 3; ++d) xyz[d] = R(origin(pb, d)) + (R((double)ijk[d]) + R(0.5)) * R(pb->dx);
 }
 
+// Confining sphere (Sec. 3: the star sits inside an impenetrable, immovable
+// sphere inscribed in the cube): a cell is fluid when its centre lies
+// strictly inside the sphere of radius confine_r about the coordinate origin.
+inline bool fluid_cell(const oracle_problem *pb, const double xyz[3]) {
+    if (!(pb->confine_r > 0.0)) return true;
+    return xyz[0] * xyz[0] + xyz[1] * xyz[1] + xyz[2] * xyz[2] < pb->confine_r * pb->confine_r;
+}
+
+// The fluid cells of a pencil, [i0, i0 + n): the whole pencil without a
+// confining sphere.  A line meets a ball in one segment, so they are
+// contiguous (checked); false when the pencil has none.
+bool pencil_run(const oracle_problem *pb, int axis, int ja, int jb, int *i0, int *n) {
+    const int N = extent(pb, axis);
+    if (!(pb->confine_r > 0.0)) {
+        *i0 = 0;
+        *n = N;
+        return true;
+    }
+    int a = -1, b = -1, count = 0;
+    for (int i = 0; i < N; ++i) {
+        double xyz[3];
+        cell_position<double>(pb, axis, i, ja, jb, xyz);
+        if (fluid_cell(pb, xyz)) {
+            if (a < 0) a = i;
+            b = i + 1;
+            ++count;
+        }
+    }
+    if (a < 0) return false;
+    if (count != b - a) {
+        std::fprintf(stderr, "oracle: fluid cells of a pencil are not contiguous\n");
+        std::abort();
+    }
+    *i0 = a;
+    *n = b - a;
+    return true;
+}
+
 // --------------------------------------------------------------------------
 // One pencil: all per-cell and per-face arrays of one 1-D pass.
 // Cell i lives at [i+G] for i in [-G, n+G); face j+1/2 lives at [j+G].
@@ -194,6 +240,8 @@ enum { V_R = 0, V_U = 1, V_V = 2, V_W = 3, V_P = 4, NH = 5 };
 template <class R>
 struct Pencil {
     int n = 0, axis = 0, ja = 0, jb = 0;
+    int i0 = 0;                 // global index (along the pass) of local cell 0
+    bool confined = false;      // a fluid run inside a confining sphere: walls at both ends
     bool wall_lo = false, wall_hi = false;
     // conserved, deviation form, rotated frame (n = along the pass)
     std::vector<R> rd, mn, mt1, mt2, ed, fv, on, ot1, ot2;
@@ -237,14 +285,14 @@ struct Pencil {
 template <class R>
 void gather(const oracle_problem *pb, Pencil<R> &P, double *const q[9]) {
     const int a = P.axis, n = P.n;
-    const int bl = pb->bc[2 * a], bh = pb->bc[2 * a + 1];
+    const int bl = P.confined ? 1 : pb->bc[2 * a], bh = P.confined ? 1 : pb->bc[2 * a + 1];
     P.wall_lo = (bl == 1);
     P.wall_hi = (bh == 1);
     const R gm1 = R(pb->gamma - 1.0);
     const int t1 = (a + 1) % 3, t2 = (a + 2) % 3;
     for (int i = -G; i < n + G; ++i) {
         bool flip;
-        int m = map_cell(i, n, bl, bh, &flip);
+        int m = P.i0 + map_cell(i, n, bl, bh, &flip);
         size_t c = cell_index(pb, a, m, P.ja, P.jb);
         R xyz[3];
         cell_position(pb, a, m, P.ja, P.jb, xyz);
@@ -271,7 +319,7 @@ void gather(const oracle_problem *pb, Pencil<R> &P, double *const q[9]) {
         int Pf = map_face(j, n, bl, bh);
         R xyz[3];
         cell_position(pb, a, 0, P.ja, P.jb, xyz);
-        xyz[a] = lo + R((double)Pf) * R(pb->dx);
+        xyz[a] = lo + R((double)(P.i0 + Pf)) * R(pb->dx);
         BasePoint<R> b = base_at(pb, xyz);
         P.rho0f[Pencil<R>::at(j)] = b.rho0;
         P.p0f[Pencil<R>::at(j)] = b.p0;
@@ -733,7 +781,7 @@ void sources(const oracle_problem *pb, Pencil<R> &P, R dt) {
     for (int i = 0; i < P.n; ++i) {
         const int k = Pencil<R>::at(i);
         R xyz[3];
-        cell_position(pb, P.axis, i, P.ja, P.jb, xyz);
+        cell_position(pb, P.axis, P.i0 + i, P.ja, P.jb, xyz);
         const R s = source_coord(pb, xyz);
         if (pb->heat) P.edn[k] = P.edn[k] + dt * lerp_tab(pb, pb->heat, s);
         if (pb->damp) {
@@ -774,7 +822,7 @@ void scatter(const oracle_problem *pb, const Pencil<R> &P, double *q[9]) {
     const R gm1 = R(pb->gamma - 1.0);
     for (int i = 0; i < P.n; ++i) {
         const int k = Pencil<R>::at(i);
-        size_t c = cell_index(pb, a, i, P.ja, P.jb);
+        size_t c = cell_index(pb, a, P.i0 + i, P.ja, P.jb);
         q[0][c] = val(P.rho0c[k] + P.rdn[k]);
         q[1 + a][c] = val(P.mnn[k]);
         q[1 + t1][c] = val(P.mt1n[k]);
@@ -807,6 +855,8 @@ void sweep_all(const oracle_problem *pb, double *q[9], int axis, double dt, int 
         P.ja = (int)(p % na);
         P.jb = (int)(p / na);
         P.c_nonsmooth = P.c_flat = P.c_theta = P.c_fct = P.c_clamp = 0;
+        if (!pencil_run(pb, axis, P.ja, P.jb, &P.i0, &P.n)) return;
+        P.confined = pb->confine_r > 0.0;
         gather(pb, P, q);
         pass(pb, P, R(dt), with_sources);
         scatter(pb, P, q);
@@ -858,6 +908,7 @@ double oracle_cfl_dt(const oracle_problem *pb, double *const q[9], double cfl) {
         int i = (int)(c % pb->nx), j = (int)((c / pb->nx) % pb->ny), k = (int)(c / ((long long)pb->nx * pb->ny));
         double xyz[3];
         cell_position<double>(pb, 0, i, j, k, xyz);
+        if (!fluid_cell(pb, xyz)) continue;   // solid cells of a confining sphere
         BasePoint<double> b = base_at<double>(pb, xyz);
         double rho = q[0][c];
         double u = q[1][c] / rho, v = q[2][c] / rho, w = q[3][c] / rho;
@@ -873,24 +924,27 @@ double oracle_cfl_dt(const oracle_problem *pb, double *const q[9], double cfl) {
 
 void oracle_sweep_pencil(const oracle_problem *pb, int axis, int ja, int jb, double *const in[9],
                          double *out[9], double dt, int with_sources) {
-    // Build a one-pencil grid view: copy the pencil into a full-size scratch
-    // only along the pencil by indexing through a private problem whose
-    // transverse extents are those of the grid (positions must stay exact).
-    const int n = extent(pb, axis);
+    // The same pass on one pencil given as separate arrays (positions are
+    // those of pencil (ja, jb) of the grid); solid cells are copied through.
+    const int N = extent(pb, axis);
+    for (int v = 0; v < 9; ++v)
+        for (int i = 0; i < N; ++i) out[v][i] = in[v][i];
     Pencil<double> P;
-    P.alloc(n);
+    P.alloc(N);
     P.axis = axis;
     P.ja = ja;
     P.jb = jb;
-    // gather from the pencil arrays
-    const int bl = pb->bc[2 * axis], bh = pb->bc[2 * axis + 1];
+    if (!pencil_run(pb, axis, ja, jb, &P.i0, &P.n)) return;
+    P.confined = pb->confine_r > 0.0;
+    const int n = P.n;
+    const int bl = P.confined ? 1 : pb->bc[2 * axis], bh = P.confined ? 1 : pb->bc[2 * axis + 1];
     P.wall_lo = (bl == 1);
     P.wall_hi = (bh == 1);
     const double gm1 = pb->gamma - 1.0;
     const int t1 = (axis + 1) % 3, t2 = (axis + 2) % 3;
     for (int i = -G; i < n + G; ++i) {
         bool flip;
-        int m = map_cell(i, n, bl, bh, &flip);
+        const int m = P.i0 + map_cell(i, n, bl, bh, &flip);
         double xyz[3];
         cell_position<double>(pb, axis, m, ja, jb, xyz);
         BasePoint<double> b = base_at<double>(pb, xyz);
@@ -913,7 +967,7 @@ void oracle_sweep_pencil(const oracle_problem *pb, int axis, int ja, int jb, dou
         int Pf = map_face(j, n, bl, bh);
         double xyz[3];
         cell_position<double>(pb, axis, 0, ja, jb, xyz);
-        xyz[axis] = lo + (double)Pf * pb->dx;
+        xyz[axis] = lo + (double)(P.i0 + Pf) * pb->dx;
         BasePoint<double> b = base_at<double>(pb, xyz);
         P.rho0f[Pencil<double>::at(j)] = b.rho0;
         P.p0f[Pencil<double>::at(j)] = b.p0;
@@ -921,15 +975,16 @@ void oracle_sweep_pencil(const oracle_problem *pb, int axis, int ja, int jb, dou
     pass(pb, P, dt, with_sources && has_sources(pb));
     for (int i = 0; i < n; ++i) {
         const int k = Pencil<double>::at(i);
-        out[0][i] = P.rho0c[k] + P.rdn[k];
-        out[1 + axis][i] = P.mnn[k];
-        out[1 + t1][i] = P.mt1n[k];
-        out[1 + t2][i] = P.mt2n[k];
-        out[4][i] = P.p0c[k] / gm1 + P.edn[k];
-        out[5][i] = P.fvn[k];
-        out[6 + axis][i] = P.onn[k];
-        out[6 + t1][i] = P.ot1n[k];
-        out[6 + t2][i] = P.ot2n[k];
+        const int m = P.i0 + i;
+        out[0][m] = P.rho0c[k] + P.rdn[k];
+        out[1 + axis][m] = P.mnn[k];
+        out[1 + t1][m] = P.mt1n[k];
+        out[1 + t2][m] = P.mt2n[k];
+        out[4][m] = P.p0c[k] / gm1 + P.edn[k];
+        out[5][m] = P.fvn[k];
+        out[6 + axis][m] = P.onn[k];
+        out[6 + t1][m] = P.ot1n[k];
+        out[6 + t2][m] = P.ot2n[k];
     }
     flush_counters(P);
 }
@@ -985,10 +1040,8 @@ void oracle_sweep_z_slab(const oracle_problem *pb, double *q[9], int k0, int nzl
                 P.rho0f[Pencil<double>::at(j)] = b.rho0;
                 P.p0f[Pencil<double>::at(j)] = b.p0;
             }
-            // sources need the global position of each updated cell
-            oracle_problem sub = *pb;
-            sub.z0 = pb->z0 + k0 * pb->dx;
-            pass(&sub, P, dt, src);
+            P.i0 = k0;   // sources use the global position of each updated cell
+            pass(pb, P, dt, src);
             for (int i = 0; i < nzl; ++i) {
                 const int k = Pencil<double>::at(i);
                 const long long c = (long long)(i + G) * plane + pidx;
@@ -1085,6 +1138,8 @@ void oracle_count_flops(const oracle_problem *pb, double *const q[9], int axis, 
     for (long long p = 0; p < (long long)na * nb; ++p) {
         P.ja = (int)(p % na);
         P.jb = (int)(p / na);
+        if (!pencil_run(pb, axis, P.ja, P.jb, &P.i0, &P.n)) continue;
+        P.confined = pb->confine_r > 0.0;
         gather(pb, P, qc);
         Counted::flops = 0;
         Counted::selects = 0;

@@ -42,6 +42,11 @@ typedef struct {
     double s0, ds;
     const double *rho0, *p0, *g;   /* base density, pressure, signed acceleration along +s */
     const double *heat, *damp;     /* optional (NULL): heating rate, damping rate */
+    double confine_r;       /* > 0: confining sphere of this radius about the coordinate
+                               origin (Sec. 3); cells whose centre is not strictly inside
+                               are solid: never updated, not part of the CFL maximum, and
+                               every fluid run of a pencil has reflecting walls at its ends.
+                               Requires reflecting walls on all six cube faces. */
 } oracle_problem;
 
 /* One 1-D pass along axis (0=x,1=y,2=z) over the whole grid, in place.
@@ -60,7 +65,8 @@ double oracle_cfl_dt(const oracle_problem *pb, double *const q[9], double cfl);
 void oracle_sweep_pencil(const oracle_problem *pb, int axis, int ja, int jb,
                          double *const in[9], double *out[9], double dt, int sources);
 
-/* One z pass of the slab of global planes [k0, k0+nzl) of the grid of pb,
+/* One z pass of the slab of global planes [k0, k0+nzl) of the grid of pb
+ * (no confining sphere),
  * for a domain decomposition into z slabs: q[v] holds nx*ny*(nzl+8) values,
  * plane 0 = global plane k0-4, i.e. 4 halo planes on each side filled by the
  * caller (neighbours' planes, or the wrapped / mirrored planes of the global

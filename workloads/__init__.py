@@ -142,6 +142,7 @@ class Problem:
     steps: int = 20
     seed: int = 0
     extra: dict = field(default_factory=dict)
+    confine_r: float = 0.0  # > 0: confining sphere of this radius about the origin
 
     @property
     def ncell(self) -> int:
@@ -339,10 +340,16 @@ def strat_box(shape=(128, 128, 128), seed: int = 2810, g0: float = 1.25,
 def sphere(n: int = 1024, seed: int = 5810, xi_R: float = 3.0, gamma: float = 5.0 / 3.0,
            mach: float = 0.03, heat_rate: float = 1e-3, tau_damp: float = 2.0,
            mu_ratio: float = 1.0 / 1.3, r_if: float = 0.6, width: float = 0.01,
-           nmodes: int = 8, kmax: int = 6, shape=None) -> Problem:
+           nmodes: int = 8, kmax: int = 6, shape=None, confine: bool = False,
+           taper_cells=(6.0, 2.0)) -> Problem:
     """Sphere-in-cube on [-1,1]^3 (R=1): n=3 polytrope with xi(R)=xi_R so the
     cube corners (r=sqrt 3) stay inside the star; rho0=theta^3 s(r),
-    g = 4 theta'(xi)/alpha (alpha=R/xi_R), p0 re-integrated from the centre."""
+    g = 4 theta'(xi)/alpha (alpha=R/xi_R), p0 re-integrated from the centre.
+
+    confine=True: the star is enclosed in the sphere of radius 1 inscribed in
+    the cube, and gravity falls smoothly to zero between taper_cells[0] and
+    taper_cells[1] cells inside that sphere (cubic smoothstep in r), with p0
+    integrated against the tapered gravity so the base stays hydrostatic."""
     shape = tuple(shape) if shape is not None else (n, n, n)
     nx, ny, nz = shape
     L = 2.0
@@ -357,6 +364,10 @@ def sphere(n: int = 1024, seed: int = 5810, xi_R: float = 3.0, gamma: float = 5.
     scale = 1.0 - fv0 + fv0 * mu_ratio
     rho0 = th ** 3 * scale
     g = 4.0 * dth / alpha
+    if confine:
+        r_in, r_out = 1.0 - taper_cells[0] * dx, 1.0 - taper_cells[1] * dx
+        t = np.clip((r_out - r) / (r_out - r_in), 0.0, 1.0)
+        g = g * (t * t * (3.0 - 2.0 * t))
     p0 = _integrate_pressure(r, rho0, g, 1.0)
     heat = heat_rate * 0.25 * (1.0 + np.tanh((r - 0.25) / 0.01)) * (1.0 - np.tanh((r - 0.3) / 0.01))
     damp = (1.0 / tau_damp) * (0.5 * (1.0 - np.tanh((r - 0.2) / 0.01))
@@ -365,7 +376,7 @@ def sphere(n: int = 1024, seed: int = 5810, xi_R: float = 3.0, gamma: float = 5.
     return Problem("sphere", shape, (-1.0, -1.0, -1.0), dx, gamma, (BC_REFLECT,) * 6,
                    GRAV_CENTRAL, tab, cfl=0.7, steps=100, seed=seed,
                    extra=dict(mach=mach, r_if=r_if, width=width, mu_ratio=mu_ratio,
-                              nmodes=nmodes, kmax=kmax))
+                              nmodes=nmodes, kmax=kmax), confine_r=1.0 if confine else 0.0)
 
 
 def ensemble_boxes(nbox: int = 24, seed: int = 3810, sizes=tuple(range(48, 193, 16))) -> List[Problem]:
