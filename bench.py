@@ -343,6 +343,27 @@ def run_ours(args):
         del c64
         torch.cuda.empty_cache()
 
+    # ---------------- confining sphere (FP32, same grid) ------------------
+    conf = None
+    if not args.no_confined:
+        pc = workloads.sphere(n=n, confine=True)
+        cc = ppm.Context.from_problem(pc, precision=ppm.FP32_DEVIATION, stream=stream, device=local)
+        _upload(cc, pc, torch)
+        cc.cfl_dt(pc.cfl, fetch=False)
+        for _ in range(args.warmup):
+            cc.step(0.0)
+        barrier()
+        tc = max_over_ranks(_time_steps(cc, torch, stream, args.confined_steps))
+        nflu = math.pi / 6.0 * n ** 3   # fluid cells ~ volume of the inscribed sphere
+        conf = {"workload": f"star confined in the sphere inscribed in the {n}^3 cube, gravity tapered "
+                            f"to zero inside it, FP32", "cells": ncell,
+                "value": 2.0 * ncell * args.confined_steps * ws / tc, "unit": UNIT,
+                "fluid_cell_updates_per_s": 2.0 * nflu * args.confined_steps * ws / tc,
+                "ms_per_step": 1e3 * tc / args.confined_steps, "steps": args.confined_steps}
+        cc.close()
+        del cc
+        torch.cuda.empty_cache()
+
     # ---------------- batched ensemble of uneven boxes (FP32) -------------
     ens_out = None
     if not args.no_ensemble:
@@ -397,7 +418,8 @@ def run_ours(args):
                            "step": "Strang double step X Y Z [src] Z Y X [src] = 2 3-D steps",
                            "l2": "inputs larger than L2 (39 GB vs 129 MB); no flush"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clocks, "fp64": fp64, "ensemble": ens_out, "state_ok": ok_state}
+                "clocks": clocks, "fp64": fp64, "confined": conf, "ensemble": ens_out,
+                "state_ok": ok_state}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -419,6 +441,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-confined", action="store_true")
+    ap.add_argument("--confined-steps", type=int, default=3)
     ap.add_argument("--ens-boxes", type=int, default=24)
     args = ap.parse_args()
     if args.warmup < 3:

@@ -80,6 +80,16 @@ typedef struct {
     const double *damp;    /* optional: velocity damping rate on the gravity grid (NULL) */
     void *stream;          /* cudaStream_t to queue work on, or NULL for a private stream */
     int device;            /* CUDA device ordinal */
+    double confine_r;      /* > 0: confining sphere of this radius about the coordinate
+                              origin (Sec. 3: the star is enclosed in an impenetrable,
+                              immovable sphere inscribed in the cube).  A cell is fluid
+                              when its centre (x0 + (i+1/2) dx, ...) lies strictly inside,
+                              tested in FP64 as x*x + y*y + z*z < r*r.  Each pass updates
+                              every pencil's run of fluid cells with reflecting walls at its
+                              ends; solid cells are never read or written by a pass and are
+                              left out of the CFL maximum (diagnostics still sum them).  The
+                              tapered gravity of Sec. 3 is the caller's g table.  Needs
+                              PPM_BC_REFLECT on all six faces (else EINVAL); 0 = off. */
 } ppm_options;
 
 /* Create a context: nx, ny, nz >= 4; gamma > 1; bc[6] per face
@@ -111,15 +121,28 @@ int ppm_get_region(ppm_ctx *ctx, const int lo[3], const int hi[3], double *const
 int ppm_cfl_dt(ppm_ctx *ctx, double cfl, double *dt_out);
 
 /* One Strang double step (Sec. 1 / Sec. 4 directional splitting):
- * passes X Y Z [sources] Z Y X [sources], all with the same dt, as one CUDA
- * graph launch.  dt > 0 uses that value; dt <= 0 uses the device value from
+ * passes X Y Z [heating/damping] Z Y X [heating/damping, rotation increment],
+ * all with the same dt, as one CUDA graph launch.  dt > 0 uses that value; dt <= 0 uses the device value from
  * the last ppm_cfl_dt or, after a step, the CFL maximum fused into that
  * step's last pass (ESTATE if there is none).  Never waits for the device. */
 int ppm_step(ppm_ctx *ctx, double dt);
 
-/* One 1-D pass along axis (0=x, 1=y, 2=z) with time step dt > 0;
- * sources != 0 applies heating/damping after the pass. */
+/* One 1-D pass along axis (0=x, 1=y, 2=z) with time step dt > 0.
+ * sources (0..3, else EINVAL): bit 0 applies heating/damping after the
+ * pass, bit 1 the rotation increment of ppm_set_rotation. */
 int ppm_sweep(ppm_ctx *ctx, int axis, double dt, int sources);
+
+/* Rotation ramp (Sec. 3: a solid-body rotational flow is added gradually
+ * over the first several thousand steps, until the wanted rate is reached).
+ * Every ppm_step queued after this call adds, after its last X pass, the
+ * velocity domega * (-y, x, 0) (rotation about the z axis through the
+ * coordinate origin) to every fluid cell, E gaining the kinetic energy it
+ * adds: new momentum m + rho*du, new E = E + m.du + rho|du|^2/2; the device
+ * CFL maximum for the next step is then taken on the rotated state.  One
+ * extra kernel per step while domega != 0; call with 0 to end the ramp.
+ * ppm_sweep applies it with sources bit 1.  Host state only (no device
+ * work, no wait); EINVAL if not finite. */
+int ppm_set_rotation(ppm_ctx *ctx, double domega);
 
 /* FP64 reductions of the current state:
  * totals[7] = (M, Px, Py, Pz, E, sum rho*FV, sum FV), each times dx^3;

@@ -38,7 +38,7 @@ class _Problem(C.Structure):
         ("ntab", C.c_int),
         ("s0", C.c_double), ("ds", C.c_double),
         ("rho0", _DP), ("p0", _DP), ("g", _DP), ("heat", _DP), ("damp", _DP),
-        ("confine_r", C.c_double),
+        ("confine_r", C.c_double), ("domega", C.c_double),
     ]
 
 
@@ -116,6 +116,7 @@ class Oracle:
         s.heat = _ptr(heat) if heat is not None else None
         s.damp = _ptr(damp) if damp is not None else None
         s.confine_r = float(getattr(p, "confine_r", 0.0) or 0.0)
+        s.domega = 0.0
         self.s = s
         self.problem = p
 
@@ -126,7 +127,12 @@ class Oracle:
             assert a.size == n, (a.shape, n)
         return (_DP * 9)(*[_ptr(a) for a in q])
 
-    def sweep(self, q, axis: int, dt: float, sources: bool = False):
+    def set_rotation(self, domega: float):
+        """Rotation increment added once per double step (0 = none)."""
+        self.s.domega = float(domega)
+
+    def sweep(self, q, axis: int, dt: float, sources: int = 0):
+        """sources: 1 (or True) heating/damping, 2 rotation increment, 3 both."""
         self.lib.oracle_sweep(C.byref(self.s), self._q(q), axis, dt, int(sources))
 
     def double_step(self, q, dt: float):

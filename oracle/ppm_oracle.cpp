@@ -772,27 +772,51 @@ void ppb_update(const oracle_problem *pb, Pencil<R> &P, R dt) {
     }
 }
 
-// Heating and damping (applied after the Z pass of X Y Z and the X pass of
-// Z Y X): E' += dt*heat(s); velocities scaled by max(0, 1 - dt*damp(s)) with
-// the kinetic energy removed from E'.
+// Sources, after the pass update of each cell of the run.  flags & 1:
+// heating and damping (after the Z pass of X Y Z and the X pass of Z Y X):
+// E' += dt*heat(s); velocities scaled by max(0, 1 - dt*damp(s)) with the
+// kinetic energy removed from E'.  flags & 2: the rotation ramp of Sec. 3, a
+// solid-body flow added gradually: once per double step (after the X pass of
+// Z Y X) every fluid cell gains the velocity domega * (-y, x, 0) about the z
+// axis through the origin, E' gaining the kinetic energy this adds.
 template <class R>
-void sources(const oracle_problem *pb, Pencil<R> &P, R dt) {
-    if (!pb->heat && !pb->damp) return;
+void sources(const oracle_problem *pb, Pencil<R> &P, R dt, int flags) {
+    const bool heatdamp = (flags & 1) && (pb->heat || pb->damp);
+    const bool rotate = (flags & 2) && pb->domega != 0.0;
+    if (!heatdamp && !rotate) return;
+    const int a = P.axis, t1 = (a + 1) % 3, t2 = (a + 2) % 3;
     for (int i = 0; i < P.n; ++i) {
         const int k = Pencil<R>::at(i);
         R xyz[3];
         cell_position(pb, P.axis, P.i0 + i, P.ja, P.jb, xyz);
-        const R s = source_coord(pb, xyz);
-        if (pb->heat) P.edn[k] = P.edn[k] + dt * lerp_tab(pb, pb->heat, s);
-        if (pb->damp) {
-            const R kd = lerp_tab(pb, pb->damp, s);
-            const R f = Max(R(0.0), R(1.0) - dt * kd);
+        if (heatdamp) {
+            const R s = source_coord(pb, xyz);
+            if (pb->heat) P.edn[k] = P.edn[k] + dt * lerp_tab(pb, pb->heat, s);
+            if (pb->damp) {
+                const R kd = lerp_tab(pb, pb->damp, s);
+                const R f = Max(R(0.0), R(1.0) - dt * kd);
+                const R rho = P.rho0c[k] + P.rdn[k];
+                const R ke = R(0.5) * (P.mnn[k] * P.mnn[k] + (P.mt1n[k] * P.mt1n[k] + P.mt2n[k] * P.mt2n[k])) / rho;
+                P.mnn[k] = P.mnn[k] * f;
+                P.mt1n[k] = P.mt1n[k] * f;
+                P.mt2n[k] = P.mt2n[k] * f;
+                P.edn[k] = P.edn[k] - (R(1.0) - f * f) * ke;
+            }
+        }
+        if (rotate) {
             const R rho = P.rho0c[k] + P.rdn[k];
-            const R ke = R(0.5) * (P.mnn[k] * P.mnn[k] + (P.mt1n[k] * P.mt1n[k] + P.mt2n[k] * P.mt2n[k])) / rho;
-            P.mnn[k] = P.mnn[k] * f;
-            P.mt1n[k] = P.mt1n[k] * f;
-            P.mt2n[k] = P.mt2n[k] * f;
-            P.edn[k] = P.edn[k] - (R(1.0) - f * f) * ke;
+            const R w = R(pb->domega);
+            R du[3];
+            du[0] = -(w * xyz[1]);
+            du[1] = w * xyz[0];
+            du[2] = R(0.0);
+            const R dn = du[a], d1 = du[t1], d2 = du[t2];
+            const R dE = (P.mnn[k] * dn + (P.mt1n[k] * d1 + P.mt2n[k] * d2)) +
+                         R(0.5) * rho * (dn * dn + (d1 * d1 + d2 * d2));
+            P.mnn[k] = P.mnn[k] + rho * dn;
+            P.mt1n[k] = P.mt1n[k] + rho * d1;
+            P.mt2n[k] = P.mt2n[k] + rho * d2;
+            P.edn[k] = P.edn[k] + dE;
         }
     }
 }
@@ -812,7 +836,7 @@ void pass(const oracle_problem *pb, Pencil<R> &P, R dt, int with_sources) {
     ppb_fluxes(pb, P, dt);
     ppb_fct(P);
     ppb_update(pb, P, dt);
-    if (with_sources) sources(pb, P, dt);
+    if (with_sources) sources(pb, P, dt, with_sources);
 }
 
 // Step a1 inverse: back to full variables in the unrotated frame.
@@ -881,22 +905,27 @@ void sweep_all(const oracle_problem *pb, double *q[9], int axis, double dt, int 
 
 bool has_sources(const oracle_problem *pb) { return pb->heat || pb->damp; }
 
+// Source flags a pass actually applies: bit 0 heating/damping (when tables
+// exist), bit 1 the rotation increment (when domega != 0).
+int source_flags(const oracle_problem *pb, int requested) {
+    return ((requested & 1) && has_sources(pb) ? 1 : 0) | ((requested & 2) && pb->domega != 0.0 ? 2 : 0);
+}
+
 }  // namespace
 
 extern "C" {
 
 void oracle_sweep(const oracle_problem *pb, double *q[9], int axis, double dt, int with_sources) {
-    sweep_all<double>(pb, q, axis, dt, with_sources && has_sources(pb), true);
+    sweep_all<double>(pb, q, axis, dt, source_flags(pb, with_sources), true);
 }
 
 void oracle_double_step(const oracle_problem *pb, double *q[9], double dt) {
-    const int src = has_sources(pb) ? 1 : 0;
     oracle_sweep(pb, q, 0, dt, 0);
     oracle_sweep(pb, q, 1, dt, 0);
-    oracle_sweep(pb, q, 2, dt, src);
+    oracle_sweep(pb, q, 2, dt, 1);
     oracle_sweep(pb, q, 2, dt, 0);
     oracle_sweep(pb, q, 1, dt, 0);
-    oracle_sweep(pb, q, 0, dt, src);
+    oracle_sweep(pb, q, 0, dt, 1 | 2);
 }
 
 double oracle_cfl_dt(const oracle_problem *pb, double *const q[9], double cfl) {
@@ -972,7 +1001,7 @@ void oracle_sweep_pencil(const oracle_problem *pb, int axis, int ja, int jb, dou
         P.rho0f[Pencil<double>::at(j)] = b.rho0;
         P.p0f[Pencil<double>::at(j)] = b.p0;
     }
-    pass(pb, P, dt, with_sources && has_sources(pb));
+    pass(pb, P, dt, source_flags(pb, with_sources));
     for (int i = 0; i < n; ++i) {
         const int k = Pencil<double>::at(i);
         const int m = P.i0 + i;
@@ -994,7 +1023,7 @@ void oracle_sweep_z_slab(const oracle_problem *pb, double *q[9], int k0, int nzl
     const int bl = pb->bc[4], bh = pb->bc[5];
     const double gm1 = pb->gamma - 1.0;
     const long long plane = (long long)pb->nx * pb->ny;
-    const int src = with_sources && has_sources(pb);
+    const int src = source_flags(pb, with_sources);
 #pragma omp parallel num_threads(g_threads > 0 ? g_threads : omp_get_max_threads())
     {
         Pencil<double> P;

@@ -47,13 +47,16 @@ typedef struct {
                                are solid: never updated, not part of the CFL maximum, and
                                every fluid run of a pencil has reflecting walls at its ends.
                                Requires reflecting walls on all six cube faces. */
+    double domega;          /* rotation ramp (Sec. 3): velocity domega * (-y, x, 0) added to
+                               every fluid cell once per double step (0 = none) */
 } oracle_problem;
 
 /* One 1-D pass along axis (0=x,1=y,2=z) over the whole grid, in place.
- * sources != 0 applies heating/damping to every cell after the pass. */
+ * sources: bit 0 applies heating/damping to every updated cell after the
+ * pass, bit 1 the rotation increment domega. */
 void oracle_sweep(const oracle_problem *pb, double *q[9], int axis, double dt, int sources);
 
-/* One Strang double step: X Y Z [sources] Z Y X [sources], same dt. */
+/* One Strang double step: X Y Z [heat/damp] Z Y X [heat/damp, rotation], same dt. */
 void oracle_double_step(const oracle_problem *pb, double *q[9], double dt);
 
 /* dt = cfl * dx / max over cells of (max_d |u_d| + c). */

@@ -60,7 +60,7 @@ class _Gravity(C.Structure):
 class _Options(C.Structure):
     _fields_ = [("x0", C.c_double), ("y0", C.c_double), ("z0", C.c_double), ("dx", C.c_double),
                 ("precision", C.c_int), ("heat", _DP), ("damp", _DP), ("stream", C.c_void_p),
-                ("device", C.c_int)]
+                ("device", C.c_int), ("confine_r", C.c_double)]
 
 
 class _Box(C.Structure):
@@ -96,6 +96,7 @@ def _load():
     lib.ppm_cfl_dt.argtypes = [P, C.c_double, _DP]
     lib.ppm_step.argtypes = [P, C.c_double]
     lib.ppm_sweep.argtypes = [P, C.c_int, C.c_double, C.c_int]
+    lib.ppm_set_rotation.argtypes = [P, C.c_double]
     lib.ppm_diagnostics.argtypes = [P, _DP, C.c_int, C.c_double, _DP, _DP]
     lib.ppm_sync.argtypes = [P]
     lib.ppm_launch_count.argtypes = [P]
@@ -140,7 +141,7 @@ class Context:
 
     def __init__(self, shape, gamma: float, bc: Sequence[int], grav_kind: int, s0: float, ds: float,
                  rho0, p0, g, origin=(0.0, 0.0, 0.0), dx: float = 1.0, precision: int = FP32_DEVIATION,
-                 heat=None, damp=None, stream=None, device: int = 0):
+                 heat=None, damp=None, stream=None, device: int = 0, confine_r: float = 0.0):
         self.lib = _load()
         self.shape = tuple(int(v) for v in shape)
         self._keep = [_f64(rho0), _f64(p0), _f64(g)]
@@ -158,7 +159,7 @@ class Context:
         if stream is not None:
             sptr = int(getattr(stream, "cuda_stream", stream))
         opt = _Options(float(origin[0]), float(origin[1]), float(origin[2]), float(dx), int(precision),
-                       hp, dp, sptr, int(device))
+                       hp, dp, sptr, int(device), float(confine_r))
         h = C.c_void_p()
         rc = self.lib.ppm_create(C.byref(h), self.shape[0], self.shape[1], self.shape[2], float(gamma),
                                  (C.c_int * 6)(*[int(b) for b in bc]), C.byref(gr), C.byref(opt))
@@ -172,11 +173,12 @@ class Context:
     def from_problem(cls, p, precision: int = FP32_DEVIATION, stream=None, device: int = 0):
         """Build from any object with the fields of a problem description
         (shape, gamma, bc, grav, tables(s0, ds, rho0, p0, g, heat, damp),
-        origin, dx)."""
+        origin, dx, optional confine_r)."""
         t = p.tables
         return cls(p.shape, p.gamma, p.bc, p.grav, t.s0, t.ds, t.rho0, t.p0, t.g, origin=p.origin,
                    dx=p.dx, precision=precision, heat=getattr(t, "heat", None),
-                   damp=getattr(t, "damp", None), stream=stream, device=device)
+                   damp=getattr(t, "damp", None), stream=stream, device=device,
+                   confine_r=float(getattr(p, "confine_r", 0.0) or 0.0))
 
     # ------------------------------------------------------------------
     def _check(self, rc: int):
@@ -257,8 +259,13 @@ class Context:
     def step(self, dt: float = 0.0):
         self._check(self.lib.ppm_step(self.h, float(dt)))
 
-    def sweep(self, axis: int, dt: float, sources: bool = False):
-        self._check(self.lib.ppm_sweep(self.h, int(axis), float(dt), int(bool(sources))))
+    def sweep(self, axis: int, dt: float, sources: int = 0):
+        """sources: 1 (or True) heating/damping, 2 rotation increment, 3 both."""
+        self._check(self.lib.ppm_sweep(self.h, int(axis), float(dt), int(sources)))
+
+    def set_rotation(self, domega: float):
+        """Rotation increment added by each following double step (0 ends the ramp)."""
+        self._check(self.lib.ppm_set_rotation(self.h, float(domega)))
 
     def diagnostics(self, nbins: int = 0, rmax: float = 1.0):
         tot = np.zeros(7)

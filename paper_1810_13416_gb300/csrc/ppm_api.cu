@@ -62,6 +62,8 @@ struct ppm_ctx {
     int ntab;
     double s0, ds;
     double rho0c, p0c;         // uniform base (no gravity)
+    double confine_r;          // > 0: confining sphere about the coordinate origin
+    double domega;             // rotation increment per double step (0 = none)
     int has_heat, has_damp;
     int device;
     cudaStream_t stream;
@@ -145,7 +147,8 @@ SweepArgs<R> make_args(ppm_ctx *c, int axis) {
     a.ntab4 = c->ntab4;
     a.s4_0 = c->s4_0;
     a.inv_ds4 = c->inv_ds4;
-    a.vec_x = (std::is_same<R, float>::value && axis == 0 && (c->n[0] % 8) == 0) ? 1 : 0;
+    a.confine_r = c->confine_r;
+    a.vec_x = (std::is_same<R, float>::value && axis == 0 && (c->n[0] % 8) == 0 && !(c->confine_r > 0.0)) ? 1 : 0;
     a.rho0_c = (R)c->rho0c;
     a.p0_c = (R)c->p0c;
     a.s0 = c->s0;
@@ -278,6 +281,10 @@ __global__ void cfl_kernel(SweepArgs<R> A, const R *st, long long ncell, int nx,
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < ncell;
          t += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(t % nx), j = (int)((t / nx) % ny), k = (int)(t / ((long long)nx * ny));
+        if (A.confine_r > 0.0 &&
+            !fluid_point(cell_centre(A.org[0], A.dx, i), cell_centre(A.org[1], A.dx, j),
+                         cell_centre(A.org[2], A.dx, k), A.confine_r))
+            continue;  // solid cell of the confining sphere
         const Base<R> b = cell_base(A, i, j, k);
         const R rd = PLAIN ? xsub(st[t], b.rho0) : st[t];
         const R ed = PLAIN ? xsub(st[4 * ncell + t], xdiv(b.p0, gm1)) : st[4 * ncell + t];
@@ -291,6 +298,52 @@ __global__ void cfl_kernel(SweepArgs<R> A, const R *st, long long ncell, int nx,
         smax = rmax(smax, s);
     }
     block_max_atomic((double)smax, out);
+}
+
+// Rotation ramp (Sec. 3): every fluid cell gains the velocity
+// domega * (-y, x, 0) (about the z axis through the coordinate origin), E the
+// kinetic energy this adds (m.du + rho|du|^2/2, summed in x, y, z order); then,
+// unless smax_out is NULL, the max over fluid cells of (max_d |u_d| + c) of
+// the new state (the CFL maximum of the step, as the last pass would give).
+// Launched after the step's last pass only while an increment is set, so the
+// passes themselves carry none of it.
+template <typename R, bool PLAIN>
+__global__ void rotate_kernel(SweepArgs<R> A, R *st, long long ncell, int nx, int ny, double domega,
+                              unsigned long long *smax_out) {
+    const R gam = (R)A.gamma, gm1 = (R)(A.gamma - 1.0);
+    const R w = (R)domega;
+    R smax = 0;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < ncell;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(t % nx), j = (int)((t / nx) % ny), k = (int)(t / ((long long)nx * ny));
+        if (A.confine_r > 0.0 &&
+            !fluid_point(cell_centre(A.org[0], A.dx, i), cell_centre(A.org[1], A.dx, j),
+                         cell_centre(A.org[2], A.dx, k), A.confine_r))
+            continue;  // solid cell of the confining sphere
+        const Base<R> b = cell_base(A, i, j, k);
+        const R rho = PLAIN ? st[t] : b.rho0 + st[t];
+        R mx = st[ncell + t], my = st[2 * ncell + t];
+        const R mz = st[3 * ncell + t];
+        const R dux = -(w * coord(A, 1, j)), duy = w * coord(A, 0, i), duz = (R)0;
+        const R dE = (mx * dux + (my * duy + mz * duz)) + (R)0.5 * rho * (dux * dux + (duy * duy + duz * duz));
+        mx = mx + rho * dux;
+        my = my + rho * duy;
+        const R E = st[4 * ncell + t] + dE;
+        st[ncell + t] = mx;
+        st[2 * ncell + t] = my;
+        st[4 * ncell + t] = E;
+        if (smax_out) {
+            const R rd = PLAIN ? xsub(st[t], b.rho0) : st[t];
+            const R ed = PLAIN ? xsub(E, xdiv(b.p0, gm1)) : E;
+            const R rh = b.rho0 + rd;
+            const R ri = (R)1 / rh;
+            const R u = mx * ri, v = my * ri, ww = mz * ri;
+            const R ke = (R)0.5 * (mx * u + (my * v + mz * ww));
+            const R p = b.p0 + gm1 * (ed - ke);
+            smax = rmax(smax, rmax(rmax(rabs(u), rabs(v)), rabs(ww)) + rsq(gam * p * ri));
+        }
+    }
+    if (smax_out) block_max_atomic((double)smax, smax_out);
 }
 
 // FP64 diagnostics: totals and shell averages.  acc layout: [0..6] totals,
@@ -372,6 +425,25 @@ int grid_for(long long n, int block) {
     if (g < 1) g = 1;
     return (int)g;
 }
+
+static int launch_rotate(ppm_ctx *c, bool with_cfl) {
+    const int g = grid_for(c->ncell, 256);
+    unsigned long long *so = nullptr;
+    if (with_cfl) {
+        CK(c, cudaMemsetAsync(&c->ds_dev->smax, 0, sizeof(unsigned long long), c->stream));
+        so = &c->ds_dev->smax;
+    }
+    if (c->prec == PPM_FP32_DEVIATION)
+        rotate_kernel<float, false><<<g, 256, 0, c->stream>>>(make_args<float>(c, 0), (float *)c->state, c->ncell,
+                                                               c->n[0], c->n[1], c->domega, so);
+    else
+        rotate_kernel<double, true><<<g, 256, 0, c->stream>>>(make_args<double>(c, 0), (double *)c->state, c->ncell,
+                                                               c->n[0], c->n[1], c->domega, so);
+    c->launches++;
+    CK(c, cudaGetLastError());
+    return PPM_OK;
+}
+
 
 SweepArgs<double> args64(ppm_ctx *c) { return make_args<double>(c, 0); }
 
@@ -491,6 +563,12 @@ int ppm_create(ppm_ctx **out, int nx, int ny, int nz, double gamma, const int bc
     if (!(opt->dx > 0.0)) return fail(nullptr, PPM_EINVAL, "dx must be positive");
     if (grav->kind == PPM_GRAV_NONE && (opt->heat || opt->damp))
         return fail(nullptr, PPM_EINVAL, "heating/damping tables need a gravity coordinate (plane or central)");
+    if (!(opt->confine_r >= 0.0) || !std::isfinite(opt->confine_r))
+        return fail(nullptr, PPM_EINVAL, "confine_r must be finite and >= 0");
+    if (opt->confine_r > 0.0)
+        for (int f = 0; f < 6; ++f)
+            if (bc[f] != PPM_BC_REFLECT)
+                return fail(nullptr, PPM_EINVAL, "a confining sphere needs reflecting walls on all six faces");
 
     ppm_ctx *c = new ppm_ctx();
     c->n[0] = nx; c->n[1] = ny; c->n[2] = nz;
@@ -508,6 +586,7 @@ int ppm_create(ppm_ctx **out, int nx, int ny, int nz, double gamma, const int bc
     c->ds = grav->ds;
     c->has_heat = opt->heat != nullptr;
     c->has_damp = opt->damp != nullptr;
+    c->confine_r = opt->confine_r;
     c->device = opt->device;
 
     auto bail = [&](int code) {
@@ -724,6 +803,7 @@ int ppm_step(ppm_ctx *c, double dt) {
     CK(c, cudaGraphLaunch(c->gexec, c->stream));
     c->launches += 7;
     c->have_speed = true;
+    if (c->domega != 0.0) return launch_rotate(c, true);
     return PPM_OK;
 }
 
@@ -734,9 +814,18 @@ int ppm_sweep(ppm_ctx *c, int axis, double dt, int sources) {
     set_scalar_kernel<<<1, 32, 0, c->stream>>>(&c->ds_dev->dt, dt);
     c->launches++;
     CK(c, cudaGetLastError());
-    int r = launch_sweep(c, axis, sources && (c->has_heat || c->has_damp), 0);
+    if (sources < 0 || sources > 3) return fail(c, PPM_EINVAL, "sources must be 0..3");
+    int r = launch_sweep(c, axis, (sources & 1) && (c->has_heat || c->has_damp) ? 1 : 0, 0);
     c->have_speed = false;
+    if (r == PPM_OK && (sources & 2) && c->domega != 0.0) r = launch_rotate(c, false);
     return r;
+}
+
+int ppm_set_rotation(ppm_ctx *c, double domega) {
+    if (!c) return PPM_EINVAL;
+    if (!std::isfinite(domega)) return fail(c, PPM_EINVAL, "domega is not finite");
+    c->domega = domega;
+    return PPM_OK;
 }
 
 int ppm_diagnostics(ppm_ctx *c, double totals[7], int nbins, double rmax, double *profiles, double *max_mach) {

@@ -35,6 +35,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <climits>
 
 #include <type_traits>
 
@@ -69,6 +70,7 @@ struct SweepArgs {
     int ntab4;
     float s4_0, inv_ds4;
     int vec_x;            // x pass with 16-byte copies (n % 4 == 0)
+    double confine_r;     // > 0: confining sphere; each pencil updates its fluid run only
     double gamma;
     const double *dt;     // device time step
     int sources;          // apply heating/damping after the pass
@@ -257,27 +259,45 @@ __device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
     e = fmaf(a, b, -p);
 }
 
-// Map a ghost index onto the pencil (periodic wrap or mirror).
+// Map a ghost index onto the pencil (periodic wrap or mirror).  With walls
+// at both ends the pencil and its mirror images repeat with period 2n, so a
+// ghost deeper than n cells (a short fluid run inside a confining sphere) is
+// an image of an image: same orientation, no flip.
 __device__ __forceinline__ int map_cell(int i, int n, int bl, int bh, bool &flip) {
     flip = false;
-    if (i < 0) {
-        if (bl == 0) return i + n;
-        flip = true;
-        return -1 - i;
+    if (i >= 0 && i < n) return i;
+    if ((i < 0 && bl == 0) || (i >= n && bh == 0)) {
+        const int k = i % n;
+        return k < 0 ? k + n : k;
     }
-    if (i >= n) {
-        if (bh == 0) return i - n;
-        flip = true;
-        return 2 * n - 1 - i;
-    }
-    return i;
+    int k = i % (2 * n);
+    if (k < 0) k += 2 * n;
+    if (k < n) return k;
+    flip = true;
+    return 2 * n - 1 - k;
 }
+// Position (cells from the low end) of face j+1/2 after the same mapping.
 __device__ __forceinline__ int map_face(int j, int n, int bl, int bh) {
-    int P = j + 1;
-    if (P < 0) return bl == 0 ? P + n : -P;
-    if (P > n) return bh == 0 ? P - n : 2 * n - P;
-    if (P == n && bh == 0) return 0;
-    return P;
+    const int P = j + 1;
+    if (P >= 0 && P <= n) return (P == n && bh == 0) ? 0 : P;
+    if ((P < 0 && bl == 0) || (P > n && bh == 0)) {
+        const int k = P % n;
+        return k < 0 ? k + n : k;
+    }
+    int k = P % (2 * n);
+    if (k < 0) k += 2 * n;
+    return k <= n ? k : 2 * n - k;
+}
+
+// Confining sphere (Sec. 3): a cell is fluid when its centre lies strictly
+// inside the sphere of radius r about the coordinate origin.  Evaluated in
+// FP64 without contraction, with the centre at org + (idx + 1/2) dx and the
+// squares summed in x, y, z order, so every kernel classifies a cell alike.
+__device__ __forceinline__ double cell_centre(double org, double dx, int idx) {
+    return __dadd_rn(org, __dmul_rn(__dadd_rn((double)idx, 0.5), dx));
+}
+__device__ __forceinline__ bool fluid_point(double x, double y, double z, double r) {
+    return __dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z)) < __dmul_rn(r, r);
 }
 
 // ---------------------------------------------------------------------------
@@ -371,7 +391,7 @@ constexpr int SWEEP_UNROLL = PPM_SWEEP_UNROLL;  // unroll factor of the march lo
 // ---------------------------------------------------------------------------
 // One block of the pass: NB consecutive pencils (lane_block) of pencil row
 // blk.  Called by the single-grid kernel and by the work-list kernel.
-template <typename R, bool PLAIN, bool VEC, int NB>
+template <typename R, bool PLAIN, bool VEC, int NB, bool CONF = false>
 __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block, int blk,
                                            unsigned char *smem_raw) {
     constexpr int SWEEP_NB = NB;
@@ -380,13 +400,64 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
     const int tid = threadIdx.x;
     const int lane = lane_block * NB + threadIdx.x;
     // threads past the edge take part in the final warp reduction only
-    const bool active = (lane < A.nlane) && (blk < A.nblk);
+    bool active = (lane < A.nlane) && (blk < A.nblk);
     R smax_local = 0;
     bool bad = false;
-    if (active) {
-    const int n = A.n;
     const int ax = VEC ? 0 : A.axis, t1d = (ax + 1) % 3, t2d = (ax + 2) % 3;
-    R *__restrict__ q = A.q + (long long)lane * A.s_lane + (long long)blk * A.s_blk;
+    const bool lane_t1 = (A.lane_dim == t1d);
+    // The cells this pencil updates: [i0, i0 + n) with boundary kinds bcl,
+    // bch.  Without a confining sphere that is the whole pencil; with one, it
+    // is the pencil's run of fluid cells (a line meets a ball in one segment,
+    // and the fluid test is monotone in the distance from the cell nearest
+    // the centre), found by bisection on each side, with walls at both ends.
+    int i0 = 0, n = A.n, bcl = A.bc_lo, bch = A.bc_hi;
+    if (CONF && active) {
+        const double c1 = cell_centre(A.org[t1d], A.dx, lane_t1 ? lane : blk);
+        const double c2 = cell_centre(A.org[t2d], A.dx, lane_t1 ? blk : lane);
+        auto inside = [&](int i) {
+            const double ca = cell_centre(A.org[ax], A.dx, i);
+            const double x = (ax == 0) ? ca : (t1d == 0 ? c1 : c2);
+            const double y = (ax == 1) ? ca : (t1d == 1 ? c1 : c2);
+            const double z = (ax == 2) ? ca : (t1d == 2 ? c1 : c2);
+            return fluid_point(x, y, z, A.confine_r);
+        };
+        const int N = A.n;
+        int ic = min(max((int)floor(-A.org[ax] / A.dx), 0), N - 1);
+        if (!inside(ic)) {  // (a neighbour at the same distance up to rounding)
+            if (ic > 0 && inside(ic - 1)) --ic;
+            else if (ic + 1 < N && inside(ic + 1)) ++ic;
+        }
+        if (!inside(ic)) {
+            active = false;
+        } else {
+            int lo = 0, hi = ic;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (inside(mid)) hi = mid; else lo = mid + 1;
+            }
+            i0 = lo;
+            lo = ic;
+            hi = N - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (inside(mid)) lo = mid; else hi = mid - 1;
+            }
+            n = lo + 1 - i0;
+            bcl = bch = 1;
+        }
+    }
+    // The lanes of a warp march over the same global cell index, each
+    // taking part while it is inside its own run (plus ghosts), so that
+    // their loads and stores stay coalesced when the runs start at
+    // different cells.  Without a confining sphere every lane has the
+    // whole pencil and this is the plain march.
+    int w_lo = 0, w_hi = n;
+    if constexpr (CONF) {
+        w_lo = __reduce_min_sync(0xffffffffu, active ? i0 : INT_MAX);
+        w_hi = __reduce_max_sync(0xffffffffu, active ? i0 + n : INT_MIN);
+    }
+    if (active) {
+    R *__restrict__ q = A.q + (long long)lane * A.s_lane + (long long)blk * A.s_blk + (long long)i0 * A.s_axis;
     const long long vs = A.vs, sa = A.s_axis;
     // Cells are held in the pass frame: slot k of a cell is stored variable
     // vslot(k) (normal momentum and moment first, then the two transverse
@@ -409,7 +480,6 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
 
     // transverse position of this pencil (the lane and block indices run
     // over the two transverse axes)
-    const bool lane_t1 = (A.lane_dim == t1d);
     const R xt1 = coord(A, t1d, lane_t1 ? lane : blk);
     const R xt2 = coord(A, t2d, lane_t1 ? blk : lane);
     // physical coordinates of a point at coordinate `along` on the pencil
@@ -466,19 +536,21 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
         if (A.grav == 2) r.z *= t.xa;  // (g/r) * x_axis
         return r;
     };
-    auto xcell32 = [&](int mm) { return orgf + ((float)mm + 0.5f) * dxf; };
-    auto xface32 = [&](int j) { return orgf + (float)map_face(j, n, A.bc_lo, A.bc_hi) * dxf; };
+    auto xcell32 = [&](int mm) { return orgf + ((float)(i0 + mm) + 0.5f) * dxf; };
+    auto xface32 = [&](int j) { return orgf + (float)(i0 + map_face(j, n, bcl, bch)) * dxf; };
     TabFetch cell_next, face_next;
     if constexpr (F32) {
         bool fl0;
-        cell_next = tab_issue(xcell32(map_cell(-G, n, A.bc_lo, A.bc_hi, fl0)));
+        cell_next = tab_issue(xcell32(map_cell(-G, n, bcl, bch, fl0)));
         face_next = tab_issue(xface32(-G - 3));
     }
 
     // per-thread stash of the 4 cells that serve as high-side ghosts
     // (every entry is written before it is read, since n >= 4)
     R stash[4][9];
-    auto stash_index = [&](int cc) { return (A.bc_hi == 0) ? (cc - n) : (n + 3 - cc); };
+    // stash slot of cell m: cells 0..3 (periodic) or the last four cells
+    // (walls; all cells of a run shorter than 4)
+    const int stash_lo = (bch == 0) ? 0 : max(0, n - 4);
 
     // prefetch rings (shared memory, private to each thread)
     R *ring = reinterpret_cast<R *>(smem_raw);
@@ -487,7 +559,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
     auto fetch = [&](int cf) {
         if (cf < n) {
             bool fl;
-            const int mm = map_cell(cf, n, A.bc_lo, A.bc_hi, fl);
+            const int mm = map_cell(cf, n, bcl, bch, fl);
             const R *src = q + (long long)mm * sa;
             R *dst = ring + ((cf + G) & (RING - 1)) * 9 * SWEEP_NB + tid;
 #pragma unroll
@@ -498,7 +570,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
     auto fetchg = [&](int g) {  // group of cells 4g-G .. 4g-G+3 (x pass, FP32)
         const int c0 = 4 * g - G;
         if (c0 < n) {
-            const int m0 = (c0 < 0) ? ((A.bc_lo == 0) ? n - 4 : 0) : c0;
+            const int m0 = (c0 < 0) ? ((bcl == 0) ? n - 4 : 0) : c0;
             const float *src = reinterpret_cast<const float *>(q) + m0;
             float *dst = ringv + (((g & 3) * 9) * SWEEP_NB + tid) * 4;
 #pragma unroll
@@ -546,7 +618,9 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
     R rdn4 = 0, mnn4 = 0, m1n4 = 0, m2n4 = 0, edn4 = 0;
 
 #pragma unroll SWEEP_UNROLL
-    for (int c = -G; c < n + G; ++c) {
+    for (int cg = w_lo - G; cg < w_hi + G; ++cg) {
+        const int c = CONF ? cg - i0 : cg;  // this lane's cell (index within its run)
+        if (CONF && (c < -G || c >= n + G)) continue;
         // ================= a1: load cell c ==================================
         if constexpr (VEC) {
             if (((c + G) & 3) == 0) {
@@ -559,15 +633,15 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
         }
         R raw[9];
         bool flip = false;
-        const int m = map_cell(c, n, A.bc_lo, A.bc_hi, flip);
+        const int m = map_cell(c, n, bcl, bch, flip);
         if (c >= n) {
-            const int si = stash_index(c);
+            const int si = m - stash_lo;
 #pragma unroll
             for (int v = 0; v < 9; ++v) raw[v] = stash[si][v];
         } else {
             if constexpr (VEC) {
                 const int sub = (c + G) & 3;
-                const int idx = (c < 0 && A.bc_lo == 1) ? 3 - sub : sub;
+                const int idx = (c < 0 && bcl == 1) ? 3 - sub : sub;
                 const float *src = ringv + ((((c + G) >> 2) & 3) * 9 * SWEEP_NB + tid) * 4 + idx;
 #pragma unroll
                 for (int v = 0; v < 9; ++v) raw[v] = src[v * SWEEP_NB * 4];
@@ -577,7 +651,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
                 for (int v = 0; v < 9; ++v) raw[v] = src[v * SWEEP_NB];
             }
             if (c >= 0) {
-                const int si = (A.bc_hi == 0) ? c : (c - (n - 4));
+                const int si = c - stash_lo;
                 if (si >= 0 && si < 4) {
 #pragma unroll
                     for (int v = 0; v < 9; ++v) stash[si][v] = raw[v];
@@ -591,10 +665,10 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
             b_p0 = bb.y;
             b_g = bb.z;
             bool fln;
-            cell_next = tab_issue(xcell32(map_cell(c + 1, n, A.bc_lo, A.bc_hi, fln)));
+            cell_next = tab_issue(xcell32(map_cell(c + 1, n, bcl, bch, fln)));
         } else {
             R cx, cy, cz;
-            point(coord(A, ax, m), cx, cy, cz);
+            point(coord(A, ax, i0 + m), cx, cy, cz);
             const BaseAx<R> b = base_along(A, cx, cy, cz, ax);
             b_rho0 = b.rho0;
             b_p0 = b.p0;
@@ -747,7 +821,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
                 p0 = bf.y;
                 face_next = tab_issue(xface32(j + 1));
             } else {
-                const R xf = xadd(lo, xmul((R)map_face(j, n, A.bc_lo, A.bc_hi), (R)A.dx));
+                const R xf = xadd(lo, xmul((R)(i0 + map_face(j, n, bcl, bch)), (R)A.dx));
                 R fx, fy, fz;
                 point(xf, fx, fy, fz);
                 const BaseAx<R> bf = base_along(A, fx, fy, fz, ax);
@@ -770,7 +844,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
             pst = pdL + WLi * (WRi * (uL - uR) + (pdR - pdL)) / den;
             ust = uL + (WRi * (uR - uL) + (pdL - pdR)) / den;
             if (p0 + pst < pfl) pst = pfl - p0;
-            if ((j == -1 && A.bc_lo == 1) || (j == n - 1 && A.bc_hi == 1)) ust = (R)0;
+            if ((j == -1 && bcl == 1) || (j == n - 1 && bch == 1)) ust = (R)0;
             const bool left = (ust >= (R)0);
             const R rds = left ? rdL : rdR;
             const R pds = left ? pdL : pdR;
@@ -980,7 +1054,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
                     kd = hs.y;
                 } else {
                     R cx, cy, cz;
-                    point(coord(A, ax, i), cx, cy, cz);
+                    point(coord(A, ax, i0 + i), cx, cy, cz);
                     const R s = (A.grav == 1) ? cz
                                               : xsqrt(xadd(xadd(xmul(cx, cx), xmul(cy, cy)), xmul(cz, cz)));
                     if (A.t_heat) heat = lerp_tab(A, A.t_heat, s);
@@ -1067,10 +1141,13 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
     }
 }
 
-template <typename R, bool PLAIN, bool VEC>
+// CONF: grid with a confining sphere (per-pencil fluid runs, lanes marching
+// on the global cell index); a separate instantiation so that the plain
+// grid's kernel carries none of it.
+template <typename R, bool PLAIN, bool VEC, bool CONF = false>
 __global__ void __launch_bounds__(SWEEP_NB, PPM_SWEEP_MINB) sweep_kernel(const SweepArgs<R> A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    sweep_body<R, PLAIN, VEC, SWEEP_NB>(A, blockIdx.x, blockIdx.y, smem_raw);
+    sweep_body<R, PLAIN, VEC, SWEEP_NB, CONF>(A, blockIdx.x, blockIdx.y, smem_raw);
 }
 
 // ---------------------------------------------------------------------------

@@ -3,11 +3,18 @@
 
 namespace ppm {
 cudaError_t prepare_sweep_f64() {
+    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<double, true, false, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         sweep_smem_bytes<double, false>());
+    if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(sweep_kernel<double, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 sweep_smem_bytes<double, false>());
 }
 
 void launch_sweep_f64(const SweepArgs<double> &a, dim3 grid, dim3 block, cudaStream_t st) {
-    sweep_kernel<double, true, false><<<grid, block, sweep_smem_bytes<double, false>(), st>>>(a);
+    if (a.confine_r > 0.0)
+        sweep_kernel<double, true, false, true><<<grid, block, sweep_smem_bytes<double, false>(), st>>>(a);
+    else
+        sweep_kernel<double, true, false><<<grid, block, sweep_smem_bytes<double, false>(), st>>>(a);
 }
 }  // namespace ppm

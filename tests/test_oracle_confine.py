@@ -160,3 +160,54 @@ def test_confined_pencil_entry_point_matches_grid_pass():
             out = o.sweep_pencil([a[npidx] for a in q], axis, ja, jb, dt, sources=True)
             for v in range(9):
                 assert np.array_equal(out[v], qa[v][npidx]), (axis, ja, jb, v)
+
+
+# --------------------------------------------------------------------------
+# Rotation ramp (Sec. 3): a solid-body flow added gradually, once per double
+# step, after the last X pass, to the fluid cells.
+def test_rotation_increment_closed_form():
+    """With dt = 0 the passes change nothing, so one double step adds exactly
+    the increment: m += rho*domega*(-y, x, 0), E += m.du + rho|du|^2/2, and
+    solid cells keep their values."""
+    p = _confined(16, sources=False)
+    q = workloads.build(p)
+    q0 = _copy(q)
+    o = oracle.Oracle(p)
+    w = 0.037
+    o.set_rotation(w)
+    o.double_step(q, 0.0)
+    nx, ny, nz = p.shape
+    x = p.origin[0] + (np.arange(nx) + 0.5) * p.dx
+    y = p.origin[1] + (np.arange(ny) + 0.5) * p.dx
+    Z, Y, X = np.meshgrid(np.zeros(nz), y, x, indexing="ij")
+    fluid = ~_solid(p)
+    rho = q0[0]
+    dux, duy = -w * Y, w * X
+    ex_mx = q0[1] + rho * dux
+    ex_my = q0[2] + rho * duy
+    ex_E = q0[4] + (q0[1] * dux + q0[2] * duy) + 0.5 * rho * (dux * dux + duy * duy)
+    scale = np.abs(rho * w).max()
+    assert np.abs(q[1] - np.where(fluid, ex_mx, q0[1])).max() <= 1e-14 * scale
+    assert np.abs(q[2] - np.where(fluid, ex_my, q0[2])).max() <= 1e-14 * scale
+    assert np.abs(q[4] - np.where(fluid, ex_E, q0[4])).max() <= 1e-14 * np.abs(q0[4]).max()
+    for v in (0, 3, 5, 6, 7, 8):
+        assert np.array_equal(q[v], q0[v]), v
+    # angular momentum about z grows by domega * sum rho (x^2 + y^2)
+    Lz = lambda s: (X * s[2] - Y * s[1])[fluid].sum()
+    dL = Lz(q) - Lz(q0)
+    assert abs(dL - w * (rho * (X * X + Y * Y))[fluid].sum()) <= 1e-12 * abs(dL)
+
+
+def test_rotation_only_in_the_last_x_pass():
+    """Single passes apply the increment only when asked (sources bit 1)."""
+    p = _confined(16, sources=False)
+    q = workloads.build(p)
+    o = oracle.Oracle(p)
+    o.set_rotation(0.02)
+    dt = o.cfl_dt(q)
+    qa, qb = _copy(q), _copy(q)
+    o.sweep(qa, 0, dt, sources=0)
+    o.set_rotation(0.0)
+    o.sweep(qb, 0, dt, sources=2)
+    for v in range(9):
+        assert np.array_equal(qa[v], qb[v]), v
