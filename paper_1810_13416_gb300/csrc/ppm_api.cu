@@ -355,21 +355,45 @@ __global__ void diag_kernel(SweepArgs<double> A64, const R *st, long long ncell,
     __shared__ double stot[7][32];
     for (int b = threadIdx.x; b < 6 * nbins; b += blockDim.x) sbin[b] = 0.0;
     __syncthreads();
-    const double gam = A64.gamma, gm1 = A64.gamma - 1.0;
+    // FP64 is slow on this part: per cell one square root (r, central
+    // gravity only) and two divisions; the table lookup multiplies by 1/ds
+    // and the Mach number is maximised as its square.  Results agree with
+    // the exact-lookup formulas to rounding.
+    const double gam = A64.gamma, gm1 = A64.gamma - 1.0, igm1 = 1.0 / gm1;
+    const double inv_ds = 1.0 / A64.ds;
+    const double *t_r = A64.t_rho0, *t_p = A64.t_p0;
     double tot[7] = {0, 0, 0, 0, 0, 0, 0};
-    double mmax = 0.0;
+    double m2max = 0.0;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < ncell;
          t += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(t % nx), j = (int)((t / nx) % ny), k = (int)(t / ((long long)nx * ny));
-        double xyz[3] = {coord(A64, 0, i), coord(A64, 1, j), coord(A64, 2, k)};
-        const Base<double> b = base_at(A64, xyz);
-        double rho, E;
+        const double x = coord(A64, 0, i), y = coord(A64, 1, j), z = coord(A64, 2, k);
+        double rho0, p0, r = -1.0;
+        if (A64.grav == 0) {
+            rho0 = A64.rho0_c;
+            p0 = A64.p0_c;
+        } else {
+            double sv = z;
+            if (A64.grav == 2) {
+                r = sqrt(x * x + y * y + z * z);
+                sv = r;
+            }
+            const double u = (sv - A64.s0) * inv_ds;
+            const double fl = fmin(fmax(floor(u), 0.0), (double)(A64.ntab - 2));
+            const int ii = (int)fl;
+            const double wt = u - fl;
+            rho0 = fma(wt, t_r[ii + 1] - t_r[ii], t_r[ii]);
+            p0 = fma(wt, t_p[ii + 1] - t_p[ii], t_p[ii]);
+        }
+        double rho, E, Ed;
         if (PLAIN) {
             rho = (double)st[t];
             E = (double)st[4 * ncell + t];
+            Ed = E - p0 * igm1;
         } else {
-            rho = b.rho0 + (double)st[t];
-            E = b.p0 / gm1 + (double)st[4 * ncell + t];
+            rho = rho0 + (double)st[t];
+            Ed = (double)st[4 * ncell + t];
+            E = p0 * igm1 + Ed;
         }
         const double mx = st[ncell + t], my = st[2 * ncell + t], mz = st[3 * ncell + t];
         double fv = st[5 * ncell + t];
@@ -381,17 +405,16 @@ __global__ void diag_kernel(SweepArgs<double> A64, const R *st, long long ncell,
         tot[4] += E;
         tot[5] += rho * fv;
         tot[6] += fv;
-        const double u = mx / rho, v = my / rho, w = mz / rho;
-        const double ke = 0.5 * (mx * u + my * v + mz * w);
-        const double p = b.p0 + gm1 * ((E - b.p0 / gm1) - ke);
-        const double cs = sqrt(gam * p / rho);
-        const double spd = sqrt(u * u + v * v + w * w);
-        mmax = fmax(mmax, spd / cs);
+        const double m2 = mx * mx + my * my + mz * mz;
+        const double rinv = 1.0 / rho;
+        const double p = p0 + gm1 * (Ed - 0.5 * m2 * rinv);
+        m2max = fmax(m2max, m2 / (gam * p * rho));   // |u|^2 / c^2
         if (nbins > 0) {
-            const double r = sqrt(xyz[0] * xyz[0] + xyz[1] * xyz[1] + xyz[2] * xyz[2]);
+            if (r < 0.0) r = sqrt(x * x + y * y + z * z);
             const int bin = (int)floor(r / rmax_ * nbins);
             if (bin >= 0 && bin < nbins) {
-                const double ur = r > 0.0 ? (u * xyz[0] + v * xyz[1] + w * xyz[2]) / r : 0.0;
+                const double spd = sqrt(m2) * rinv;
+                const double ur = r > 0.0 ? (mx * x + my * y + mz * z) * rinv / r : 0.0;
                 double *a = sbin + 6 * bin;
                 atomicAdd(a + 0, 1.0);
                 atomicAdd(a + 1, rho);
@@ -416,7 +439,7 @@ __global__ void diag_kernel(SweepArgs<double> A64, const R *st, long long ncell,
     }
     for (int b = threadIdx.x; b < 6 * nbins; b += blockDim.x)
         if (sbin[b] != 0.0) atomicAdd(acc + 8 + b, sbin[b]);
-    block_max_atomic(mmax, reinterpret_cast<unsigned long long *>(acc + 7));
+    block_max_atomic(m2max, reinterpret_cast<unsigned long long *>(acc + 7));
 }
 
 int grid_for(long long n, int block) {
@@ -855,7 +878,7 @@ int ppm_diagnostics(ppm_ctx *c, double totals[7], int nbins, double rmax, double
         const double *a = &h[8 + 6 * b];
         for (int m = 0; m < 5; ++m) profiles[5 * b + m] = a[0] > 0.0 ? a[1 + m] / a[0] : 0.0;
     }
-    if (max_mach) *max_mach = h[7];
+    if (max_mach) *max_mach = std::sqrt(h[7]);   // the kernel maximises Mach^2
     return check_flags(c);
 }
 

@@ -200,7 +200,16 @@ __device__ __forceinline__ R smooth5(R am2, R am1, R a0, R ap1, R ap2, R scale) 
     const R S = rmax(rmax(rabs(d1m1), rabs(d10)), rmax(rmax(rabs(d2m), rabs(d20)), rabs(d2p)));
     const R fl = (R)1e-9 * scale;
     const R x = T - (R)0.5 * S - fl;
-    return rclamp(x / ((R)0.5 * S + fl), (R)0, (R)1);
+    if constexpr (std::is_same<R, float>::value) {
+        // FP32: no branch (non-smooth cells are scattered, so it would
+        // diverge in almost every warp)
+        return rclamp(x / ((R)0.5 * S + fl), (R)0, (R)1);
+    } else {
+        // FP64: keep the division (slow on this part) off the smooth path
+        R w = (R)0;
+        if (x > (R)0) w = rmin((R)1, x / ((R)0.5 * S + fl));
+        return w;
+    }
 }
 
 // a4: parabola of one variable; returns aL, aR, a6 (da = aR - aL).  The
@@ -915,15 +924,22 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
             const R a2 = (R)0.25 * (won[3] - won[1]);
             const R ep = (R)0.5 * mm + a2 * (R)(1.0 / 6.0);
             const R em = a2 * (R)(1.0 / 6.0) - (R)0.5 * mm;
-            // (selects, not branches: bound-limited profiles are scattered)
             R gmax = rmax(ep, em), gmin = rmin(ep, em);
-            {
+            if constexpr (F32) {
+                // selects, not branches: bound-limited profiles are scattered
                 const bool nz = (a2 != (R)0);
                 const R xv = -mm / ((R)2 * (nz ? a2 : (R)1));   // interior extremum
                 const R gv = mm * xv + a2 * (xv * xv - (R)(1.0 / 12.0));
                 const bool in = nz && (rabs(xv) < (R)0.5);
                 gmax = in ? rmax(gmax, gv) : gmax;
                 gmin = in ? rmin(gmin, gv) : gmin;
+            } else if (a2 != (R)0) {
+                const R xv = -mm / ((R)2 * a2);
+                if (rabs(xv) < (R)0.5) {
+                    const R gv = mm * xv + a2 * (xv * xv - (R)(1.0 / 12.0));
+                    gmax = rmax(gmax, gv);
+                    gmin = rmin(gmin, gv);
+                }
             }
             R th = (R)1;
             if constexpr (F32) {
