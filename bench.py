@@ -416,7 +416,7 @@ def run_ours(args):
                 "config": {"workload": f"sphere-in-cube {n}^3, FP32 base-state-deviation form, in place",
                            "cells": ncell, "state_bytes": 9 * 4 * ncell, "cfl": p.cfl,
                            "step": "Strang double step X Y Z [src] Z Y X [src] = 2 3-D steps",
-                           "l2": "inputs larger than L2 (39 GB vs 129 MB); no flush"},
+                           "l2": f"inputs larger than L2 ({9 * 4 * ncell / 1e9:.2f} GB vs 129 MB); no flush"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks, "fp64": fp64, "confined": conf, "ensemble": ens_out,
                 "state_ok": ok_state}
