@@ -38,7 +38,7 @@ class _Problem(C.Structure):
         ("ntab", C.c_int),
         ("s0", C.c_double), ("ds", C.c_double),
         ("rho0", _DP), ("p0", _DP), ("g", _DP), ("heat", _DP), ("damp", _DP),
-        ("confine_r", C.c_double), ("domega", C.c_double),
+        ("confine_r", C.c_double), ("domega", C.c_double), ("nmom", C.c_int),
     ]
 
 
@@ -62,7 +62,7 @@ def _load():
         build()
         lib = C.CDLL(_LIB)
         P = C.POINTER(_Problem)
-        Q = _DP * 9
+        Q = C.POINTER(_DP)
         lib.oracle_sweep.argtypes = [P, Q, C.c_int, C.c_double, C.c_int]
         lib.oracle_double_step.argtypes = [P, Q, C.c_double]
         lib.oracle_cfl_dt.argtypes = [P, Q, C.c_double]
@@ -117,15 +117,19 @@ class Oracle:
         s.damp = _ptr(damp) if damp is not None else None
         s.confine_r = float(getattr(p, "confine_r", 0.0) or 0.0)
         s.domega = 0.0
+        s.nmom = int(getattr(p, "nmom", 3) or 3)
+        if s.nmom not in (3, 9):
+            raise ValueError("nmom must be 3 or 9")
+        self.nvar = 15 if s.nmom == 9 else 9
         self.s = s
         self.problem = p
 
     def _q(self, q: Sequence[np.ndarray]):
-        assert len(q) == 9
+        assert len(q) == self.nvar, (len(q), self.nvar)
         n = self.problem.ncell
         for a in q:
             assert a.size == n, (a.shape, n)
-        return (_DP * 9)(*[_ptr(a) for a in q])
+        return (_DP * 15)(*[_ptr(a) for a in q])
 
     def set_rotation(self, domega: float):
         """Rotation increment added once per double step (0 = none)."""
@@ -146,20 +150,21 @@ class Oracle:
                      dt: float, sources: bool = False) -> List[np.ndarray]:
         n = self.problem.shape[axis]
         pin = [np.ascontiguousarray(a, dtype=np.float64) for a in pencil_in]
+        assert len(pin) == self.nvar
         for a in pin:
             assert a.size == n
-        out = [np.zeros(n) for _ in range(9)]
+        out = [np.zeros(n) for _ in range(self.nvar)]
         self.lib.oracle_sweep_pencil(C.byref(self.s), axis, ja, jb,
-                                     (_DP * 9)(*[_ptr(a) for a in pin]),
-                                     (_DP * 9)(*[_ptr(a) for a in out]), dt, int(sources))
+                                     (_DP * 15)(*[_ptr(a) for a in pin]),
+                                     (_DP * 15)(*[_ptr(a) for a in out]), dt, int(sources))
         return out
 
     def sweep_z_slab(self, qloc, k0: int, nzl: int, dt: float, sources: bool = False):
         """z pass of global planes [k0, k0+nzl) given with 4 halo planes on
         each side (qloc: 9 arrays of shape (nzl+8, ny, nx))."""
         nx, ny, _ = self.problem.shape
-        if self.s.confine_r > 0.0:
-            raise ValueError("sweep_z_slab: no confining sphere")
+        if self.s.confine_r > 0.0 or self.s.nmom == 9:
+            raise ValueError("sweep_z_slab: no confining sphere, first moments only")
         for a in qloc:
             assert a.shape == (nzl + 8, ny, nx) and a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
         self.lib.oracle_sweep_z_slab(C.byref(self.s), (_DP * 9)(*[_ptr(a) for a in qloc]), int(k0), int(nzl),

@@ -262,6 +262,11 @@ struct Pencil {
     std::vector<R> PHI, KM;                     // mass transfer and its first moment
     std::vector<R> Rp, Rm, Gf, Kf;              // FCT
     std::vector<R> fvn, onn, ot1n, ot2n;
+    // ten-value PPB (nmom == 9): second moments along the pass (qn) and across
+    // it (q1, q2), mixed moments across (c12) and with the pass axis (cn1, cn2)
+    bool ten = false;
+    std::vector<R> qn, q1, q2, c12, cn1, cn2, qnn, q1n, q2n, c12n, cn1n, cn2n;
+    std::vector<R> K2L, K2H, K2f, KM2, U1, U2, Q1, Q2, C12;
     long long c_nonsmooth = 0, c_flat = 0, c_theta = 0, c_fct = 0, c_clamp = 0;
 
     void alloc(int n_) {
@@ -270,7 +275,9 @@ struct Pencil {
         for (auto *v : {&rd, &mn, &mt1, &mt2, &ed, &fv, &on, &ot1, &ot2, &rho0c, &p0c, &gn,
                         &rho0f, &p0f, &rho, &cs, &c2, &pfull, &flat, &us, &ps, &Fr, &Fn, &Ft1,
                         &Ft2, &FE, &rdn, &mnn, &mt1n, &mt2n, &edn, &meff, &aeff, &GL, &GH, &KL,
-                        &KH, &T1, &T2, &PHI, &KM, &Rp, &Rm, &Gf, &Kf, &fvn, &onn, &ot1n, &ot2n})
+                        &KH, &T1, &T2, &PHI, &KM, &Rp, &Rm, &Gf, &Kf, &fvn, &onn, &ot1n, &ot2n,
+                        &qn, &q1, &q2, &c12, &cn1, &cn2, &qnn, &q1n, &q2n, &c12n, &cn1n, &cn2n,
+                        &K2L, &K2H, &K2f, &KM2, &U1, &U2, &Q1, &Q2, &C12})
             v->assign(m, R(0.0));
         for (int k = 0; k < NH; ++k) {
             for (auto *v : {&W[k], &af[k], &PL[k], &PR[k], &PD[k], &P6[k], &WL[k], &WR[k]})
@@ -311,6 +318,16 @@ void gather(const oracle_problem *pb, Pencil<R> &P, double *const q[9]) {
         P.on[k] = flip ? -R(q[6 + a][c]) : R(q[6 + a][c]);
         P.ot1[k] = R(q[6 + t1][c]);
         P.ot2[k] = R(q[6 + t2][c]);
+        if (P.ten) {
+            // q[9+d]: second moment along d; q[12+e]: mixed moment of the two
+            // axes other than e.  A mirror flips the moments odd in the normal.
+            P.qn[k] = R(q[9 + a][c]);
+            P.q1[k] = R(q[9 + t1][c]);
+            P.q2[k] = R(q[9 + t2][c]);
+            P.c12[k] = R(q[12 + a][c]);
+            P.cn1[k] = flip ? -R(q[12 + t2][c]) : R(q[12 + t2][c]);
+            P.cn2[k] = flip ? -R(q[12 + t1][c]) : R(q[12 + t1][c]);
+        }
         (void)sgn;
     }
     // base state at faces j+1/2, j in [-G, n+G-1]
@@ -772,6 +789,238 @@ void ppb_update(const oracle_problem *pb, Pencil<R> &P, R dt) {
     }
 }
 
+// --------------------------------------------------------------------------
+// Ten-value PPB (Sec. 1 and Sec. 4: the production form carries the average
+// and 9 moments of FV per cell, so that each 1-D pass has a purely local
+// parabola and constraints are almost never needed).  On the unit cell
+// (xi, eta, zeta in [-1/2, 1/2]) the sub-cell profile is
+//   f = FV + sum_d m_d P1(xi_d) + sum_d q_d P2(xi_d) + sum_{d<e} c_de xi_d xi_e,
+// P1 = xi, P2 = xi^2 - 1/12, with m_d = 12 int xi_d f, q_d = 180 int P2(xi_d) f,
+// c_de = 144 int xi_d xi_e f (the L2 projection on these polynomials).  In a
+// pass along xi (transverse eta, zeta) the profile integrated across is the
+// local parabola FV + m_n xi + q_n P2(xi); the eta-moment density along xi is
+// (m_1 + c_n1 xi)/12, the zeta one (m_2 + c_n2 xi)/12, and the P2(eta),
+// P2(zeta) and eta*zeta densities are the constants q_1/180, q_2/180,
+// c_12/144.  Pieces of content and of mass are moved rigidly as in the
+// four-value form, and every moment of the new cell is re-taken about its
+// centre, relative to the mass distribution to first order.
+// --------------------------------------------------------------------------
+
+// Step a9a': the local parabola along the pass, bound-limited (theta) as in
+// the four-value form, with the cell's own second moment as curvature.
+template <class R>
+void ppb10_profiles(Pencil<R> &P) {
+    for (int i = -G + 1; i <= P.n + G - 2; ++i) {
+        const int k = Pencil<R>::at(i);
+        const R F = P.fv[k], m = P.on[k], a2 = P.qn[k];
+        const R ep = R(0.5) * m + a2 * R(1.0 / 6.0);
+        const R em = a2 * R(1.0 / 6.0) - R(0.5) * m;
+        R gmax = Max(ep, em), gmin = Min(ep, em);
+        if (a2 != R(0.0)) {
+            const R xv = -m / (R(2.0) * a2);
+            if (Abs(xv) < R(0.5)) {
+                const R gv = m * xv + a2 * (xv * xv - R(1.0 / 12.0));
+                gmax = Max(gmax, gv);
+                gmin = Min(gmin, gv);
+            }
+        }
+        R th = R(1.0);
+        if (F + gmax > R(1.0)) th = Min(th, (R(1.0) - F) / gmax);
+        if (F + gmin < R(0.0)) th = Min(th, F / (-gmin));
+        if (i >= 0 && i < P.n && val(th) < 1.0) ++P.c_theta;
+        P.meff[k] = th * m;
+        P.aeff[k] = th * a2;
+    }
+}
+
+// Step a9b': transfers across face j+1/2 (signed, positive = to +x): the
+// four-value ones (content, first moments of content and mass about the
+// donor's centre) plus the second moments of content and mass about that
+// centre, the transverse first moments with their xi-moments, and the
+// transverse second and mixed moments (constant across the swept slab).
+template <class R>
+void ppb10_fluxes(const oracle_problem *pb, Pencil<R> &P, R dt) {
+    const R dtdx = dt / R(pb->dx);
+    for (int j = -G + 2; j <= P.n + G - 4; ++j) {
+        const int k = Pencil<R>::at(j);
+        const R sig = P.us[k] * dtdx;
+        const R phi = dtdx * P.Fr[k];
+        const bool fromleft = (sig >= R(0.0));
+        const int d = fromleft ? k : k + 1;
+        const R s = fromleft ? sig : -sig;
+        // means of xi^p over the swept slab [1/2 - s, 1/2] of a left donor
+        // (odd powers change sign for the slab [-1/2, -1/2 + s] of a right one)
+        R M1 = R(0.5) - R(0.5) * s;
+        const R M2 = R(0.25) - R(0.5) * s + s * s * R(1.0 / 3.0);
+        R M3 = R(0.125) - R(0.375) * s + R(0.5) * s * s - R(0.25) * s * s * s;
+        const R M4 = R(0.0625) - R(0.25) * s + R(0.5) * s * s - R(0.5) * s * s * s + R(0.2) * s * s * s * s;
+        if (!fromleft) {
+            M1 = -M1;
+            M3 = -M3;
+        }
+        const R F = P.fv[d], me = P.meff[d], ae = P.aeff[d];
+        const R phibar = F + me * M1 + ae * (M2 - R(1.0 / 12.0));
+        const R psibar = F * M1 + me * M2 + ae * (M3 - M1 * R(1.0 / 12.0));
+        const R chibar = F * M2 + me * M3 + ae * (M4 - M2 * R(1.0 / 12.0));
+        P.GL[k] = phi * F;
+        P.GH[k] = phi * phibar;
+        P.KL[k] = phi * F * M1;
+        P.KH[k] = phi * psibar;
+        P.K2L[k] = phi * F * M2;
+        P.K2H[k] = phi * chibar;
+        P.PHI[k] = phi;
+        P.KM[k] = phi * M1;
+        P.KM2[k] = phi * M2;
+        P.T1[k] = phi * (P.ot1[d] + P.cn1[d] * M1);
+        P.T2[k] = phi * (P.ot2[d] + P.cn2[d] * M1);
+        P.U1[k] = phi * (P.ot1[d] * M1 + P.cn1[d] * M2);
+        P.U2[k] = phi * (P.ot2[d] * M1 + P.cn2[d] * M2);
+        P.Q1[k] = phi * P.q1[d];
+        P.Q2[k] = phi * P.q2[d];
+        P.C12[k] = phi * P.c12[d];
+    }
+}
+
+// Step a9c': the same FCT; the limited second moment of content follows the
+// content with the same factor.
+template <class R>
+void ppb10_fct(Pencil<R> &P) {
+    ppb_fct(P);
+    for (int j = -1; j <= P.n - 1; ++j) {
+        const int k = Pencil<R>::at(j);
+        const R A = P.GH[k] - P.GL[k];
+        const R C = (A >= R(0.0)) ? Min(P.Rp[k + 1], P.Rm[k]) : Min(P.Rp[k], P.Rm[k + 1]);
+        P.K2f[k] = P.K2L[k] + C * (P.K2H[k] - P.K2L[k]);
+    }
+}
+
+// Step a9d': new FV and its nine moments.  Raw moments (about the new cell's
+// centre) of the staying piece (shifted by the mean face displacement) and of
+// the incoming pieces (shifted by their face's displacement); the old cell's
+// mass is uniform.  With rho = rho_bar (1 + r1 xi + ...) the content moments
+// relative to the mass give, to first order in the mass moments,
+//   rho m_n / 12   = C1 - FV R1,
+//   rho q_n / 180  = C2' - FV R2' - m_n R1 / 15      (C2', R2': P2-moments),
+//   rho c_n1 / 12  = Y1 - m_1 R1                      (Y1 = 12 int xi eta c),
+// and the transverse moments are conserved contents (rho m_1, rho q_1, ...).
+// All in difference form (X_new = X + (X dPhi - dQ)/rho_new), so a cell with
+// no transfer keeps its values bit for bit.  Then realisability bounds for a
+// profile in [0,1] with mean FV: |m| <= 6 FV(1-FV), -15 FV(1-FV)(1+FV) <= q
+// <= 15 FV(1-FV)(2-FV) (all content at the centre / at the two ends), and
+// |c| <= 36 FV(1-FV) (all content in one corner).
+template <class R>
+void ppb10_update(const oracle_problem *pb, Pencil<R> &P, R dt) {
+    const R dtdx = dt / R(pb->dx);
+    for (int i = 0; i < P.n; ++i) {
+        const int k = Pencil<R>::at(i);
+        const R rold = P.rho0c[k] + P.rd[k];
+        const R rnew = P.rho0c[k] + P.rdn[k];
+        const R sm = P.us[k - 1] * dtdx, sp = P.us[k] * dtdx;
+        const R cold = rold * P.fv[k];
+        // outgoing amounts and moments about this cell's centre; incoming
+        // moments about it after the move
+        R c_out = R(0.0), z_out = R(0.0), z2_out = R(0.0), z_in = R(0.0), z2_in = R(0.0);
+        R m_out = R(0.0), zr_out = R(0.0), zr2_out = R(0.0), zr_in = R(0.0), zr2_in = R(0.0);
+        R t1_out = R(0.0), u1_out = R(0.0), u1_in = R(0.0);
+        R t2_out = R(0.0), u2_out = R(0.0), u2_in = R(0.0);
+        if (sp >= R(0.0)) {
+            c_out = c_out + P.Gf[k];
+            z_out = z_out + P.Kf[k];
+            z2_out = z2_out + P.K2f[k];
+            m_out = m_out + P.PHI[k];
+            zr_out = zr_out + P.KM[k];
+            zr2_out = zr2_out + P.KM2[k];
+            t1_out = t1_out + P.T1[k];
+            u1_out = u1_out + P.U1[k];
+            t2_out = t2_out + P.T2[k];
+            u2_out = u2_out + P.U2[k];
+        } else {
+            const R h = sp + R(1.0);
+            z_in = z_in - (P.Kf[k] + P.Gf[k] * h);
+            z2_in = z2_in - (P.K2f[k] + R(2.0) * h * P.Kf[k] + h * h * P.Gf[k]);
+            zr_in = zr_in - (P.KM[k] + P.PHI[k] * h);
+            zr2_in = zr2_in - (P.KM2[k] + R(2.0) * h * P.KM[k] + h * h * P.PHI[k]);
+            u1_in = u1_in - (P.U1[k] + P.T1[k] * h);
+            u2_in = u2_in - (P.U2[k] + P.T2[k] * h);
+        }
+        if (sm >= R(0.0)) {
+            const R h = sm - R(1.0);
+            z_in = z_in + (P.Kf[k - 1] + P.Gf[k - 1] * h);
+            z2_in = z2_in + (P.K2f[k - 1] + R(2.0) * h * P.Kf[k - 1] + h * h * P.Gf[k - 1]);
+            zr_in = zr_in + (P.KM[k - 1] + P.PHI[k - 1] * h);
+            zr2_in = zr2_in + (P.KM2[k - 1] + R(2.0) * h * P.KM[k - 1] + h * h * P.PHI[k - 1]);
+            u1_in = u1_in + (P.U1[k - 1] + P.T1[k - 1] * h);
+            u2_in = u2_in + (P.U2[k - 1] + P.T2[k - 1] * h);
+        } else {
+            c_out = c_out - P.Gf[k - 1];
+            z_out = z_out - P.Kf[k - 1];
+            z2_out = z2_out - P.K2f[k - 1];
+            m_out = m_out - P.PHI[k - 1];
+            zr_out = zr_out - P.KM[k - 1];
+            zr2_out = zr2_out - P.KM2[k - 1];
+            t1_out = t1_out - P.T1[k - 1];
+            u1_out = u1_out - P.U1[k - 1];
+            t2_out = t2_out - P.T2[k - 1];
+            u2_out = u2_out - P.U2[k - 1];
+        }
+        const R sbar = R(0.5) * (sm + sp);
+        const R dPhi = P.PHI[k] - P.PHI[k - 1];
+        const R dG = P.Gf[k] - P.Gf[k - 1];
+        // staying content: amount S0, first moment S1 (about the old centre)
+        const R S0 = cold - c_out;
+        const R S1 = rold * P.on[k] * R(1.0 / 12.0) - z_out;
+        const R dZc = S0 * sbar + z_in - z_out;                                   // C1 change
+        const R dZc2 = R(2.0) * sbar * S1 + sbar * sbar * S0 + z2_in - z2_out;   // C2 change
+        const R Zr = (rold - m_out) * sbar + zr_in - zr_out;                      // R1 (old: 0)
+        const R Zr2 = R(-2.0) * sbar * zr_out + sbar * sbar * (rold - m_out) + zr2_in - zr2_out
+                      + (rold - rnew) * R(1.0 / 12.0);                            // R2' = R2 - rnew/12
+        const R fvn = Clamp(P.fv[k] + (P.fv[k] * dPhi - dG) / rnew, R(0.0), R(1.0));
+        R onn = P.on[k] + (P.on[k] * dPhi + R(12.0) * (dZc - fvn * Zr)) / rnew;
+        // P2-moment change of content: C2 change minus (content change)/12
+        const R dC2p = dZc2 + dG * R(1.0 / 12.0);
+        R qnn = P.qn[k] + (P.qn[k] * dPhi + R(180.0) * (dC2p - fvn * Zr2) - R(12.0) * onn * Zr) / rnew;
+        R o1 = P.ot1[k] + (P.ot1[k] * dPhi - (P.T1[k] - P.T1[k - 1])) / rnew;
+        R o2 = P.ot2[k] + (P.ot2[k] * dPhi - (P.T2[k] - P.T2[k - 1])) / rnew;
+        const R dY1 = (rold * P.ot1[k] - t1_out) * sbar + u1_in - u1_out;
+        const R dY2 = (rold * P.ot2[k] - t2_out) * sbar + u2_in - u2_out;
+        R cn1 = P.cn1[k] + (P.cn1[k] * dPhi + R(12.0) * (dY1 - o1 * Zr)) / rnew;
+        R cn2 = P.cn2[k] + (P.cn2[k] * dPhi + R(12.0) * (dY2 - o2 * Zr)) / rnew;
+        R q1 = P.q1[k] + (P.q1[k] * dPhi - (P.Q1[k] - P.Q1[k - 1])) / rnew;
+        R q2 = P.q2[k] + (P.q2[k] * dPhi - (P.Q2[k] - P.Q2[k - 1])) / rnew;
+        R c12 = P.c12[k] + (P.c12[k] * dPhi - (P.C12[k] - P.C12[k - 1])) / rnew;
+        const R g = fvn * (R(1.0) - fvn);
+        const R bm = R(6.0) * g, bc = R(36.0) * g;
+        const R qlo = R(-15.0) * g * (R(1.0) + fvn), qhi = R(15.0) * g * (R(2.0) - fvn);
+        bool clamped = false;
+        auto cl = [&](R &x, R lo, R hi) {
+            if (x < lo || x > hi) {
+                x = Clamp(x, lo, hi);
+                clamped = true;
+            }
+        };
+        cl(onn, -bm, bm);
+        cl(o1, -bm, bm);
+        cl(o2, -bm, bm);
+        cl(qnn, qlo, qhi);
+        cl(q1, qlo, qhi);
+        cl(q2, qlo, qhi);
+        cl(cn1, -bc, bc);
+        cl(cn2, -bc, bc);
+        cl(c12, -bc, bc);
+        if (clamped) ++P.c_clamp;
+        P.fvn[k] = fvn;
+        P.onn[k] = onn;
+        P.ot1n[k] = o1;
+        P.ot2n[k] = o2;
+        P.qnn[k] = qnn;
+        P.q1n[k] = q1;
+        P.q2n[k] = q2;
+        P.cn1n[k] = cn1;
+        P.cn2n[k] = cn2;
+        P.c12n[k] = c12;
+    }
+}
+
 // Sources, after the pass update of each cell of the run.  flags & 1:
 // heating and damping (after the Z pass of X Y Z and the X pass of Z Y X):
 // E' += dt*heat(s); velocities scaled by max(0, 1 - dt*damp(s)) with the
@@ -832,10 +1081,17 @@ void pass(const oracle_problem *pb, Pencil<R> &P, R dt, int with_sources) {
     trace(pb, P, dt);
     riemann_fluxes(pb, P);
     hydro_update(pb, P, dt);
-    ppb_profiles(P);
-    ppb_fluxes(pb, P, dt);
-    ppb_fct(P);
-    ppb_update(pb, P, dt);
+    if (P.ten) {
+        ppb10_profiles(P);
+        ppb10_fluxes(pb, P, dt);
+        ppb10_fct(P);
+        ppb10_update(pb, P, dt);
+    } else {
+        ppb_profiles(P);
+        ppb_fluxes(pb, P, dt);
+        ppb_fct(P);
+        ppb_update(pb, P, dt);
+    }
     if (with_sources) sources(pb, P, dt, with_sources);
 }
 
@@ -856,6 +1112,14 @@ void scatter(const oracle_problem *pb, const Pencil<R> &P, double *q[9]) {
         q[6 + a][c] = val(P.onn[k]);
         q[6 + t1][c] = val(P.ot1n[k]);
         q[6 + t2][c] = val(P.ot2n[k]);
+        if (P.ten) {
+            q[9 + a][c] = val(P.qnn[k]);
+            q[9 + t1][c] = val(P.q1n[k]);
+            q[9 + t2][c] = val(P.q2n[k]);
+            q[12 + a][c] = val(P.c12n[k]);
+            q[12 + t2][c] = val(P.cn1n[k]);
+            q[12 + t1][c] = val(P.cn2n[k]);
+        }
     }
 }
 
@@ -881,6 +1145,7 @@ void sweep_all(const oracle_problem *pb, double *q[9], int axis, double dt, int 
         P.c_nonsmooth = P.c_flat = P.c_theta = P.c_fct = P.c_clamp = 0;
         if (!pencil_run(pb, axis, P.ja, P.jb, &P.i0, &P.n)) return;
         P.confined = pb->confine_r > 0.0;
+        P.ten = pb->nmom == 9;
         gather(pb, P, q);
         pass(pb, P, R(dt), with_sources);
         scatter(pb, P, q);
@@ -956,13 +1221,15 @@ void oracle_sweep_pencil(const oracle_problem *pb, int axis, int ja, int jb, dou
     // The same pass on one pencil given as separate arrays (positions are
     // those of pencil (ja, jb) of the grid); solid cells are copied through.
     const int N = extent(pb, axis);
-    for (int v = 0; v < 9; ++v)
+    const int nv = pb->nmom == 9 ? 15 : 9;
+    for (int v = 0; v < nv; ++v)
         for (int i = 0; i < N; ++i) out[v][i] = in[v][i];
     Pencil<double> P;
     P.alloc(N);
     P.axis = axis;
     P.ja = ja;
     P.jb = jb;
+    P.ten = pb->nmom == 9;
     if (!pencil_run(pb, axis, ja, jb, &P.i0, &P.n)) return;
     P.confined = pb->confine_r > 0.0;
     const int n = P.n;
@@ -990,6 +1257,14 @@ void oracle_sweep_pencil(const oracle_problem *pb, int axis, int ja, int jb, dou
         P.on[k] = flip ? -in[6 + axis][m] : in[6 + axis][m];
         P.ot1[k] = in[6 + t1][m];
         P.ot2[k] = in[6 + t2][m];
+        if (P.ten) {
+            P.qn[k] = in[9 + axis][m];
+            P.q1[k] = in[9 + t1][m];
+            P.q2[k] = in[9 + t2][m];
+            P.c12[k] = in[12 + axis][m];
+            P.cn1[k] = flip ? -in[12 + t2][m] : in[12 + t2][m];
+            P.cn2[k] = flip ? -in[12 + t1][m] : in[12 + t1][m];
+        }
     }
     const double lo = origin(pb, axis);
     for (int j = -G; j < n + G; ++j) {
@@ -1014,6 +1289,14 @@ void oracle_sweep_pencil(const oracle_problem *pb, int axis, int ja, int jb, dou
         out[6 + axis][m] = P.onn[k];
         out[6 + t1][m] = P.ot1n[k];
         out[6 + t2][m] = P.ot2n[k];
+        if (P.ten) {
+            out[9 + axis][m] = P.qnn[k];
+            out[9 + t1][m] = P.q1n[k];
+            out[9 + t2][m] = P.q2n[k];
+            out[12 + axis][m] = P.c12n[k];
+            out[12 + t2][m] = P.cn1n[k];
+            out[12 + t1][m] = P.cn2n[k];
+        }
     }
     flush_counters(P);
 }
@@ -1149,9 +1432,10 @@ void oracle_reset_counters(void) {
 
 void oracle_count_flops(const oracle_problem *pb, double *const q[9], int axis, double dt, double out[2]) {
     const long long ncell = (long long)pb->nx * pb->ny * pb->nz;
-    std::vector<std::vector<double>> copy(9, std::vector<double>((size_t)ncell));
-    double *qc[9];
-    for (int v = 0; v < 9; ++v) {
+    const int nv = pb->nmom == 9 ? 15 : 9;
+    std::vector<std::vector<double>> copy(nv, std::vector<double>((size_t)ncell));
+    double *qc[15];
+    for (int v = 0; v < nv; ++v) {
         std::memcpy(copy[v].data(), q[v], sizeof(double) * (size_t)ncell);
         qc[v] = copy[v].data();
     }
@@ -1169,6 +1453,7 @@ void oracle_count_flops(const oracle_problem *pb, double *const q[9], int axis, 
         P.jb = (int)(p / na);
         if (!pencil_run(pb, axis, P.ja, P.jb, &P.i0, &P.n)) continue;
         P.confined = pb->confine_r > 0.0;
+        P.ten = pb->nmom == 9;
         gather(pb, P, qc);
         Counted::flops = 0;
         Counted::selects = 0;

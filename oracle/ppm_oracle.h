@@ -9,7 +9,7 @@
  *
  * Every function works on full (not base-subtracted) FP64 state arrays
  * q[9] = (rho, rho*u, rho*v, rho*w, E, FV, m_x, m_y, m_z), each nx*ny*nz with
- * x fastest.  Internally each 1-D pass gathers one pencil at a time, subtracts
+ * x fastest (q[15] with the second and mixed moments when nmom == 9).  Internally each 1-D pass gathers one pencil at a time, subtracts
  * the hydrostatic base state (Sec. 1, "subtract it out ... very carefully"),
  * runs the pass step by step on whole-pencil arrays, and scatters back.
  *
@@ -49,6 +49,10 @@ typedef struct {
                                Requires reflecting walls on all six cube faces. */
     double domega;          /* rotation ramp (Sec. 3): velocity domega * (-y, x, 0) added to
                                every fluid cell once per double step (0 = none) */
+    int nmom;               /* FV moments carried: 3 (or 0: first moments only, q[9]) or 9
+                               (the ten-value PPB of Sec. 1/4, q[15]: after the first moments
+                               q[9..11] = second moments along x, y, z and q[12..14] = the mixed
+                               moments yz, xz, xy) */
 } oracle_problem;
 
 /* One 1-D pass along axis (0=x,1=y,2=z) over the whole grid, in place.
