@@ -153,8 +153,10 @@ def _upload(ctx, p, torch, slab=64):
     nz = p.shape[2]
     for z0 in range(0, nz, slab):
         z1 = min(nz, z0 + slab)
-        qs = workloads.initial_state(p, device="cuda", z_lo=z0, z_hi=z1)
-        ctx.set_region((0, 0, z0), (p.shape[0], p.shape[1], z1), [t.contiguous() for t in qs], device=True)
+        qs = [t.contiguous() for t in workloads.initial_state(p, device="cuda", z_lo=z0, z_hi=z1)]
+        # ten-value PPB: second and mixed moments start at zero
+        qs += [torch.zeros_like(qs[0]) for _ in range(ctx.nvar - len(qs))]
+        ctx.set_region((0, 0, z0), (p.shape[0], p.shape[1], z1), qs, device=True)
         del qs
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
@@ -364,6 +366,27 @@ def run_ours(args):
         del cc
         torch.cuda.empty_cache()
 
+    # ---------------- ten-value PPB (FP32, same grid) ---------------------
+    ten = None
+    if not args.no_ppb10:
+        import copy as _copy
+        pt = _copy.copy(p)
+        pt.nmom = 9
+        ct = ppm.Context.from_problem(pt, precision=ppm.FP32_DEVIATION, stream=stream, device=local)
+        _upload(ct, pt, torch)
+        ct.cfl_dt(pt.cfl, fetch=False)
+        for _ in range(args.warmup):
+            ct.step(0.0)
+        barrier()
+        tt = max_over_ranks(_time_steps(ct, torch, stream, args.ppb10_steps))
+        ten = {"workload": f"sphere-in-cube {n}^3, FP32, FV with 9 moments (15 values per cell)",
+               "cells": ncell, "value": 2.0 * ncell * args.ppb10_steps * ws / tt, "unit": UNIT,
+               "ms_per_step": 1e3 * tt / args.ppb10_steps, "steps": args.ppb10_steps,
+               "algorithmic_bytes_per_cell_pass": 120}
+        ct.close()
+        del ct
+        torch.cuda.empty_cache()
+
     # ---------------- batched ensemble of uneven boxes (FP32) -------------
     ens_out = None
     if not args.no_ensemble:
@@ -418,7 +441,7 @@ def run_ours(args):
                            "step": "Strang double step X Y Z [src] Z Y X [src] = 2 3-D steps",
                            "l2": f"inputs larger than L2 ({9 * 4 * ncell / 1e9:.2f} GB vs 129 MB); no flush"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clocks, "fp64": fp64, "confined": conf, "ensemble": ens_out,
+                "clocks": clocks, "fp64": fp64, "confined": conf, "ppb10": ten, "ensemble": ens_out,
                 "state_ok": ok_state}
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -442,6 +465,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-confined", action="store_true")
+    ap.add_argument("--no-ppb10", action="store_true")
+    ap.add_argument("--ppb10-steps", type=int, default=3)
     ap.add_argument("--confined-steps", type=int, default=3)
     ap.add_argument("--ens-boxes", type=int, default=24)
     args = ap.parse_args()

@@ -18,6 +18,10 @@
  *     rho and E are full values (the base state is never subtracted in the
  *     caller's arrays).  FV is the volume fraction of the tracked fluid and
  *     m_d = 12 * integral over the cell of xi_d * FV (xi in [-1/2,1/2]).
+ *     With nmom = 9 (ten-value PPB) 15 arrays: q[9..11] = q_d = 180 *
+ *     integral of (xi_d^2 - 1/12) FV, q[12..14] = 144 * integral of
+ *     (xi_y xi_z, xi_x xi_z, xi_x xi_y) FV.  The q[] parameters below have
+ *     6 + nmom entries.
  *   - Memory: the library owns all device memory; caller arrays are read or
  *     written only during the call and never retained.  Host pointers may
  *     be pageable or pinned.
@@ -90,6 +94,11 @@ typedef struct {
                               left out of the CFL maximum (diagnostics still sum them).  The
                               tapered gravity of Sec. 3 is the caller's g table.  Needs
                               PPM_BC_REFLECT on all six faces (else EINVAL); 0 = off. */
+    int nmom;              /* FV moments carried per cell: 3 (or 0) = first moments only;
+                              9 = the ten-value PPB of Sec. 1/4 (first, second and mixed
+                              moments; each pass uses the cell's own parabola).  With 9 the
+                              state has 15 arrays (below); not combined with confine_r
+                              (EINVAL); the x pass then uses the scalar path. */
 } ppm_options;
 
 /* Create a context: nx, ny, nz >= 4; gamma > 1; bc[6] per face

@@ -60,7 +60,7 @@ class _Gravity(C.Structure):
 class _Options(C.Structure):
     _fields_ = [("x0", C.c_double), ("y0", C.c_double), ("z0", C.c_double), ("dx", C.c_double),
                 ("precision", C.c_int), ("heat", _DP), ("damp", _DP), ("stream", C.c_void_p),
-                ("device", C.c_int), ("confine_r", C.c_double)]
+                ("device", C.c_int), ("confine_r", C.c_double), ("nmom", C.c_int)]
 
 
 class _Box(C.Structure):
@@ -85,7 +85,7 @@ def _load():
         raise ImportError(f"libppm.so is not built ({path}); run paper_1810_13416_gb300.build()")
     lib = C.CDLL(path)
     P = C.c_void_p
-    Q = _DP * 9
+    Q = C.POINTER(_DP)   # 6 + nmom array pointers
     I3 = C.c_int * 3
     lib.ppm_create.argtypes = [C.POINTER(P), C.c_int, C.c_int, C.c_int, C.c_double, C.c_int * 6,
                                C.POINTER(_Gravity), C.POINTER(_Options)]
@@ -133,7 +133,7 @@ def _f64(a) -> np.ndarray:
 
 
 def _ptrs(arrs) -> "C.Array":
-    return (_DP * 9)(*[a.ctypes.data_as(_DP) for a in arrs])
+    return (_DP * len(arrs))(*[a.ctypes.data_as(_DP) for a in arrs])
 
 
 class Context:
@@ -141,7 +141,8 @@ class Context:
 
     def __init__(self, shape, gamma: float, bc: Sequence[int], grav_kind: int, s0: float, ds: float,
                  rho0, p0, g, origin=(0.0, 0.0, 0.0), dx: float = 1.0, precision: int = FP32_DEVIATION,
-                 heat=None, damp=None, stream=None, device: int = 0, confine_r: float = 0.0):
+                 heat=None, damp=None, stream=None, device: int = 0, confine_r: float = 0.0,
+                 nmom: int = 3):
         self.lib = _load()
         self.shape = tuple(int(v) for v in shape)
         self._keep = [_f64(rho0), _f64(p0), _f64(g)]
@@ -159,7 +160,7 @@ class Context:
         if stream is not None:
             sptr = int(getattr(stream, "cuda_stream", stream))
         opt = _Options(float(origin[0]), float(origin[1]), float(origin[2]), float(dx), int(precision),
-                       hp, dp, sptr, int(device), float(confine_r))
+                       hp, dp, sptr, int(device), float(confine_r), int(nmom))
         h = C.c_void_p()
         rc = self.lib.ppm_create(C.byref(h), self.shape[0], self.shape[1], self.shape[2], float(gamma),
                                  (C.c_int * 6)(*[int(b) for b in bc]), C.byref(gr), C.byref(opt))
@@ -167,6 +168,7 @@ class Context:
             raise PpmError(rc, self.lib.ppm_last_error(None).decode())
         self.h = h
         self.precision = precision
+        self.nvar = 15 if int(nmom) == 9 else 9
         self.ncell = self.shape[0] * self.shape[1] * self.shape[2]
 
     @classmethod
@@ -178,7 +180,8 @@ class Context:
         return cls(p.shape, p.gamma, p.bc, p.grav, t.s0, t.ds, t.rho0, t.p0, t.g, origin=p.origin,
                    dx=p.dx, precision=precision, heat=getattr(t, "heat", None),
                    damp=getattr(t, "damp", None), stream=stream, device=device,
-                   confine_r=float(getattr(p, "confine_r", 0.0) or 0.0))
+                   confine_r=float(getattr(p, "confine_r", 0.0) or 0.0),
+                   nmom=int(getattr(p, "nmom", 3) or 3))
 
     # ------------------------------------------------------------------
     def _check(self, rc: int):
@@ -205,12 +208,12 @@ class Context:
     # ------------------------------------------------------------------
     def set_state(self, q: Sequence[np.ndarray]):
         arrs = [_f64(a) for a in q]
-        assert len(arrs) == 9 and all(a.size == self.ncell for a in arrs)
+        assert len(arrs) == self.nvar and all(a.size == self.ncell for a in arrs)
         self._check(self.lib.ppm_set_state(self.h, _ptrs(arrs)))
 
     def get_state(self) -> List[np.ndarray]:
         nx, ny, nz = self.shape
-        out = [np.empty((nz, ny, nx)) for _ in range(9)]
+        out = [np.empty((nz, ny, nx)) for _ in range(self.nvar)]
         self._check(self.lib.ppm_get_state(self.h, _ptrs(out)))
         return out
 
@@ -225,10 +228,11 @@ class Context:
         torch.cuda.synchronize()
 
     def set_region(self, lo, hi, q, device: bool = False):
-        """q: 9 host float64 arrays, or 9 CUDA float64 tensors when device=True."""
+        """q: 6 + nmom host float64 arrays, or CUDA float64 tensors when device=True."""
+        assert len(q) == self.nvar
         if device:
             self._sync_torch()
-            ptrs = (_DP * 9)(*[C.cast(C.c_void_p(int(t.data_ptr())), _DP) for t in q])
+            ptrs = (_DP * len(q))(*[C.cast(C.c_void_p(int(t.data_ptr())), _DP) for t in q])
         else:
             q = [_f64(a) for a in q]
             ptrs = _ptrs(q)
@@ -238,10 +242,11 @@ class Context:
     def get_region(self, lo, hi, out=None, device: bool = False):
         b = [hi[d] - lo[d] for d in range(3)]
         if out is None:
-            out = [np.empty((b[2], b[1], b[0])) for _ in range(9)]
+            out = [np.empty((b[2], b[1], b[0])) for _ in range(self.nvar)]
+        assert len(out) == self.nvar
         if device:
             self._sync_torch()
-            ptrs = (_DP * 9)(*[C.cast(C.c_void_p(int(t.data_ptr())), _DP) for t in out])
+            ptrs = (_DP * len(out))(*[C.cast(C.c_void_p(int(t.data_ptr())), _DP) for t in out])
         else:
             ptrs = _ptrs(out)
         self._check(self.lib.ppm_get_region(self.h, (C.c_int * 3)(*lo), (C.c_int * 3)(*hi), ptrs,
@@ -352,7 +357,7 @@ class Ensemble:
     def set_region(self, box: int, lo, hi, q, device: bool = False):
         if device:
             Context._sync_torch()
-            ptrs = (_DP * 9)(*[C.cast(C.c_void_p(int(t.data_ptr())), _DP) for t in q])
+            ptrs = (_DP * len(q))(*[C.cast(C.c_void_p(int(t.data_ptr())), _DP) for t in q])
         else:
             q = [_f64(a) for a in q]
             ptrs = _ptrs(q)

@@ -28,7 +28,8 @@ using namespace ppm;
 
 namespace {
 
-constexpr int NVAR = 9;
+constexpr int NVAR = 9;        // stored values per cell (first moments only)
+constexpr int NVAR_MAX = 15;   // with the ten-value PPB
 constexpr int SWEEP_BLOCK = ppm::SWEEP_NB;
 constexpr int MAX_BINS = 1024;
 
@@ -64,6 +65,8 @@ struct ppm_ctx {
     double rho0c, p0c;         // uniform base (no gravity)
     double confine_r;          // > 0: confining sphere about the coordinate origin
     double domega;             // rotation increment per double step (0 = none)
+    int nmom;                  // FV moments carried: 3 or 9 (ten-value PPB)
+    int nvar;                  // stored values per cell: 6 + nmom
     int has_heat, has_damp;
     int device;
     cudaStream_t stream;
@@ -148,6 +151,7 @@ SweepArgs<R> make_args(ppm_ctx *c, int axis) {
     a.s4_0 = c->s4_0;
     a.inv_ds4 = c->inv_ds4;
     a.confine_r = c->confine_r;
+    a.ten = (c->nmom == 9) ? 1 : 0;
     a.vec_x = (std::is_same<R, float>::value && axis == 0 && (c->n[0] % 8) == 0 && !(c->confine_r > 0.0)) ? 1 : 0;
     a.rho0_c = (R)c->rho0c;
     a.p0_c = (R)c->p0c;
@@ -209,7 +213,7 @@ __device__ __forceinline__ Base<R> cell_base(const SweepArgs<R> &A, int i, int j
 template <typename R, bool PLAIN>
 __global__ void set_region_kernel(SweepArgs<double> A64, R *st, long long ncell, int nx, int ny,
                                   int lo0, int lo1, int lo2, int bx, int by, int bz,
-                                  const double *const *src, long long src_off) {
+                                  const double *const *src, long long src_off, int nvar) {
     const long long nb = (long long)bx * by * bz;
     const double gm1 = A64.gamma - 1.0;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nb;
@@ -217,8 +221,8 @@ __global__ void set_region_kernel(SweepArgs<double> A64, R *st, long long ncell,
         const int i = (int)(t % bx), j = (int)((t / bx) % by), k = (int)(t / ((long long)bx * by));
         const int gi = lo0 + i, gj = lo1 + j, gk = lo2 + k;
         const long long cidx = ((long long)gk * ny + gj) * nx + gi;
-        double v[NVAR];
-        for (int q = 0; q < NVAR; ++q) v[q] = src[q][src_off + t];
+        double v[NVAR_MAX];
+        for (int q = 0; q < nvar; ++q) v[q] = src[q][src_off + t];
         if (!PLAIN) {
             const Base<double> b = cell_base(A64, gi, gj, gk);
             v[0] = xsub(v[0], b.rho0);
@@ -230,8 +234,15 @@ __global__ void set_region_kernel(SweepArgs<double> A64, R *st, long long ncell,
             for (int q = 0; q < 5; ++q) st[q * ncell + cidx] = (R)v[q];
             st[5 * ncell + cidx] = (R)s;
             for (int q = 6; q < 9; ++q) st[q * ncell + cidx] = (R)fminf(fmaxf((float)v[q], -bnd), bnd);
+            if (nvar > 9) {
+                // second and mixed moments within their bounds (as the passes clamp)
+                const float g = bnd * (1.0f / 6.0f), f = (float)fv;
+                const float qlo = -15.0f * g * (1.0f + f), qhi = 15.0f * g * (2.0f - f), bc = 36.0f * g;
+                for (int q = 9; q < 12; ++q) st[q * ncell + cidx] = (R)fminf(fmaxf((float)v[q], qlo), qhi);
+                for (int q = 12; q < 15; ++q) st[q * ncell + cidx] = (R)fminf(fmaxf((float)v[q], -bc), bc);
+            }
         } else {
-            for (int q = 0; q < NVAR; ++q) st[q * ncell + cidx] = (R)v[q];
+            for (int q = 0; q < nvar; ++q) st[q * ncell + cidx] = (R)v[q];
         }
     }
 }
@@ -239,7 +250,7 @@ __global__ void set_region_kernel(SweepArgs<double> A64, R *st, long long ncell,
 template <typename R, bool PLAIN>
 __global__ void get_region_kernel(SweepArgs<double> A64, const R *st, long long ncell, int nx, int ny,
                                   int lo0, int lo1, int lo2, int bx, int by, int bz,
-                                  double *const *dst, long long dst_off) {
+                                  double *const *dst, long long dst_off, int nvar) {
     const long long nb = (long long)bx * by * bz;
     const double gm1 = A64.gamma - 1.0;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nb;
@@ -247,15 +258,15 @@ __global__ void get_region_kernel(SweepArgs<double> A64, const R *st, long long 
         const int i = (int)(t % bx), j = (int)((t / bx) % by), k = (int)(t / ((long long)bx * by));
         const int gi = lo0 + i, gj = lo1 + j, gk = lo2 + k;
         const long long cidx = ((long long)gk * ny + gj) * nx + gi;
-        double v[NVAR];
-        for (int q = 0; q < NVAR; ++q) v[q] = (double)st[q * ncell + cidx];
+        double v[NVAR_MAX];
+        for (int q = 0; q < nvar; ++q) v[q] = (double)st[q * ncell + cidx];
         if (!PLAIN) {
             const Base<double> b = cell_base(A64, gi, gj, gk);
             v[0] = xadd(b.rho0, v[0]);
             v[4] = xadd(xdiv(b.p0, gm1), v[4]);
             v[5] = signbit(v[5]) ? 1.0 + v[5] : v[5];
         }
-        for (int q = 0; q < NVAR; ++q) dst[q][dst_off + t] = v[q];
+        for (int q = 0; q < nvar; ++q) dst[q][dst_off + t] = v[q];
     }
 }
 
@@ -489,7 +500,8 @@ int region_io(ppm_ctx *c, const int lo[3], const int hi[3], double *const *arrs,
             return fail(c, PPM_EINVAL, "region [%d,%d) outside axis %d of extent %d", lo[d], hi[d], d, c->n[d]);
         b[d] = hi[d] - lo[d];
     }
-    for (int q = 0; q < NVAR; ++q)
+    const int nv = c->nvar;
+    for (int q = 0; q < nv; ++q)
         if (!arrs[q]) return fail(c, PPM_EINVAL, "q[%d] is NULL", q);
     if (mem != PPM_MEM_HOST && mem != PPM_MEM_DEVICE) return fail(c, PPM_EINVAL, "bad mem kind %d", mem);
     const SweepArgs<double> A = args64(c);
@@ -499,7 +511,7 @@ int region_io(ppm_ctx *c, const int lo[3], const int hi[3], double *const *arrs,
     double **dptab = reinterpret_cast<double **>(c->diag_acc + 8 + 6 * MAX_BINS);
     long long kchunk = (mem == PPM_MEM_DEVICE) ? b[2] : std::max(1LL, c->stage_cells / plane);
     if (mem == PPM_MEM_HOST && !c->stage) {
-        if (cudaMalloc(&c->stage, (size_t)NVAR * c->stage_cells * sizeof(double)) != cudaSuccess) {
+        if (cudaMalloc(&c->stage, (size_t)nv * c->stage_cells * sizeof(double)) != cudaSuccess) {
             cudaGetLastError();
             c->stage = nullptr;
             return fail(c, PPM_ENOMEM, "cannot allocate the host-transfer staging buffer");
@@ -513,30 +525,30 @@ int region_io(ppm_ctx *c, const int lo[3], const int hi[3], double *const *arrs,
     for (long long k0 = 0; k0 < b[2]; k0 += kchunk) {
         const long long nk = std::min(kchunk, (long long)b[2] - k0);
         const long long cnt = plane * nk;
-        for (int q = 0; q < NVAR; ++q)
+        for (int q = 0; q < nv; ++q)
             ptab[q] = (mem == PPM_MEM_DEVICE) ? arrs[q] + k0 * plane : c->stage + (long long)q * c->stage_cells;
-        CK(c, cudaMemcpyAsync(dptab, ptab, NVAR * sizeof(double *), cudaMemcpyHostToDevice, c->stream));
+        CK(c, cudaMemcpyAsync(dptab, ptab, nv * sizeof(double *), cudaMemcpyHostToDevice, c->stream));
         if (to_dev && mem == PPM_MEM_HOST)
-            for (int q = 0; q < NVAR; ++q)
+            for (int q = 0; q < nv; ++q)
                 CK(c, cudaMemcpyAsync(c->stage + (long long)q * c->stage_cells, arrs[q] + k0 * plane,
                                       cnt * sizeof(double), cudaMemcpyHostToDevice, c->stream));
         const int g = grid_for(cnt, 256);
         const int lz = lo[2] + (int)k0;
         if (to_dev) {
             if (c->prec == PPM_FP32_DEVIATION)
-                set_region_kernel<float, false><<<g, 256, 0, c->stream>>>(A, (float *)c->state, c->ncell, c->n[0], c->n[1], lo[0], lo[1], lz, b[0], b[1], (int)nk, dptab, 0);
+                set_region_kernel<float, false><<<g, 256, 0, c->stream>>>(A, (float *)c->state, c->ncell, c->n[0], c->n[1], lo[0], lo[1], lz, b[0], b[1], (int)nk, dptab, 0, nv);
             else
-                set_region_kernel<double, true><<<g, 256, 0, c->stream>>>(A, (double *)c->state, c->ncell, c->n[0], c->n[1], lo[0], lo[1], lz, b[0], b[1], (int)nk, dptab, 0);
+                set_region_kernel<double, true><<<g, 256, 0, c->stream>>>(A, (double *)c->state, c->ncell, c->n[0], c->n[1], lo[0], lo[1], lz, b[0], b[1], (int)nk, dptab, 0, nv);
         } else {
             if (c->prec == PPM_FP32_DEVIATION)
-                get_region_kernel<float, false><<<g, 256, 0, c->stream>>>(A, (const float *)c->state, c->ncell, c->n[0], c->n[1], lo[0], lo[1], lz, b[0], b[1], (int)nk, dptab, 0);
+                get_region_kernel<float, false><<<g, 256, 0, c->stream>>>(A, (const float *)c->state, c->ncell, c->n[0], c->n[1], lo[0], lo[1], lz, b[0], b[1], (int)nk, dptab, 0, nv);
             else
-                get_region_kernel<double, true><<<g, 256, 0, c->stream>>>(A, (const double *)c->state, c->ncell, c->n[0], c->n[1], lo[0], lo[1], lz, b[0], b[1], (int)nk, dptab, 0);
+                get_region_kernel<double, true><<<g, 256, 0, c->stream>>>(A, (const double *)c->state, c->ncell, c->n[0], c->n[1], lo[0], lo[1], lz, b[0], b[1], (int)nk, dptab, 0, nv);
         }
         c->launches++;
         CK(c, cudaGetLastError());
         if (!to_dev && mem == PPM_MEM_HOST)
-            for (int q = 0; q < NVAR; ++q)
+            for (int q = 0; q < nv; ++q)
                 CK(c, cudaMemcpyAsync(arrs[q] + k0 * plane, c->stage + (long long)q * c->stage_cells,
                                       cnt * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         // the pinned pointer table is reused by the next chunk
@@ -588,6 +600,10 @@ int ppm_create(ppm_ctx **out, int nx, int ny, int nz, double gamma, const int bc
         return fail(nullptr, PPM_EINVAL, "heating/damping tables need a gravity coordinate (plane or central)");
     if (!(opt->confine_r >= 0.0) || !std::isfinite(opt->confine_r))
         return fail(nullptr, PPM_EINVAL, "confine_r must be finite and >= 0");
+    const int nmom = (opt->nmom == 0) ? 3 : opt->nmom;
+    if (nmom != 3 && nmom != 9) return fail(nullptr, PPM_EINVAL, "nmom must be 3 or 9 (got %d)", opt->nmom);
+    if (nmom == 9 && opt->confine_r > 0.0)
+        return fail(nullptr, PPM_EINVAL, "the ten-value PPB (nmom 9) is not combined with a confining sphere");
     if (opt->confine_r > 0.0)
         for (int f = 0; f < 6; ++f)
             if (bc[f] != PPM_BC_REFLECT)
@@ -610,6 +626,8 @@ int ppm_create(ppm_ctx **out, int nx, int ny, int nz, double gamma, const int bc
     c->has_heat = opt->heat != nullptr;
     c->has_damp = opt->damp != nullptr;
     c->confine_r = opt->confine_r;
+    c->nmom = nmom;
+    c->nvar = 6 + nmom;
     c->device = opt->device;
 
     auto bail = [&](int code) {
@@ -635,7 +653,7 @@ int ppm_create(ppm_ctx **out, int nx, int ny, int nz, double gamma, const int bc
         c->own_stream = true;
     }
     const size_t es = (c->prec == PPM_FP32_DEVIATION) ? sizeof(float) : sizeof(double);
-    const size_t sbytes = (size_t)NVAR * (size_t)c->ncell * es;
+    const size_t sbytes = (size_t)c->nvar * (size_t)c->ncell * es;
     if (cudaMalloc(&c->state, sbytes) != cudaSuccess) {
         cudaGetLastError();
         fail(c, PPM_ENOMEM, "cannot allocate %zu bytes of state", sbytes);
@@ -1349,13 +1367,13 @@ int ppm_ensemble_tune(ppm_ens *e, const char *cache_path, int *from_cache) {
     // snapshot the states, time every candidate on the real data, restore
     std::vector<void *> snap(e->nbox, nullptr);
     size_t total = 0;
-    for (ppm_ctx *c : e->box) total += (size_t)NVAR * c->ncell * (e->prec == PPM_FP32_DEVIATION ? 4 : 8);
+    for (ppm_ctx *c : e->box) total += (size_t)c->nvar * c->ncell * (e->prec == PPM_FP32_DEVIATION ? 4 : 8);
     char *scratch = nullptr;
     ECK(e, cudaMalloc(&scratch, total));
     auto copy_all = [&](bool save) -> int {
         size_t off = 0;
         for (ppm_ctx *c : e->box) {
-            const size_t bytes = (size_t)NVAR * c->ncell * (e->prec == PPM_FP32_DEVIATION ? 4 : 8);
+            const size_t bytes = (size_t)c->nvar * c->ncell * (e->prec == PPM_FP32_DEVIATION ? 4 : 8);
             ECK(e, cudaMemcpyAsync(save ? scratch + off : c->state, save ? c->state : scratch + off, bytes,
                                    cudaMemcpyDeviceToDevice, e->stream));
             off += bytes;

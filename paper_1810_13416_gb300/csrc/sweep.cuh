@@ -71,6 +71,7 @@ struct SweepArgs {
     float s4_0, inv_ds4;
     int vec_x;            // x pass with 16-byte copies (n % 4 == 0)
     double confine_r;     // > 0: confining sphere; each pencil updates its fluid run only
+    int ten;              // ten-value PPB (15 stored values per cell)
     double gamma;
     const double *dt;     // device time step
     int sources;          // apply heating/damping after the pass
@@ -379,10 +380,11 @@ constexpr int SWEEP_NB = PPM_SWEEP_NB;   // threads per block
 constexpr int RING = 8;         // scalar prefetch ring slots per thread
 constexpr int PREF = 4;         // scalar prefetch distance (cells)
 
-// Dynamic shared memory of one block of the pass.
-template <typename R, bool VEC, int NB = SWEEP_NB>
+// Dynamic shared memory of one block of the pass (NV stored values per cell:
+// 9, or 15 with the ten-value PPB).
+template <typename R, bool VEC, int NB = SWEEP_NB, int NV = 9>
 constexpr int sweep_smem_bytes() {
-    return VEC ? (4 * 9 * NB * 16 + 9 * NB * 32) : (RING * 9 * NB * (int)sizeof(R));
+    return VEC ? (4 * NV * NB * 16 + NV * NB * 32) : (RING * NV * NB * (int)sizeof(R));
 }
 
 #ifndef PPM_SWEEP_UNROLL
@@ -400,12 +402,15 @@ constexpr int SWEEP_UNROLL = PPM_SWEEP_UNROLL;  // unroll factor of the march lo
 // ---------------------------------------------------------------------------
 // One block of the pass: NB consecutive pencils (lane_block) of pencil row
 // blk.  Called by the single-grid kernel and by the work-list kernel.
-template <typename R, bool PLAIN, bool VEC, int NB, bool CONF = false>
+// TEN: the ten-value PPB (FV, 3 first, 3 second and 3 mixed moments; 15
+// stored values per cell), with a purely local parabola along the pass.
+template <typename R, bool PLAIN, bool VEC, int NB, bool CONF = false, bool TEN = false>
 __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block, int blk,
                                            unsigned char *smem_raw) {
     constexpr int SWEEP_NB = NB;
     constexpr bool F32 = std::is_same<R, float>::value;
     static_assert(!VEC || F32, "vector path is FP32 only");
+    constexpr int NV = TEN ? 15 : 9;
     const int tid = threadIdx.x;
     const int lane = lane_block * NB + threadIdx.x;
     // threads past the edge take part in the final warp reduction only
@@ -472,10 +477,15 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
     // vslot(k) (normal momentum and moment first, then the two transverse
     // ones in cyclic order), so that no per-cell array is indexed by the
     // run-time axis.
+    // Ten-value form: slots 9..11 = second moments (normal, t1, t2), 12 =
+    // the mixed moment of the two transverse axes, 13 / 14 = the mixed
+    // moments of the normal with t1 / t2 (stored at 12 + the remaining axis).
     const int pn = 1 + ax, p1 = 1 + t1d, p2 = 1 + t2d;
     auto voff = [&](int k) -> long long {
         const int v = (k == 1) ? pn : (k == 2) ? p1 : (k == 3) ? p2
-                    : (k == 6) ? pn + 5 : (k == 7) ? p1 + 5 : (k == 8) ? p2 + 5 : k;
+                    : (k == 6) ? pn + 5 : (k == 7) ? p1 + 5 : (k == 8) ? p2 + 5
+                    : (k == 9) ? 9 + ax : (k == 10) ? 9 + t1d : (k == 11) ? 9 + t2d
+                    : (k == 12) ? 12 + ax : (k == 13) ? 12 + t2d : (k == 14) ? 12 + t1d : k;
         return (long long)v * vs;
     };
 
@@ -556,7 +566,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
 
     // per-thread stash of the 4 cells that serve as high-side ghosts
     // (every entry is written before it is read, since n >= 4)
-    R stash[4][9];
+    R stash[4][NV];
     // stash slot of cell m: cells 0..3 (periodic) or the last four cells
     // (walls; all cells of a run shorter than 4)
     const int stash_lo = (bch == 0) ? 0 : max(0, n - 4);
@@ -564,15 +574,15 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
     // prefetch rings (shared memory, private to each thread)
     R *ring = reinterpret_cast<R *>(smem_raw);
     float *ringv = reinterpret_cast<float *>(smem_raw);
-    float *outv = reinterpret_cast<float *>(smem_raw) + 4 * 9 * SWEEP_NB * 4;
+    float *outv = reinterpret_cast<float *>(smem_raw) + 4 * NV * SWEEP_NB * 4;
     auto fetch = [&](int cf) {
         if (cf < n) {
             bool fl;
             const int mm = map_cell(cf, n, bcl, bch, fl);
             const R *src = q + (long long)mm * sa;
-            R *dst = ring + ((cf + G) & (RING - 1)) * 9 * SWEEP_NB + tid;
+            R *dst = ring + ((cf + G) & (RING - 1)) * NV * SWEEP_NB + tid;
 #pragma unroll
-            for (int v = 0; v < 9; ++v) cp_async<(int)sizeof(R)>(dst + v * SWEEP_NB, src + voff(v));
+            for (int v = 0; v < NV; ++v) cp_async<(int)sizeof(R)>(dst + v * SWEEP_NB, src + voff(v));
         }
         cp_commit();
     };
@@ -581,9 +591,9 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
         if (c0 < n) {
             const int m0 = (c0 < 0) ? ((bcl == 0) ? n - 4 : 0) : c0;
             const float *src = reinterpret_cast<const float *>(q) + m0;
-            float *dst = ringv + (((g & 3) * 9) * SWEEP_NB + tid) * 4;
+            float *dst = ringv + (((g & 3) * NV) * SWEEP_NB + tid) * 4;
 #pragma unroll
-            for (int v = 0; v < 9; ++v) cp_async<16>(dst + v * SWEEP_NB * 4, src + v * vs);
+            for (int v = 0; v < NV; ++v) cp_async<16>(dst + v * SWEEP_NB * 4, src + voff(v));
         }
         cp_commit();
     };
@@ -603,6 +613,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
     R wg[5];                                   // gravity along the pass
     R wfs[5];                                  // stored (FP32: folded) FV
     R wmn[5], wm1[5], wm2[5], wed[5];          // conserved momenta and E'
+    R wqn[5], wq1[5], wq2[5], wc12[5], wcn1[5], wcn2[5];  // ten-value form only
 #pragma unroll
     for (int s = 0; s < 5; ++s) {
         wrd[s] = wu[s] = wv[s] = ww[s] = wpd[s] = (R)0;
@@ -610,6 +621,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
         wro[s] = wr0[s] = wp0[s] = (R)1;
         wg[s] = wfs[s] = (R)0;
         wmn[s] = wm1[s] = wm2[s] = wed[s] = (R)0;
+        wqn[s] = wq1[s] = wq2[s] = wc12[s] = wcn1[s] = wcn2[s] = (R)0;
     }
     // interface values of face (c-3)+1/2 (from the previous step)
     R afp[5] = {0, 0, 0, 0, 0};
@@ -623,6 +635,11 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
     R Rp4 = 0, Rm4 = 0;
     // limited transfers of face (c-5)+1/2
     R Gq = 0, Kq = 0, T1q = 0, T2q = 0, PHIq = 0, KMq = 0, sgq = 0;
+    // ten-value form: second moments of content (low / high order) and of
+    // mass, transverse xi-moments, transverse second and mixed moments of
+    // face (c-4)+1/2, and the same (content limited) of face (c-5)+1/2
+    R K2Lp = 0, K2Hp = 0, KM2p = 0, U1p = 0, U2p = 0, Q1p = 0, Q2p = 0, C12p = 0;
+    R K2q = 0, KM2q = 0, U1q = 0, U2q = 0, Q1q = 0, Q2q = 0, C12q = 0;
     // hydro update of cell c-4 (computed one step earlier)
     R rdn4 = 0, mnn4 = 0, m1n4 = 0, m2n4 = 0, edn4 = 0;
 
@@ -640,30 +657,30 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
             fetch(c + PREF);
             cp_wait<PREF>();
         }
-        R raw[9];
+        R raw[NV];
         bool flip = false;
         const int m = map_cell(c, n, bcl, bch, flip);
         if (c >= n) {
             const int si = m - stash_lo;
 #pragma unroll
-            for (int v = 0; v < 9; ++v) raw[v] = stash[si][v];
+            for (int v = 0; v < NV; ++v) raw[v] = stash[si][v];
         } else {
             if constexpr (VEC) {
                 const int sub = (c + G) & 3;
                 const int idx = (c < 0 && bcl == 1) ? 3 - sub : sub;
-                const float *src = ringv + ((((c + G) >> 2) & 3) * 9 * SWEEP_NB + tid) * 4 + idx;
+                const float *src = ringv + ((((c + G) >> 2) & 3) * NV * SWEEP_NB + tid) * 4 + idx;
 #pragma unroll
-                for (int v = 0; v < 9; ++v) raw[v] = src[v * SWEEP_NB * 4];
+                for (int v = 0; v < NV; ++v) raw[v] = src[v * SWEEP_NB * 4];
             } else {
-                const R *src = ring + ((c + G) & (RING - 1)) * 9 * SWEEP_NB + tid;
+                const R *src = ring + ((c + G) & (RING - 1)) * NV * SWEEP_NB + tid;
 #pragma unroll
-                for (int v = 0; v < 9; ++v) raw[v] = src[v * SWEEP_NB];
+                for (int v = 0; v < NV; ++v) raw[v] = src[v * SWEEP_NB];
             }
             if (c >= 0) {
                 const int si = c - stash_lo;
                 if (si >= 0 && si < 4) {
 #pragma unroll
-                    for (int v = 0; v < 9; ++v) stash[si][v] = raw[v];
+                    for (int v = 0; v < NV; ++v) stash[si][v] = raw[v];
                 }
             }
         }
@@ -703,6 +720,10 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
             wo2[s] = wo2[s + 1]; wro[s] = wro[s + 1]; wp0[s] = wp0[s + 1]; wr0[s] = wr0[s + 1];
             wg[s] = wg[s + 1]; wfs[s] = wfs[s + 1];
             wmn[s] = wmn[s + 1]; wm1[s] = wm1[s + 1]; wm2[s] = wm2[s + 1]; wed[s] = wed[s + 1];
+            if constexpr (TEN) {
+                wqn[s] = wqn[s + 1]; wq1[s] = wq1[s + 1]; wq2[s] = wq2[s + 1];
+                wc12[s] = wc12[s + 1]; wcn1[s] = wcn1[s + 1]; wcn2[s] = wcn2[s + 1];
+            }
         }
         wrd[4] = rd; wu[4] = u; wv[4] = v; ww[4] = w; wpd[4] = pd;
         if constexpr (F32) {
@@ -717,6 +738,10 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
         wro[4] = rho; wp0[4] = b_p0; wr0[4] = b_rho0;
         wg[4] = sg * b_g;
         wmn[4] = mn; wm1[4] = m1; wm2[4] = m2; wed[4] = ed;
+        if constexpr (TEN) {
+            wqn[4] = raw[9]; wq1[4] = raw[10]; wq2[4] = raw[11];
+            wc12[4] = raw[12]; wcn1[4] = sg * raw[13]; wcn2[4] = sg * raw[14];
+        }
 
         // ================= a2: interface values of face (c-2)+1/2 ==========
         R afn[5];
@@ -921,7 +946,9 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
         R me2, ae2;
         {
             const R F = wfv[2], mm = won[2];
-            const R a2 = (R)0.25 * (won[3] - won[1]);
+            // curvature: the cell's own second moment (ten-value form), else
+            // from the neighbours' slopes
+            const R a2 = TEN ? wqn[2] : (R)0.25 * (won[3] - won[1]);
             const R ep = (R)0.5 * mm + a2 * (R)(1.0 / 6.0);
             const R em = a2 * (R)(1.0 / 6.0) - (R)0.5 * mm;
             R gmax = rmax(ep, em), gmin = rmin(ep, em);
@@ -957,6 +984,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
         }
         // transfers across face (c-3)+1/2: donor c-3 (slot 1) or c-2 (slot 2)
         R GLc, Ac, KLc, KHc, T1c, T2c, PHIc, KMc, sgc;
+        R K2Lc = 0, K2Hc = 0, KM2c = 0, U1c = 0, U2c = 0, Q1c = 0, Q2c = 0, C12c = 0;
         {
             const R Fr = Frc + Frlc;
             const R sig = usc * dtdx;
@@ -986,6 +1014,25 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
             PHIc = phi;
             KMc = phi * M1;
             sgc = sig;
+            if constexpr (TEN) {
+                // second moments about the donor's centre (mean of xi^4 over
+                // the slab: even power, same for both donors); transverse
+                // moments with their linear variation along the pass
+                const R M4 = (R)0.0625 - (R)0.25 * s + (R)0.5 * s * s - (R)0.5 * s * s * s + (R)0.2 * s * s * s * s;
+                const R chibar = F * M2 + me * M3 + ae * (M4 - M2 * (R)(1.0 / 12.0));
+                const R cn1 = fromleft ? wcn1[1] : wcn1[2];
+                const R cn2 = fromleft ? wcn2[1] : wcn2[2];
+                K2Lc = phi * F * M2;
+                K2Hc = phi * chibar;
+                KM2c = phi * M2;
+                T1c = phi * (ot1 + cn1 * M1);
+                T2c = phi * (ot2 + cn2 * M1);
+                U1c = phi * (ot1 * M1 + cn1 * M2);
+                U2c = phi * (ot2 * M1 + cn2 * M2);
+                Q1c = phi * (fromleft ? wq1[1] : wq1[2]);
+                Q2c = phi * (fromleft ? wq2[1] : wq2[2]);
+                C12c = phi * (fromleft ? wc12[1] : wc12[2]);
+            }
         }
         // FCT factors of cell c-3 (slot 1), bounds [0,1]
         R Rp3, Rm3;
@@ -1001,11 +1048,12 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
             Rm3 = (Pm > (R)0) ? rclamp(Qm / Pm, (R)0, (R)1) : (R)0;
         }
         // limit face (c-4)+1/2 with the factors of cells c-4 and c-3
-        R Gc4, Kc4;
+        R Gc4, Kc4, K2c4 = 0;
         {
             const R Cf = (Ap >= (R)0) ? rmin(Rp3, Rm4) : rmin(Rp4, Rm3);
             Gc4 = GLp + Cf * Ap;
             Kc4 = KLp + Cf * (KHp - KLp);
+            if constexpr (TEN) K2c4 = K2Lp + Cf * (K2Hp - K2Lp);
         }
 
         // ================= final update of cell c-4 (slot 0) ===============
@@ -1055,6 +1103,68 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
             R onn = won[0] + (won[0] * dPhi + (R)12 * (dZc - fvn * Zr)) * rinvn;
             R o1 = wo1[0] + (wo1[0] * dPhi - (T1p - T1q)) * rinvn;
             R o2 = wo2[0] + (wo2[0] * dPhi - (T2p - T2q)) * rinvn;
+            R qnn = 0, q1n = 0, q2n = 0, c12n = 0, cn1n = 0, cn2n = 0;
+            if constexpr (TEN) {
+                // second moments of the content and mass pieces about this
+                // cell's centre after the move, transverse xi-moments; then
+                // the moments relative to the new mass distribution, in
+                // difference form (the reading of the ten-value update)
+                R z2_out = 0, z2_in = 0, zr2_out = 0, zr2_in = 0;
+                R t1_out = 0, u1_out = 0, u1_in = 0, t2_out = 0, u2_out = 0, u2_in = 0;
+                if (sp >= (R)0) {
+                    z2_out = z2_out + K2c4;
+                    zr2_out = zr2_out + KM2p;
+                    t1_out = t1_out + T1p;
+                    u1_out = u1_out + U1p;
+                    t2_out = t2_out + T2p;
+                    u2_out = u2_out + U2p;
+                } else {
+                    const R h = sp + (R)1;
+                    z2_in = z2_in - (K2c4 + (R)2 * h * Kc4 + h * h * Gc4);
+                    zr2_in = zr2_in - (KM2p + (R)2 * h * KMp + h * h * PHIp);
+                    u1_in = u1_in - (U1p + T1p * h);
+                    u2_in = u2_in - (U2p + T2p * h);
+                }
+                if (sm >= (R)0) {
+                    const R h = sm - (R)1;
+                    z2_in = z2_in + (K2q + (R)2 * h * Kq + h * h * Gq);
+                    zr2_in = zr2_in + (KM2q + (R)2 * h * KMq + h * h * PHIq);
+                    u1_in = u1_in + (U1q + T1q * h);
+                    u2_in = u2_in + (U2q + T2q * h);
+                } else {
+                    z2_out = z2_out - K2q;
+                    zr2_out = zr2_out - KM2q;
+                    t1_out = t1_out - T1q;
+                    u1_out = u1_out - U1q;
+                    t2_out = t2_out - T2q;
+                    u2_out = u2_out - U2q;
+                }
+                const R S0 = cold - c_out;
+                const R S1 = rold * won[0] * (R)(1.0 / 12.0) - z_out;
+                const R dZc2 = (R)2 * sbar * S1 + sbar * sbar * S0 + z2_in - z2_out;
+                const R Zr2 = (R)-2 * sbar * zr_out + sbar * sbar * (rold - m_out) + zr2_in - zr2_out +
+                              (rold - rnew) * (R)(1.0 / 12.0);
+                const R dC2p = dZc2 + dG * (R)(1.0 / 12.0);
+                qnn = wqn[0] + (wqn[0] * dPhi + (R)180 * (dC2p - fvn * Zr2) - (R)12 * onn * Zr) * rinvn;
+                const R dY1 = (rold * wo1[0] - t1_out) * sbar + u1_in - u1_out;
+                const R dY2 = (rold * wo2[0] - t2_out) * sbar + u2_in - u2_out;
+                cn1n = wcn1[0] + (wcn1[0] * dPhi + (R)12 * (dY1 - o1 * Zr)) * rinvn;
+                cn2n = wcn2[0] + (wcn2[0] * dPhi + (R)12 * (dY2 - o2 * Zr)) * rinvn;
+                q1n = wq1[0] + (wq1[0] * dPhi - (Q1p - Q1q)) * rinvn;
+                q2n = wq2[0] + (wq2[0] * dPhi - (Q2p - Q2q)) * rinvn;
+                c12n = wc12[0] + (wc12[0] * dPhi - (C12p - C12q)) * rinvn;
+                // realisability: all content at the centre / at the ends /
+                // in one corner
+                const R g = bnd * (R)(1.0 / 6.0);
+                const R qlo = (R)-15 * g * ((R)1 + fvn), qhi = (R)15 * g * ((R)2 - fvn);
+                const R bc = (R)36 * g;
+                qnn = rclamp(qnn, qlo, qhi);
+                q1n = rclamp(q1n, qlo, qhi);
+                q2n = rclamp(q2n, qlo, qhi);
+                cn1n = rclamp(cn1n, -bc, bc);
+                cn2n = rclamp(cn2n, -bc, bc);
+                c12n = rclamp(c12n, -bc, bc);
+            }
             onn = rclamp(onn, -bnd, bnd);
             o1 = rclamp(o1, -bnd, bnd);
             o2 = rclamp(o2, -bnd, bnd);
@@ -1098,7 +1208,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
                     smax_local = rmax(smax_local, spd);
                 }
             }
-            R outc[9];
+            R outc[NV];
             outc[0] = PLAIN ? xadd(wr0[0], rdo) : rdo;
             outc[1] = mno;
             outc[2] = m1o;
@@ -1108,19 +1218,27 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
             outc[6] = onn;
             outc[7] = o1;
             outc[8] = o2;
+            if constexpr (TEN) {
+                outc[9] = qnn;
+                outc[10] = q1n;
+                outc[11] = q2n;
+                outc[12] = c12n;
+                outc[13] = cn1n;
+                outc[14] = cn2n;
+            }
             if constexpr (VEC) {
                 // stage 8 cells ([var][cell][thread]: conflict-free), then one
                 // whole 32-byte sector per variable
                 float *st = outv + (size_t)(i & 7) * SWEEP_NB + tid;
 #pragma unroll
-                for (int vv = 0; vv < 9; ++vv) st[vv * SWEEP_NB * 8] = outc[vv];
+                for (int vv = 0; vv < NV; ++vv) st[vv * SWEEP_NB * 8] = outc[vv];
                 if ((i & 7) == 7) {
                     float *g = reinterpret_cast<float *>(q) + (i - 7);
                     const float *sv = outv + tid;
 #pragma unroll
-                    for (int vv = 0; vv < 9; ++vv) {
+                    for (int vv = 0; vv < NV; ++vv) {
                         const float *r = sv + vv * SWEEP_NB * 8;
-                        float4 *d = reinterpret_cast<float4 *>(g + vv * vs);
+                        float4 *d = reinterpret_cast<float4 *>(g + voff(vv));
                         d[0] = make_float4(r[0], r[SWEEP_NB], r[2 * SWEEP_NB], r[3 * SWEEP_NB]);
                         d[1] = make_float4(r[4 * SWEEP_NB], r[5 * SWEEP_NB], r[6 * SWEEP_NB], r[7 * SWEEP_NB]);
                     }
@@ -1128,7 +1246,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
             } else {
                 R *p = q + (long long)i * sa;
 #pragma unroll
-                for (int vv = 0; vv < 9; ++vv) p[voff(vv)] = outc[vv];
+                for (int vv = 0; vv < NV; ++vv) p[voff(vv)] = outc[vv];
             }
         }
 
@@ -1142,6 +1260,10 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
         me3 = me2; ae3 = ae2;
         Gq = Gc4; Kq = Kc4; T1q = T1p; T2q = T2p; PHIq = PHIp; KMq = KMp; sgq = sgp;
         GLp = GLc; Ap = Ac; KLp = KLc; KHp = KHc; T1p = T1c; T2p = T2c; PHIp = PHIc; KMp = KMc; sgp = sgc;
+        if constexpr (TEN) {
+            K2q = K2c4; KM2q = KM2p; U1q = U1p; U2q = U2p; Q1q = Q1p; Q2q = Q2p; C12q = C12p;
+            K2Lp = K2Lc; K2Hp = K2Hc; KM2p = KM2c; U1p = U1c; U2p = U2c; Q1p = Q1c; Q2p = Q2c; C12p = C12c;
+        }
         Rp4 = Rp3; Rm4 = Rm3;
         rdn4 = rdn3; mnn4 = mnn3; m1n4 = m1n3; m2n4 = m2n3; edn4 = edn3;
     }
@@ -1160,10 +1282,12 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
 // CONF: grid with a confining sphere (per-pencil fluid runs, lanes marching
 // on the global cell index); a separate instantiation so that the plain
 // grid's kernel carries none of it.
-template <typename R, bool PLAIN, bool VEC, bool CONF = false>
-__global__ void __launch_bounds__(SWEEP_NB, PPM_SWEEP_MINB) sweep_kernel(const SweepArgs<R> A) {
+// NB: threads per block (the ten-value x pass uses 64, so that two blocks
+// with their 16-byte rings fit in shared memory).
+template <typename R, bool PLAIN, bool VEC, bool CONF = false, bool TEN = false, int NB = SWEEP_NB>
+__global__ void __launch_bounds__(NB, PPM_SWEEP_MINB) sweep_kernel(const SweepArgs<R> A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    sweep_body<R, PLAIN, VEC, SWEEP_NB, CONF>(A, blockIdx.x, blockIdx.y, smem_raw);
+    sweep_body<R, PLAIN, VEC, NB, CONF, TEN>(A, blockIdx.x, blockIdx.y, smem_raw);
 }
 
 // ---------------------------------------------------------------------------
