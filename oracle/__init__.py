@@ -39,6 +39,7 @@ class _Problem(C.Structure):
         ("s0", C.c_double), ("ds", C.c_double),
         ("rho0", _DP), ("p0", _DP), ("g", _DP), ("heat", _DP), ("damp", _DP),
         ("confine_r", C.c_double), ("domega", C.c_double), ("nmom", C.c_int),
+        ("shock_k", C.c_double),
     ]
 
 
@@ -71,6 +72,7 @@ def _load():
         lib.oracle_diagnostics.argtypes = [P, Q, _DP, C.c_int, C.c_double, _DP, _DP]
         lib.oracle_sweep_z_slab.argtypes = [P, Q, C.c_int, C.c_int, C.c_double, C.c_int]
         lib.oracle_counters.argtypes = [C.POINTER(C.c_longlong)]
+        lib.oracle_divergence.argtypes = [P, Q, _DP]
         lib.oracle_reset_counters.argtypes = []
         lib.oracle_count_flops.argtypes = [P, Q, C.c_int, C.c_double, _DP]
         lib.oracle_set_threads.argtypes = [C.c_int]
@@ -121,6 +123,9 @@ class Oracle:
         if s.nmom not in (3, 9):
             raise ValueError("nmom must be 3 or 9")
         self.nvar = 15 if s.nmom == 9 else 9
+        s.shock_k = float(getattr(p, "shock_k", 0.0) or 0.0)
+        if s.shock_k > 0.0 and s.confine_r > 0.0:
+            raise ValueError("shock dissipation is not combined with a confining sphere")
         self.s = s
         self.problem = p
 
@@ -148,6 +153,8 @@ class Oracle:
 
     def sweep_pencil(self, pencil_in: Sequence[np.ndarray], axis: int, ja: int, jb: int,
                      dt: float, sources: bool = False) -> List[np.ndarray]:
+        """One pass of one pencil (the 3-D shock dissipation needs the whole
+        grid and is not applied here)."""
         n = self.problem.shape[axis]
         pin = [np.ascontiguousarray(a, dtype=np.float64) for a in pencil_in]
         assert len(pin) == self.nvar
@@ -163,8 +170,8 @@ class Oracle:
         """z pass of global planes [k0, k0+nzl) given with 4 halo planes on
         each side (qloc: 9 arrays of shape (nzl+8, ny, nx))."""
         nx, ny, _ = self.problem.shape
-        if self.s.confine_r > 0.0 or self.s.nmom == 9:
-            raise ValueError("sweep_z_slab: no confining sphere, first moments only")
+        if self.s.confine_r > 0.0 or self.s.nmom == 9 or self.s.shock_k > 0.0:
+            raise ValueError("sweep_z_slab: no confining sphere, first moments only, no shock dissipation")
         for a in qloc:
             assert a.shape == (nzl + 8, ny, nx) and a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
         self.lib.oracle_sweep_z_slab(C.byref(self.s), (_DP * 9)(*[_ptr(a) for a in qloc]), int(k0), int(nzl),
@@ -178,6 +185,13 @@ class Oracle:
                                     _ptr(prof), _ptr(mm))
         return tot, prof[: nbins * 5].reshape(nbins, 5), float(mm[0])
 
+    def divergence(self, q) -> np.ndarray:
+        """Cell velocity divergence used by the shock dissipation."""
+        out = np.zeros(self.problem.ncell)
+        self.lib.oracle_divergence(C.byref(self.s), self._q(q), _ptr(out))
+        nx, ny, nz = self.problem.shape
+        return out.reshape(nz, ny, nx)
+
     def count_flops(self, q, axis: int, dt: float):
         out = np.zeros(2)
         self.lib.oracle_count_flops(C.byref(self.s), self._q(q), axis, dt, _ptr(out))
@@ -186,9 +200,10 @@ class Oracle:
     @staticmethod
     def counters():
         lib = _load()
-        out = (C.c_longlong * 6)()
+        out = (C.c_longlong * 7)()
         lib.oracle_counters(out)
-        keys = ("nonsmooth", "flattened", "theta_limited", "fct_limited", "moment_clamped", "cells")
+        keys = ("nonsmooth", "flattened", "theta_limited", "fct_limited", "moment_clamped", "cells",
+                "dissipative_faces")
         return dict(zip(keys, list(out)))
 
     @staticmethod

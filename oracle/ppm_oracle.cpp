@@ -48,8 +48,9 @@ constexpr double EPS_SMOOTH = 1e-9;      // detector floor, relative to rho / c 
 constexpr double EPS_SHOCK = 0.33;       // flattening: relative pressure jump
 constexpr double OMEGA1 = 0.75, OMEGA2 = 10.0;
 constexpr double P_FLOOR = 1e-10;        // Riemann: p* >= P_FLOOR * min(pL, pR)
+constexpr double SHOCK_EPS = 0.05;       // 3-D dissipation acts where -div(u) dx > SHOCK_EPS c
 
-std::atomic<long long> g_cnt[6];
+std::atomic<long long> g_cnt[7];
 int g_threads = 0;
 
 // --------------------------------------------------------------------------
@@ -266,6 +267,10 @@ struct Pencil {
     // it (q1, q2), mixed moments across (c12) and with the pass axis (cn1, cn2)
     bool ten = false;
     std::vector<R> qn, q1, q2, c12, cn1, cn2, qnn, q1n, q2n, c12n, cn1n, cn2n;
+    // 3-D shock dissipation: velocity divergence of each cell (pass start)
+    const double *divg = nullptr;
+    std::vector<R> dv;
+    long long c_diss = 0;
     std::vector<R> K2L, K2H, K2f, KM2, U1, U2, Q1, Q2, C12;
     long long c_nonsmooth = 0, c_flat = 0, c_theta = 0, c_fct = 0, c_clamp = 0;
 
@@ -277,7 +282,7 @@ struct Pencil {
                         &Ft2, &FE, &rdn, &mnn, &mt1n, &mt2n, &edn, &meff, &aeff, &GL, &GH, &KL,
                         &KH, &T1, &T2, &PHI, &KM, &Rp, &Rm, &Gf, &Kf, &fvn, &onn, &ot1n, &ot2n,
                         &qn, &q1, &q2, &c12, &cn1, &cn2, &qnn, &q1n, &q2n, &c12n, &cn1n, &cn2n,
-                        &K2L, &K2H, &K2f, &KM2, &U1, &U2, &Q1, &Q2, &C12})
+                        &K2L, &K2H, &K2f, &KM2, &U1, &U2, &Q1, &Q2, &C12, &dv})
             v->assign(m, R(0.0));
         for (int k = 0; k < NH; ++k) {
             for (auto *v : {&W[k], &af[k], &PL[k], &PR[k], &PD[k], &P6[k], &WL[k], &WR[k]})
@@ -318,6 +323,7 @@ void gather(const oracle_problem *pb, Pencil<R> &P, double *const q[9]) {
         P.on[k] = flip ? -R(q[6 + a][c]) : R(q[6 + a][c]);
         P.ot1[k] = R(q[6 + t1][c]);
         P.ot2[k] = R(q[6 + t2][c]);
+        if (P.divg) P.dv[k] = R(P.divg[c]);   // even under a mirror
         if (P.ten) {
             // q[9+d]: second moment along d; q[12+e]: mixed moment of the two
             // axes other than e.  A mirror flips the moments odd in the normal.
@@ -606,6 +612,22 @@ void riemann_fluxes(const oracle_problem *pb, Pencil<R> &P) {
         P.Ft1[k] = Fr * vst;
         P.Ft2[k] = Fr * wst;
         P.FE[k] = ust * (gg1 * pst + h0) + R(0.5) * (ust * ust + (vst * vst + wst * wst)) * Fr;
+        if (P.divg && pb->shock_k > 0.0) {
+            // 3-D dissipation inside shocks (Sec. 1): momentum and E' diffuse
+            // across the face with nu = K max(0, -div(u) dx - eps c), div(u)
+            // the full 3-D divergence averaged to the face, c the mean sound
+            // speed of the two traced states.  Mass is not diffused.
+            const R dface = R(0.5) * (P.dv[k] + P.dv[k + 1]);
+            const R cface = R(0.5) * (CL / rL + CR / rR);
+            const R nu = R(pb->shock_k) * Max(R(0.0), -(dface * R(pb->dx)) - R(SHOCK_EPS) * cface);
+            if (val(nu) > 0.0) {
+                if (j >= -1 && j <= P.n - 1) ++P.c_diss;
+                P.Fn[k] = P.Fn[k] - nu * (P.mn[k + 1] - P.mn[k]);
+                P.Ft1[k] = P.Ft1[k] - nu * (P.mt1[k + 1] - P.mt1[k]);
+                P.Ft2[k] = P.Ft2[k] - nu * (P.mt2[k + 1] - P.mt2[k]);
+                P.FE[k] = P.FE[k] - nu * (P.ed[k + 1] - P.ed[k]);
+            }
+        }
     }
 }
 
@@ -1131,6 +1153,36 @@ void flush_counters(const Pencil<R> &P) {
     g_cnt[3] += P.c_fct;
     g_cnt[4] += P.c_clamp;
     g_cnt[5] += P.n;
+    g_cnt[6] += P.c_diss;
+}
+
+// Velocity divergence of every cell for the 3-D shock dissipation: central
+// differences of u_d = (rho u_d)/rho along each axis, summed in x, y, z order;
+// ghost neighbours by the boundary conditions (periodic wrap; at a wall the
+// mirror cell with its normal velocity reversed).
+void divergence(const oracle_problem *pb, double *const q[], std::vector<double> &D) {
+    const int n[3] = {pb->nx, pb->ny, pb->nz};
+    const long long ncell = (long long)n[0] * n[1] * n[2];
+    D.assign((size_t)ncell, 0.0);
+    const double h = 0.5 / pb->dx;
+#pragma omp parallel for num_threads(g_threads > 0 ? g_threads : omp_get_max_threads())
+    for (long long c = 0; c < ncell; ++c) {
+        const int ijk[3] = {(int)(c % n[0]), (int)((c / n[0]) % n[1]), (int)(c / ((long long)n[0] * n[1]))};
+        double diff[3];
+        for (int d = 0; d < 3; ++d) {
+            double u[2];
+            for (int s = 0; s < 2; ++s) {
+                int idx[3] = {ijk[0], ijk[1], ijk[2]};
+                bool flip;
+                idx[d] = map_cell(ijk[d] + (s ? 1 : -1), n[d], pb->bc[2 * d], pb->bc[2 * d + 1], &flip);
+                const long long cc = ((long long)idx[2] * n[1] + idx[1]) * n[0] + idx[0];
+                const double v = q[1 + d][cc] / q[0][cc];
+                u[s] = flip ? -v : v;
+            }
+            diff[d] = u[1] - u[0];
+        }
+        D[(size_t)c] = ((diff[0] + diff[1]) + diff[2]) * h;
+    }
 }
 
 template <class R>
@@ -1139,10 +1191,13 @@ void sweep_all(const oracle_problem *pb, double *q[9], int axis, double dt, int 
     const int n = extent(pb, axis);
     const int na = extent(pb, (axis + 1) % 3), nb = extent(pb, (axis + 2) % 3);
     const long long npen = (long long)na * nb;
+    std::vector<double> D;
+    if (pb->shock_k > 0.0) divergence(pb, q, D);
     auto body = [&](Pencil<R> &P, long long p) {
+        P.divg = D.empty() ? nullptr : D.data();
         P.ja = (int)(p % na);
         P.jb = (int)(p / na);
-        P.c_nonsmooth = P.c_flat = P.c_theta = P.c_fct = P.c_clamp = 0;
+        P.c_nonsmooth = P.c_flat = P.c_theta = P.c_fct = P.c_clamp = P.c_diss = 0;
         if (!pencil_run(pb, axis, P.ja, P.jb, &P.i0, &P.n)) return;
         P.confined = pb->confine_r > 0.0;
         P.ten = pb->nmom == 9;
@@ -1422,12 +1477,18 @@ void oracle_diagnostics(const oracle_problem *pb, double *const q[9], double tot
     if (max_mach) *max_mach = mmax;
 }
 
-void oracle_counters(long long out[6]) {
-    for (int i = 0; i < 6; ++i) out[i] = g_cnt[i].load();
+void oracle_divergence(const oracle_problem *pb, double *const q[9], double *out) {
+    std::vector<double> D;
+    divergence(pb, q, D);
+    std::memcpy(out, D.data(), sizeof(double) * D.size());
+}
+
+void oracle_counters(long long out[7]) {
+    for (int i = 0; i < 7; ++i) out[i] = g_cnt[i].load();
 }
 
 void oracle_reset_counters(void) {
-    for (int i = 0; i < 6; ++i) g_cnt[i] = 0;
+    for (int i = 0; i < 7; ++i) g_cnt[i] = 0;
 }
 
 void oracle_count_flops(const oracle_problem *pb, double *const q[9], int axis, double dt, double out[2]) {

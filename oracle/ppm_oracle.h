@@ -53,6 +53,11 @@ typedef struct {
                                (the ten-value PPB of Sec. 1/4, q[15]: after the first moments
                                q[9..11] = second moments along x, y, z and q[12..14] = the mixed
                                moments yz, xz, xy) */
+    double shock_k;         /* > 0: 3-D dissipation inside shocks (Sec. 1) with this coefficient
+                               K: in each pass, momentum and E' diffuse across a face with
+                               nu = K max(0, -div(u) dx - 0.05 c), div(u) the 3-D velocity
+                               divergence of the pass's input state averaged to the face
+                               (grid passes only; not with a confining sphere) */
 } oracle_problem;
 
 /* One 1-D pass along axis (0=x,1=y,2=z) over the whole grid, in place.
@@ -88,10 +93,14 @@ void oracle_sweep_z_slab(const oracle_problem *pb, double *q[9], int k0, int nzl
 void oracle_diagnostics(const oracle_problem *pb, double *const q[9], double totals[7],
                         int nbins, double rmax, double *profiles, double *max_mach);
 
+/* The cell velocity divergence the shock dissipation uses (out: ncell). */
+void oracle_divergence(const oracle_problem *pb, double *const q[9], double *out);
+
 /* Event counters since the last reset: [0] cells with a non-smooth hydro
  * variable, [1] cells flattened, [2] PPB profiles bound-limited, [3] faces
- * FCT-limited (C<1), [4] moment-bound clamps, [5] cells visited. */
-void oracle_counters(long long out[6]);
+ * FCT-limited (C<1), [4] moment-bound clamps, [5] cells visited, [6] faces
+ * with shock dissipation. */
+void oracle_counters(long long out[7]);
 void oracle_reset_counters(void);
 
 /* Counted arithmetic: runs one pass along axis on a copy of q with every
