@@ -98,7 +98,15 @@ typedef struct {
                               9 = the ten-value PPB of Sec. 1/4 (first, second and mixed
                               moments; each pass uses the cell's own parabola).  With 9 the
                               state has 15 arrays (below); not combined with confine_r
-                              (EINVAL); the x pass then uses the scalar path. */
+                              (EINVAL). */
+    double shock_k;        /* > 0: 3-D dissipation inside shocks (Sec. 1) with coefficient K:
+                              before each pass a kernel takes the velocity divergence of
+                              every cell (central differences, boundary ghosts as in the
+                              passes), and the pass diffuses momentum and E' across each face
+                              with nu = K max(0, -div(u) dx - 0.05 c) (divergence averaged to
+                              the face, c the mean sound speed of the traced states); mass is
+                              not diffused.  0 = off; not combined with confine_r or nmom 9
+                              (EINVAL). */
 } ppm_options;
 
 /* Create a context: nx, ny, nz >= 4; gamma > 1; bc[6] per face

@@ -60,7 +60,8 @@ class _Gravity(C.Structure):
 class _Options(C.Structure):
     _fields_ = [("x0", C.c_double), ("y0", C.c_double), ("z0", C.c_double), ("dx", C.c_double),
                 ("precision", C.c_int), ("heat", _DP), ("damp", _DP), ("stream", C.c_void_p),
-                ("device", C.c_int), ("confine_r", C.c_double), ("nmom", C.c_int)]
+                ("device", C.c_int), ("confine_r", C.c_double), ("nmom", C.c_int),
+                ("shock_k", C.c_double)]
 
 
 class _Box(C.Structure):
@@ -142,7 +143,7 @@ class Context:
     def __init__(self, shape, gamma: float, bc: Sequence[int], grav_kind: int, s0: float, ds: float,
                  rho0, p0, g, origin=(0.0, 0.0, 0.0), dx: float = 1.0, precision: int = FP32_DEVIATION,
                  heat=None, damp=None, stream=None, device: int = 0, confine_r: float = 0.0,
-                 nmom: int = 3):
+                 nmom: int = 3, shock_k: float = 0.0):
         self.lib = _load()
         self.shape = tuple(int(v) for v in shape)
         self._keep = [_f64(rho0), _f64(p0), _f64(g)]
@@ -160,7 +161,7 @@ class Context:
         if stream is not None:
             sptr = int(getattr(stream, "cuda_stream", stream))
         opt = _Options(float(origin[0]), float(origin[1]), float(origin[2]), float(dx), int(precision),
-                       hp, dp, sptr, int(device), float(confine_r), int(nmom))
+                       hp, dp, sptr, int(device), float(confine_r), int(nmom), float(shock_k))
         h = C.c_void_p()
         rc = self.lib.ppm_create(C.byref(h), self.shape[0], self.shape[1], self.shape[2], float(gamma),
                                  (C.c_int * 6)(*[int(b) for b in bc]), C.byref(gr), C.byref(opt))
@@ -181,7 +182,8 @@ class Context:
                    dx=p.dx, precision=precision, heat=getattr(t, "heat", None),
                    damp=getattr(t, "damp", None), stream=stream, device=device,
                    confine_r=float(getattr(p, "confine_r", 0.0) or 0.0),
-                   nmom=int(getattr(p, "nmom", 3) or 3))
+                   nmom=int(getattr(p, "nmom", 3) or 3),
+                   shock_k=float(getattr(p, "shock_k", 0.0) or 0.0))
 
     # ------------------------------------------------------------------
     def _check(self, rc: int):

@@ -67,6 +67,9 @@ struct ppm_ctx {
     double domega;             // rotation increment per double step (0 = none)
     int nmom;                  // FV moments carried: 3 or 9 (ten-value PPB)
     int nvar;                  // stored values per cell: 6 + nmom
+    double shock_k;            // 3-D shock dissipation coefficient (0 = off)
+    long long graph_kernels;   // kernels in the step graph
+    void *divg;                // its per-pass cell divergence (ncell values)
     int has_heat, has_damp;
     int device;
     cudaStream_t stream;
@@ -152,6 +155,8 @@ SweepArgs<R> make_args(ppm_ctx *c, int axis) {
     a.inv_ds4 = c->inv_ds4;
     a.confine_r = c->confine_r;
     a.ten = (c->nmom == 9) ? 1 : 0;
+    a.divg = static_cast<const R *>(c->divg);
+    a.shock_k = c->shock_k;
     a.vec_x = (std::is_same<R, float>::value && axis == 0 && (c->n[0] % 8) == 0 && !(c->confine_r > 0.0)) ? 1 : 0;
     a.rho0_c = (R)c->rho0c;
     a.p0_c = (R)c->p0c;
@@ -164,7 +169,13 @@ SweepArgs<R> make_args(ppm_ctx *c, int axis) {
     return a;
 }
 
+int launch_divergence(ppm_ctx *c);
+
 int launch_sweep(ppm_ctx *c, int axis, int sources, int cfl) {
+    if (c->divg) {
+        const int r = launch_divergence(c);
+        if (r != PPM_OK) return r;
+    }
     dim3 block(SWEEP_BLOCK);
     if (c->prec == PPM_FP32_DEVIATION) {
         SweepArgs<float> a = make_args<float>(c, axis);
@@ -417,9 +428,19 @@ __global__ void diag_kernel(SweepArgs<double> A64, const R *st, long long ncell,
         tot[5] += rho * fv;
         tot[6] += fv;
         const double m2 = mx * mx + my * my + mz * mz;
-        const double rinv = 1.0 / rho;
-        const double p = p0 + gm1 * (Ed - 0.5 * m2 * rinv);
-        m2max = fmax(m2max, m2 / (gam * p * rho));   // |u|^2 / c^2
+        double rinv = 0.0, p = 0.0;
+        if (PLAIN || nbins > 0) {
+            rinv = 1.0 / rho;
+            p = p0 + gm1 * (Ed - 0.5 * m2 * rinv);
+        }
+        if (PLAIN) {
+            m2max = fmax(m2max, m2 / (gam * p * rho));   // |u|^2 / c^2
+        } else {
+            // FP32 state: its Mach number to FP32 accuracy, without FP64 divisions
+            const float rf = (float)rho, m2f = (float)m2;
+            const float pf = (float)p0 + (float)gm1 * ((float)Ed - 0.5f * m2f / rf);
+            m2max = fmax(m2max, (double)(m2f / ((float)gam * pf * rf)));
+        }
         if (nbins > 0) {
             if (r < 0.0) r = sqrt(x * x + y * y + z * z);
             const int bin = (int)floor(r / rmax_ * nbins);
@@ -458,6 +479,56 @@ int grid_for(long long n, int block) {
     if (g > 152 * 16) g = 152 * 16;
     if (g < 1) g = 1;
     return (int)g;
+}
+
+// Velocity divergence of every cell for the 3-D shock dissipation: central
+// differences of u_d = (rho u_d)/rho along each axis, summed in x, y, z order;
+// ghost neighbours by the boundary conditions (periodic wrap; at a wall the
+// mirror cell with its normal velocity reversed).
+template <typename R, bool PLAIN>
+__global__ void divergence_kernel(SweepArgs<R> A, const R *st, R *D, long long ncell, int nx, int ny, int nz,
+                                  int bx0, int bx1, int by0, int by1, int bz0, int bz1) {
+    const int n[3] = {nx, ny, nz};
+    const int bl[3] = {bx0, by0, bz0}, bh[3] = {bx1, by1, bz1};
+    const R h = (R)(0.5 / A.dx);
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < ncell;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int ijk[3] = {(int)(t % nx), (int)((t / nx) % ny), (int)(t / ((long long)nx * ny))};
+        R diff[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            R u[2];
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                int idx[3] = {ijk[0], ijk[1], ijk[2]};
+                bool flip;
+                idx[d] = map_cell(ijk[d] + (s ? 1 : -1), n[d], bl[d], bh[d], flip);
+                const long long cc = ((long long)idx[2] * ny + idx[1]) * nx + idx[0];
+                R rho = st[cc];
+                if (!PLAIN) rho = cell_base(A, idx[0], idx[1], idx[2]).rho0 + rho;
+                const R v = st[(1 + d) * ncell + cc] / rho;
+                u[s] = flip ? -v : v;
+            }
+            diff[d] = u[1] - u[0];
+        }
+        D[t] = ((diff[0] + diff[1]) + diff[2]) * h;
+    }
+}
+
+int launch_divergence(ppm_ctx *c) {
+    const int g = grid_for(c->ncell, 256);
+    const int *b = c->bc;
+    if (c->prec == PPM_FP32_DEVIATION)
+        divergence_kernel<float, false><<<g, 256, 0, c->stream>>>(make_args<float>(c, 0), (const float *)c->state,
+                                                                  (float *)c->divg, c->ncell, c->n[0], c->n[1], c->n[2],
+                                                                  b[0], b[1], b[2], b[3], b[4], b[5]);
+    else
+        divergence_kernel<double, true><<<g, 256, 0, c->stream>>>(make_args<double>(c, 0), (const double *)c->state,
+                                                                  (double *)c->divg, c->ncell, c->n[0], c->n[1], c->n[2],
+                                                                  b[0], b[1], b[2], b[3], b[4], b[5]);
+    c->launches++;
+    CK(c, cudaGetLastError());
+    return PPM_OK;
 }
 
 static int launch_rotate(ppm_ctx *c, bool with_cfl) {
@@ -563,6 +634,7 @@ void release(ppm_ctx *c) {
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->graph) cudaGraphDestroy(c->graph);
     if (c->state) cudaFree(c->state);
+    if (c->divg) cudaFree(c->divg);
     if (c->t64) cudaFree(c->t64);
     if (c->t32) cudaFree(c->t32);
     if (c->t4) cudaFree(c->t4);
@@ -604,6 +676,10 @@ int ppm_create(ppm_ctx **out, int nx, int ny, int nz, double gamma, const int bc
     if (nmom != 3 && nmom != 9) return fail(nullptr, PPM_EINVAL, "nmom must be 3 or 9 (got %d)", opt->nmom);
     if (nmom == 9 && opt->confine_r > 0.0)
         return fail(nullptr, PPM_EINVAL, "the ten-value PPB (nmom 9) is not combined with a confining sphere");
+    if (!(opt->shock_k >= 0.0) || !std::isfinite(opt->shock_k))
+        return fail(nullptr, PPM_EINVAL, "shock_k must be finite and >= 0");
+    if (opt->shock_k > 0.0 && (opt->confine_r > 0.0 || nmom == 9))
+        return fail(nullptr, PPM_EINVAL, "shock dissipation is not combined with a confining sphere or nmom 9");
     if (opt->confine_r > 0.0)
         for (int f = 0; f < 6; ++f)
             if (bc[f] != PPM_BC_REFLECT)
@@ -628,6 +704,7 @@ int ppm_create(ppm_ctx **out, int nx, int ny, int nz, double gamma, const int bc
     c->confine_r = opt->confine_r;
     c->nmom = nmom;
     c->nvar = 6 + nmom;
+    c->shock_k = opt->shock_k;
     c->device = opt->device;
 
     auto bail = [&](int code) {
@@ -657,6 +734,12 @@ int ppm_create(ppm_ctx **out, int nx, int ny, int nz, double gamma, const int bc
     if (cudaMalloc(&c->state, sbytes) != cudaSuccess) {
         cudaGetLastError();
         fail(c, PPM_ENOMEM, "cannot allocate %zu bytes of state", sbytes);
+        return bail(PPM_ENOMEM);
+    }
+    if (c->shock_k > 0.0 && cudaMalloc(&c->divg, (size_t)c->ncell * es) != cudaSuccess) {
+        cudaGetLastError();
+        c->divg = nullptr;
+        fail(c, PPM_ENOMEM, "cannot allocate the divergence buffer");
         return bail(PPM_ENOMEM);
     }
     const int nt = grav->ntab;
@@ -791,7 +874,9 @@ int ppm_cfl_dt(ppm_ctx *c, double cfl, double *dt_out) {
 
 static int capture_step(ppm_ctx *c) {
     CK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    const long long before = c->launches;
     dt_kernel<<<1, 32, 0, c->stream>>>(c->ds_dev, c->dx, -1.0);
+    c->launches++;
     const int order[6] = {0, 1, 2, 2, 1, 0};
     int rc = PPM_OK;
     for (int s = 0; s < 6 && rc == PPM_OK; ++s) {
@@ -800,7 +885,8 @@ static int capture_step(ppm_ctx *c) {
     }
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);
-    c->launches -= 6;  // captured, not yet launched
+    c->graph_kernels = c->launches - before;  // captured, not yet launched
+    c->launches = before;
     if (rc != PPM_OK) {
         if (g) cudaGraphDestroy(g);
         return rc;
@@ -842,7 +928,7 @@ int ppm_step(ppm_ctx *c, double dt) {
         CK(c, cudaGraphExecKernelNodeSetParams(c->gexec, c->dt_node, &kp));
     }
     CK(c, cudaGraphLaunch(c->gexec, c->stream));
-    c->launches += 7;
+    c->launches += c->graph_kernels;
     c->have_speed = true;
     if (c->domega != 0.0) return launch_rotate(c, true);
     return PPM_OK;

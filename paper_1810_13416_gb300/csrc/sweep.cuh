@@ -72,6 +72,8 @@ struct SweepArgs {
     int vec_x;            // x pass with 16-byte copies (n % 4 == 0)
     double confine_r;     // > 0: confining sphere; each pencil updates its fluid run only
     int ten;              // ten-value PPB (15 stored values per cell)
+    const R *divg;        // 3-D shock dissipation: cell velocity divergence (NULL: off)
+    double shock_k;       // its coefficient K
     double gamma;
     const double *dt;     // device time step
     int sources;          // apply heating/damping after the pass
@@ -404,7 +406,9 @@ constexpr int SWEEP_UNROLL = PPM_SWEEP_UNROLL;  // unroll factor of the march lo
 // blk.  Called by the single-grid kernel and by the work-list kernel.
 // TEN: the ten-value PPB (FV, 3 first, 3 second and 3 mixed moments; 15
 // stored values per cell), with a purely local parabola along the pass.
-template <typename R, bool PLAIN, bool VEC, int NB, bool CONF = false, bool TEN = false>
+// DISS: 3-D shock dissipation (momentum and E' diffuse across faces where the
+// cell velocity divergence marks a shock).
+template <typename R, bool PLAIN, bool VEC, int NB, bool CONF = false, bool TEN = false, bool DISS = false>
 __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block, int blk,
                                            unsigned char *smem_raw) {
     constexpr int SWEEP_NB = NB;
@@ -472,6 +476,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
     }
     if (active) {
     R *__restrict__ q = A.q + (long long)lane * A.s_lane + (long long)blk * A.s_blk + (long long)i0 * A.s_axis;
+    const R *__restrict__ dvp = DISS ? A.divg + (long long)lane * A.s_lane + (long long)blk * A.s_blk : nullptr;
     const long long vs = A.vs, sa = A.s_axis;
     // Cells are held in the pass frame: slot k of a cell is stored variable
     // vslot(k) (normal momentum and moment first, then the two transverse
@@ -614,6 +619,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
     R wfs[5];                                  // stored (FP32: folded) FV
     R wmn[5], wm1[5], wm2[5], wed[5];          // conserved momenta and E'
     R wqn[5], wq1[5], wq2[5], wc12[5], wcn1[5], wcn2[5];  // ten-value form only
+    R wdv[5] = {0, 0, 0, 0, 0};                // cell divergence (shock dissipation only)
 #pragma unroll
     for (int s = 0; s < 5; ++s) {
         wrd[s] = wu[s] = wv[s] = ww[s] = wpd[s] = (R)0;
@@ -720,6 +726,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
             wo2[s] = wo2[s + 1]; wro[s] = wro[s + 1]; wp0[s] = wp0[s + 1]; wr0[s] = wr0[s + 1];
             wg[s] = wg[s + 1]; wfs[s] = wfs[s + 1];
             wmn[s] = wmn[s + 1]; wm1[s] = wm1[s + 1]; wm2[s] = wm2[s + 1]; wed[s] = wed[s + 1];
+            if constexpr (DISS) wdv[s] = wdv[s + 1];
             if constexpr (TEN) {
                 wqn[s] = wqn[s + 1]; wq1[s] = wq1[s + 1]; wq2[s] = wq2[s + 1];
                 wc12[s] = wc12[s + 1]; wcn1[s] = wcn1[s + 1]; wcn2[s] = wcn2[s + 1];
@@ -738,6 +745,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
         wro[4] = rho; wp0[4] = b_p0; wr0[4] = b_rho0;
         wg[4] = sg * b_g;
         wmn[4] = mn; wm1[4] = m1; wm2[4] = m2; wed[4] = ed;
+        if constexpr (DISS) wdv[4] = __ldg(dvp + (long long)m * sa);   // even under a mirror
         if constexpr (TEN) {
             wqn[4] = raw[9]; wq1[4] = raw[10]; wq2[4] = raw[11];
             wc12[4] = raw[12]; wcn1[4] = sg * raw[13]; wcn2[4] = sg * raw[14];
@@ -914,6 +922,22 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
                 Ft2c = Fr * wst;
                 FEc = ust * (gg1 * pst + h0) + kin * Fr;
                 FElc = 0;
+            }
+            if constexpr (DISS) {
+                // 3-D dissipation inside shocks (Sec. 1): momentum and E'
+                // diffuse with nu = K max(0, -div(u) dx - 0.05 c), the cell
+                // divergences averaged to the face and c the mean sound speed
+                // of the two traced states; no mass diffusion
+                const R dface = (R)0.5 * (wdv[1] + wdv[2]);
+                const R cface = (R)0.5 * (CL / rL + CR / rR);
+                const R nu = (R)A.shock_k * rmax((R)0, -(dface * (R)A.dx) - (R)0.05 * cface);
+                Fnc = Fnc - nu * (wmn[2] - wmn[1]);
+                Ft1c = Ft1c - nu * (wm1[2] - wm1[1]);
+                Ft2c = Ft2c - nu * (wm2[2] - wm2[1]);
+                if constexpr (F32)
+                    FElc = FElc - nu * (wed[2] - wed[1]);
+                else
+                    FEc = FEc - nu * (wed[2] - wed[1]);
             }
             usc = ust;
         }
@@ -1284,10 +1308,11 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
 // grid's kernel carries none of it.
 // NB: threads per block (the ten-value x pass uses 64, so that two blocks
 // with their 16-byte rings fit in shared memory).
-template <typename R, bool PLAIN, bool VEC, bool CONF = false, bool TEN = false, int NB = SWEEP_NB>
+template <typename R, bool PLAIN, bool VEC, bool CONF = false, bool TEN = false, bool DISS = false,
+          int NB = SWEEP_NB>
 __global__ void __launch_bounds__(NB, PPM_SWEEP_MINB) sweep_kernel(const SweepArgs<R> A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    sweep_body<R, PLAIN, VEC, NB, CONF, TEN>(A, blockIdx.x, blockIdx.y, smem_raw);
+    sweep_body<R, PLAIN, VEC, NB, CONF, TEN, DISS>(A, blockIdx.x, blockIdx.y, smem_raw);
 }
 
 // ---------------------------------------------------------------------------

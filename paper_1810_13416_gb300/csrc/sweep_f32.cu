@@ -4,7 +4,7 @@
 
 namespace ppm {
 constexpr int TEN_VEC_NB = 64;
-// Raise the dynamic shared-memory limit of both variants (once per device,
+// Raise the dynamic shared-memory limit of every variant (once per device,
 // called when a context is created).
 cudaError_t prepare_sweep_f32() {
     cudaError_t e = cudaFuncSetAttribute(sweep_kernel<float, false, true>,
@@ -17,7 +17,13 @@ cudaError_t prepare_sweep_f32() {
     e = cudaFuncSetAttribute(sweep_kernel<float, false, false, false, true>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, sweep_smem_bytes<float, false, SWEEP_NB, 15>());
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(sweep_kernel<float, false, true, false, true, TEN_VEC_NB>,
+    e = cudaFuncSetAttribute(sweep_kernel<float, false, false, false, false, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, sweep_smem_bytes<float, false>());
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(sweep_kernel<float, false, true, false, false, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, sweep_smem_bytes<float, true>());
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(sweep_kernel<float, false, true, false, true, false, TEN_VEC_NB>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, sweep_smem_bytes<float, true, TEN_VEC_NB, 15>());
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(sweep_kernel<float, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -25,10 +31,15 @@ cudaError_t prepare_sweep_f32() {
 }
 
 void launch_sweep_f32(const SweepArgs<float> &a, dim3 grid, dim3 block, cudaStream_t st) {
-    if (a.ten && a.vec_x) {
+    if (a.divg) {
+        if (a.vec_x)
+            sweep_kernel<float, false, true, false, false, true><<<grid, block, sweep_smem_bytes<float, true>(), st>>>(a);
+        else
+            sweep_kernel<float, false, false, false, false, true><<<grid, block, sweep_smem_bytes<float, false>(), st>>>(a);
+    } else if (a.ten && a.vec_x) {
         // 64-thread blocks: two fit with their 15-value 16-byte rings
         const dim3 g((a.nlane + TEN_VEC_NB - 1) / TEN_VEC_NB, a.nblk);
-        sweep_kernel<float, false, true, false, true, TEN_VEC_NB>
+        sweep_kernel<float, false, true, false, true, false, TEN_VEC_NB>
             <<<g, dim3(TEN_VEC_NB), sweep_smem_bytes<float, true, TEN_VEC_NB, 15>(), st>>>(a);
     } else if (a.ten)
         sweep_kernel<float, false, false, false, true>

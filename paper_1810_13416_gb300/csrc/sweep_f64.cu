@@ -10,12 +10,17 @@ cudaError_t prepare_sweep_f64() {
     e = cudaFuncSetAttribute(sweep_kernel<double, true, false, false, true>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, sweep_smem_bytes<double, false, SWEEP_NB, 15>());
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(sweep_kernel<double, true, false, false, false, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, sweep_smem_bytes<double, false>());
+    if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(sweep_kernel<double, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 sweep_smem_bytes<double, false>());
 }
 
 void launch_sweep_f64(const SweepArgs<double> &a, dim3 grid, dim3 block, cudaStream_t st) {
-    if (a.ten)
+    if (a.divg)
+        sweep_kernel<double, true, false, false, false, true><<<grid, block, sweep_smem_bytes<double, false>(), st>>>(a);
+    else if (a.ten)
         sweep_kernel<double, true, false, false, true>
             <<<grid, block, sweep_smem_bytes<double, false, SWEEP_NB, 15>(), st>>>(a);
     else if (a.confine_r > 0.0)

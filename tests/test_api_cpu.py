@@ -40,7 +40,7 @@ def _create(lib, **kw):
     gr = ppm._Gravity(args["kind"], args["ntab"], 0.0, args["ds"], dp, dp,
                       C.cast(zero, C.POINTER(C.c_double)))
     opt = ppm._Options(0.0, 0.0, 0.0, args["dx"], args["precision"], None, None, None, 0,
-                       args.get("confine_r", 0.0))
+                       args.get("confine_r", 0.0), args.get("nmom", 3), args.get("shock_k", 0.0))
     h = C.c_void_p()
     rc = lib.ppm_create(C.byref(h), args["nx"], args["ny"], args["nz"], args["gamma"],
                         (C.c_int * 6)(*args["bc"]), C.byref(gr), C.byref(opt))
@@ -59,6 +59,9 @@ def _create(lib, **kw):
     (dict(dx=-1.0), "dx"),
     (dict(confine_r=-1.0), "confine_r"),
     (dict(confine_r=0.5), "six faces"),
+    (dict(nmom=5), "nmom"),
+    (dict(shock_k=-0.1), "shock_k"),
+    (dict(shock_k=0.1, nmom=9), "shock dissipation"),
 ])
 def test_create_rejects_bad_arguments(lib, kw, frag):
     rc, h = _create(lib, **kw)

@@ -1,0 +1,100 @@
+"""GPU parity of the 3-D shock dissipation (Sec. 1) against the FP64 oracle,
+through the C ABI: Sod and Lax tubes along each axis and a periodic box with
+forming shocks, FP64 (relative L-inf <= 1e-10), and FP32 (relative L1 <= 1e-5
+on rho and E) on the Sod tubes and the box; the dissipation is active in
+these runs (oracle counter)."""
+import copy
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1810_13416_gb300 as ppm
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ppm.build()
+    oracle.build()
+
+
+def _with_k(p, k=0.1):
+    p = copy.copy(p)
+    p.shock_k = k
+    return p
+
+
+def _shock_box():
+    p = _with_k(workloads.periodic_box(shape=(24, 20, 16), mach=0.0))
+    q = workloads.build(workloads.periodic_box(shape=(24, 20, 16), mach=0.0))
+    x = (np.arange(24) + 0.5) / 24
+    y = (np.arange(20) + 0.5) / 20
+    z = (np.arange(16) + 0.5) / 16
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    q[1] += 0.9 * np.sin(2 * np.pi * X) * np.cos(2 * np.pi * Y)
+    q[2] += 0.9 * np.sin(2 * np.pi * Y) * np.cos(2 * np.pi * Z)
+    q[3] += 0.9 * np.sin(2 * np.pi * Z)
+    q[4] += 0.5 * (q[1] ** 2 + q[2] ** 2 + q[3] ** 2) / q[0]
+    return p, q
+
+
+def _cases():
+    out = []
+    for axis in range(3):
+        out.append(("sod", axis))
+    out.append(("lax", 0))
+    out.append(("box", None))
+    return out
+
+
+def _problem(case):
+    kind, axis = case
+    if kind == "box":
+        return _shock_box()
+    p = _with_k(workloads.tube(kind, n=96, axis=axis, length=2.0 if kind == "lax" else 1.0))
+    return p, workloads.build(p)
+
+
+def _run_pair(p, q, precision, steps):
+    qo = [a.copy() for a in q]
+    o = oracle.Oracle(p)
+    ctx = ppm.Context.from_problem(p, precision=precision)
+    ctx.set_state(q)
+    oracle.Oracle.reset_counters()
+    for _ in range(steps):
+        dt = o.cfl_dt(qo, 0.5)
+        o.double_step(qo, dt)
+        ctx.step(dt)
+    qg = ctx.get_state()
+    ctx.close()
+    return qg, qo, oracle.Oracle.counters()["dissipative_faces"]
+
+
+@pytest.mark.parametrize("case", _cases())
+def test_shock_dissipation_fp64(case):
+    p, q = _problem(case)
+    qg, qo, nd = _run_pair(p, q, ppm.FP64_PLAIN, 12)
+    assert nd > 0
+    for v in range(9):
+        s = np.abs(qo[v]).max()
+        err = np.abs(qg[v] - qo[v]).max() / (s if s > 0 else 1.0)
+        assert err <= 1e-10, (case, v, err)
+
+
+@pytest.mark.parametrize("case", [c for c in _cases() if c[0] != "lax"])
+def test_shock_dissipation_fp32(case):
+    """The FP32 deviation form is built for low-Mach flow; on the Sod tube
+    and the forming-shock box it still holds the FP32 parity bar (the strong
+    Lax shock is checked in FP64 above)."""
+    p, q = _problem(case)
+    qg, qo, nd = _run_pair(p, q, ppm.FP32_DEVIATION, 12)
+    assert nd > 0
+    for v in (0, 4):
+        l1 = np.abs(qg[v] - qo[v]).sum() / np.abs(qo[v]).sum()
+        assert l1 <= 1e-5, (case, v, l1)
