@@ -27,6 +27,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -398,7 +399,8 @@ def run_ours(args):
             ens.set_region(i, (0, 0, 0), bp.shape, [t.contiguous() for t in qs], device=True)
             del qs
         torch.cuda.synchronize()
-        cache = os.environ.get("PPM_AUTOTUNE_CACHE", os.path.join(ROOT, "gpurun_out", "ppm_autotune.txt"))
+        cache = os.environ.get("PPM_AUTOTUNE_CACHE",
+                               os.path.join(tempfile.gettempdir(), "ppm_autotune.txt"))
         os.makedirs(os.path.dirname(cache), exist_ok=True)
         t_tune = time.perf_counter()
         from_cache = ens.tune(cache)

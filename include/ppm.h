@@ -130,7 +130,7 @@ int ppm_get_state(ppm_ctx *ctx, double *const q[9]);
 int ppm_set_region(ppm_ctx *ctx, const int lo[3], const int hi[3], const double *const q[9], int mem);
 int ppm_get_region(ppm_ctx *ctx, const int lo[3], const int hi[3], double *const q[9], int mem);
 
-/* CFL time step (spec dt rule): dt = cfl * dx / max over cells of
+/* CFL time step: dt = cfl * dx / max over cells of
  * (max_d |u_d| + c), c = sqrt(gamma p / rho), reduced in FP64 on the device.
  * 0 < cfl <= 1 (else ECFL).  dt_out may be NULL: the value then stays on the
  * device for ppm_step(ctx, 0).  Returns ENONPHYS if a previous pass flagged a
