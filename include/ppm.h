@@ -64,8 +64,8 @@ typedef enum {
 
 typedef enum { PPM_MEM_HOST = 0, PPM_MEM_DEVICE = 1 } ppm_mem;
 
-/* Hydrostatic base state (Sec. 1: "save the initial, spherically symmetric
- * state ... and subtract it out") on a uniform coordinate grid
+/* Hydrostatic base state (Sec. 1: the initial, spherically symmetric state is
+ * kept and removed from the scheme) on a uniform coordinate grid
  * s_i = s0 + i*ds, i < ntab (ntab >= 2); s = z (PLANE_Z) or r (CENTRAL),
  * linear interpolation, ends extrapolated from the last interval.
  * g is the signed acceleration along +s.  Arrays are host FP64 and copied. */
@@ -213,8 +213,8 @@ int ppm_totals_noalloc(const double *const q_dev[9], int nx, int ny, int nz, dou
  * kernel launch per pass for all boxes (a work list of pencil blocks, longest
  * pencils first), the whole double step captured as one CUDA graph.  Each
  * box keeps its own time step from its own CFL maximum.  This is the batched
- * form of the same passes (Sec. 4, "a large number of grid pencil updates that
- * are, pretty much, independent").
+ * form of the same passes (Sec. 4: the grid-pencil updates are nearly
+ * independent of one another).
  * ------------------------------------------------------------------------- */
 typedef struct ppm_ens ppm_ens;
 

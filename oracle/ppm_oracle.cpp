@@ -8,8 +8,9 @@
  * The paper (Woodward et al., Sec. 1 and Sec. 4) names the ingredients of the
  * pass but prints no formulas; each step below states the published method it
  * restates and the reading taken where the paper is silent:
- *   - perturbation form about a hydrostatic base state (Sec. 1, "subtract it
- *     out"): rho' = rho - rho0, E' = E - p0/(gamma-1), p' = p - p0;
+ *   - perturbation form about a hydrostatic base state (Sec. 1, the stored
+ *     initial state removed from the scheme): rho' = rho - rho0,
+ *     E' = E - p0/(gamma-1), p' = p - p0;
  *   - interface values one order higher than the parabola (Sec. 1): the
  *     fourth-order centred formula of Colella & Woodward (1984);
  *   - smoothness judged on the 5-cell stencil centred on the cell, no

@@ -10,7 +10,8 @@
  * Every function works on full (not base-subtracted) FP64 state arrays
  * q[9] = (rho, rho*u, rho*v, rho*w, E, FV, m_x, m_y, m_z), each nx*ny*nz with
  * x fastest (q[15] with the second and mixed moments when nmom == 9).  Internally each 1-D pass gathers one pencil at a time, subtracts
- * the hydrostatic base state (Sec. 1, "subtract it out ... very carefully"),
+ * the hydrostatic base state (Sec. 1: the stored initial state is removed
+ * from the scheme with care),
  * runs the pass step by step on whole-pencil arrays, and scatters back.
  *
  * Parity status of each step (what pins it, besides the CUDA path agreeing):
