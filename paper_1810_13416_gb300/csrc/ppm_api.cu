@@ -85,6 +85,9 @@ struct ppm_ctx {
     double *stage;             // FP64 staging for host regions
     long long stage_cells;
     double *diag_acc;          // diagnostics accumulators
+    double *base64;            // FP32 form: FP64 rho0 and p0/(gamma-1) of every cell, made by the
+                               // first diagnostics call (NULL: not yet, or no memory for it)
+    bool base64_tried;
     cudaGraph_t graph;
     cudaGraphExec_t gexec;
     cudaGraphNode_t dt_node;   // first node of the step graph (dt_kernel)
@@ -370,9 +373,22 @@ __global__ void rotate_kernel(SweepArgs<R> A, R *st, long long ncell, int nx, in
 
 // FP64 diagnostics: totals and shell averages.  acc layout: [0..6] totals,
 // [8..8+6*nbins) per bin (count, rho, p, FV, |u|, u_r^2), [7] max Mach bits.
+// FP64 base state of every cell for the diagnostics of the FP32 form:
+// rho0 and p0/(gamma-1), exactly as the state download forms them.
+__global__ void base_fill_kernel(SweepArgs<double> A64, double *b, long long ncell, int nx, int ny) {
+    const double gm1 = A64.gamma - 1.0;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < ncell;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(t % nx), j = (int)((t / nx) % ny), k = (int)(t / ((long long)nx * ny));
+        const Base<double> bb = cell_base(A64, i, j, k);
+        b[t] = bb.rho0;
+        b[ncell + t] = xdiv(bb.p0, gm1);
+    }
+}
+
 template <typename R, bool PLAIN>
 __global__ void diag_kernel(SweepArgs<double> A64, const R *st, long long ncell, int nx, int ny,
-                            int nbins, double rmax_, double *acc) {
+                            int nbins, double rmax_, double *acc, const double *base) {
     extern __shared__ double sbin[];
     __shared__ double stot[7][32];
     for (int b = threadIdx.x; b < 6 * nbins; b += blockDim.x) sbin[b] = 0.0;
@@ -390,8 +406,13 @@ __global__ void diag_kernel(SweepArgs<double> A64, const R *st, long long ncell,
          t += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(t % nx), j = (int)((t / nx) % ny), k = (int)(t / ((long long)nx * ny));
         const double x = coord(A64, 0, i), y = coord(A64, 1, j), z = coord(A64, 2, k);
-        double rho0, p0, r = -1.0;
-        if (A64.grav == 0) {
+        double rho0, p0, r = -1.0, E0 = 0.0;
+        if (base) {
+            // stored per cell (FP32 form): two loads instead of the lookup
+            rho0 = base[t];
+            E0 = base[ncell + t];
+            p0 = E0 * gm1;
+        } else if (A64.grav == 0) {
             rho0 = A64.rho0_c;
             p0 = A64.p0_c;
         } else {
@@ -415,7 +436,7 @@ __global__ void diag_kernel(SweepArgs<double> A64, const R *st, long long ncell,
         } else {
             rho = rho0 + (double)st[t];
             Ed = (double)st[4 * ncell + t];
-            E = p0 * igm1 + Ed;
+            E = (base ? E0 : p0 * igm1) + Ed;
         }
         const double mx = st[ncell + t], my = st[2 * ncell + t], mz = st[3 * ncell + t];
         double fv = st[5 * ncell + t];
@@ -641,6 +662,7 @@ void release(ppm_ctx *c) {
     if (c->ds_dev) cudaFree(c->ds_dev);
     if (c->stage) cudaFree(c->stage);
     if (c->diag_acc) cudaFree(c->diag_acc);
+    if (c->base64) cudaFree(c->base64);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
@@ -966,10 +988,21 @@ int ppm_diagnostics(ppm_ctx *c, double totals[7], int nbins, double rmax, double
     const SweepArgs<double> A = args64(c);
     if (c->prec == PPM_FP32_DEVIATION) {
         if (shm > 48 * 1024) CK(c, cudaFuncSetAttribute(diag_kernel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-        diag_kernel<float, false><<<g, 256, shm, c->stream>>>(A, (const float *)c->state, c->ncell, c->n[0], c->n[1], nbins, rmax, c->diag_acc);
+        if (!c->base64 && !c->base64_tried) {
+            c->base64_tried = true;
+            if (cudaMalloc(&c->base64, 2 * (size_t)c->ncell * sizeof(double)) != cudaSuccess) {
+                cudaGetLastError();   // no room: the kernel looks the base state up instead
+                c->base64 = nullptr;
+            } else {
+                base_fill_kernel<<<g, 256, 0, c->stream>>>(A, c->base64, c->ncell, c->n[0], c->n[1]);
+                c->launches++;
+                CK(c, cudaGetLastError());
+            }
+        }
+        diag_kernel<float, false><<<g, 256, shm, c->stream>>>(A, (const float *)c->state, c->ncell, c->n[0], c->n[1], nbins, rmax, c->diag_acc, c->base64);
     } else {
         if (shm > 48 * 1024) CK(c, cudaFuncSetAttribute(diag_kernel<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-        diag_kernel<double, true><<<g, 256, shm, c->stream>>>(A, (const double *)c->state, c->ncell, c->n[0], c->n[1], nbins, rmax, c->diag_acc);
+        diag_kernel<double, true><<<g, 256, shm, c->stream>>>(A, (const double *)c->state, c->ncell, c->n[0], c->n[1], nbins, rmax, c->diag_acc, nullptr);
     }
     c->launches++;
     CK(c, cudaGetLastError());
