@@ -396,7 +396,9 @@ __global__ void diag_kernel(SweepArgs<double> A64, const R *st, long long ncell,
     // FP64 is slow on this part: per cell one square root (r, central
     // gravity only) and two divisions; the table lookup multiplies by 1/ds
     // and the Mach number is maximised as its square.  Results agree with
-    // the exact-lookup formulas to rounding.
+    // the exact-lookup formulas to rounding.  With the cached base state
+    // (FP32 form) a cell needs neither its position nor a lookup unless
+    // shell averages are asked for.
     const double gam = A64.gamma, gm1 = A64.gamma - 1.0, igm1 = 1.0 / gm1;
     const double inv_ds = 1.0 / A64.ds;
     const double *t_r = A64.t_rho0, *t_p = A64.t_p0;
@@ -404,8 +406,13 @@ __global__ void diag_kernel(SweepArgs<double> A64, const R *st, long long ncell,
     double m2max = 0.0;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < ncell;
          t += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(t % nx), j = (int)((t / nx) % ny), k = (int)(t / ((long long)nx * ny));
-        const double x = coord(A64, 0, i), y = coord(A64, 1, j), z = coord(A64, 2, k);
+        double x = 0.0, y = 0.0, z = 0.0;
+        if (!base || nbins > 0) {
+            const int i = (int)(t % nx), j = (int)((t / nx) % ny), k = (int)(t / ((long long)nx * ny));
+            x = coord(A64, 0, i);
+            y = coord(A64, 1, j);
+            z = coord(A64, 2, k);
+        }
         double rho0, p0, r = -1.0, E0 = 0.0;
         if (base) {
             // stored per cell (FP32 form): two loads instead of the lookup
