@@ -293,7 +293,7 @@ def run_ours(args):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak,
                 "traffic": (tr * ncell if tr is not None else None),
-                "kernel": "ppm::sweep_kernel<float,false> (fused PPM+PPB pass)",
+                "kernel": "ppm::sweep_kernel<float,0,VEC,0,0,0,128> (fused PPM+PPB pass; x: VEC=1, y/z: VEC=0)",
                 "algorithmic_bytes_per_launch": BYTES_PER_CELL_PASS["f32"] * ncell,
                 "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})",
                 "pass_ms": {"avg_in_step": 1e3 * pass_s, "x": 1e3 * passes[0], "y": 1e3 * passes[1],
