@@ -82,7 +82,9 @@ struct ppm_ctx {
     float s4_0, inv_ds4;
     DevScal *ds_dev;
     double *h_pinned;          // 8 doubles of pinned host scratch
-    double *stage;             // FP64 staging for host regions
+    double *stage;             // FP64 staging for host regions (two buffers)
+    cudaStream_t xstream;      // host-region copies (created on first use)
+    cudaEvent_t ev_copy[2], ev_kern[2];
     long long stage_cells;
     double *diag_acc;          // diagnostics accumulators
     double *base64;            // FP32 form: FP64 rho0 and p0/(gamma-1) of every cell, made by the
@@ -223,11 +225,16 @@ __device__ __forceinline__ Base<R> cell_base(const SweepArgs<R> &A, int i, int j
     return base_at(A, xyz);
 }
 
+// The per-variable arrays of a region transfer, passed by value.
+struct RegionPtrs {
+    double *p[NVAR_MAX];
+};
+
 // FP64 full variables (a (hi-lo) box, x fastest) -> internal state.
 template <typename R, bool PLAIN>
 __global__ void set_region_kernel(SweepArgs<double> A64, R *st, long long ncell, int nx, int ny,
                                   int lo0, int lo1, int lo2, int bx, int by, int bz,
-                                  const double *const *src, long long src_off, int nvar) {
+                                  const RegionPtrs src, long long src_off, int nvar) {
     const long long nb = (long long)bx * by * bz;
     const double gm1 = A64.gamma - 1.0;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nb;
@@ -236,7 +243,7 @@ __global__ void set_region_kernel(SweepArgs<double> A64, R *st, long long ncell,
         const int gi = lo0 + i, gj = lo1 + j, gk = lo2 + k;
         const long long cidx = ((long long)gk * ny + gj) * nx + gi;
         double v[NVAR_MAX];
-        for (int q = 0; q < nvar; ++q) v[q] = src[q][src_off + t];
+        for (int q = 0; q < nvar; ++q) v[q] = src.p[q][src_off + t];
         if (!PLAIN) {
             const Base<double> b = cell_base(A64, gi, gj, gk);
             v[0] = xsub(v[0], b.rho0);
@@ -264,7 +271,7 @@ __global__ void set_region_kernel(SweepArgs<double> A64, R *st, long long ncell,
 template <typename R, bool PLAIN>
 __global__ void get_region_kernel(SweepArgs<double> A64, const R *st, long long ncell, int nx, int ny,
                                   int lo0, int lo1, int lo2, int bx, int by, int bz,
-                                  double *const *dst, long long dst_off, int nvar) {
+                                  const RegionPtrs dst, long long dst_off, int nvar) {
     const long long nb = (long long)bx * by * bz;
     const double gm1 = A64.gamma - 1.0;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nb;
@@ -280,7 +287,7 @@ __global__ void get_region_kernel(SweepArgs<double> A64, const R *st, long long 
             v[4] = xadd(xdiv(b.p0, gm1), v[4]);
             v[5] = signbit(v[5]) ? 1.0 + v[5] : v[5];
         }
-        for (int q = 0; q < nvar; ++q) dst[q][dst_off + t] = v[q];
+        for (int q = 0; q < nvar; ++q) dst.p[q][dst_off + t] = v[q];
     }
 }
 
@@ -591,6 +598,10 @@ int check_flags(ppm_ctx *c) {
     return PPM_OK;
 }
 
+// Host regions go through two device staging buffers in turn: the copies of
+// one chunk (on the context's copy stream) overlap the conversion kernel of
+// the previous chunk (on the context's stream), ordered by events.  Device
+// regions are converted in place by one kernel.  Both return when done.
 int region_io(ppm_ctx *c, const int lo[3], const int hi[3], double *const *arrs, int mem, bool to_dev) {
     if (!c || !lo || !hi || !arrs) return fail(c, PPM_EINVAL, "null argument");
     int b[3];
@@ -605,54 +616,81 @@ int region_io(ppm_ctx *c, const int lo[3], const int hi[3], double *const *arrs,
     if (mem != PPM_MEM_HOST && mem != PPM_MEM_DEVICE) return fail(c, PPM_EINVAL, "bad mem kind %d", mem);
     const SweepArgs<double> A = args64(c);
     const long long plane = (long long)b[0] * b[1];
-    // device pointer table (9 pointers) lives in the stage's header
-    double **ptab = reinterpret_cast<double **>(c->h_pinned + 8);
-    double **dptab = reinterpret_cast<double **>(c->diag_acc + 8 + 6 * MAX_BINS);
-    long long kchunk = (mem == PPM_MEM_DEVICE) ? b[2] : std::max(1LL, c->stage_cells / plane);
-    if (mem == PPM_MEM_HOST && !c->stage) {
-        if (cudaMalloc(&c->stage, (size_t)nv * c->stage_cells * sizeof(double)) != cudaSuccess) {
-            cudaGetLastError();
-            c->stage = nullptr;
-            return fail(c, PPM_ENOMEM, "cannot allocate the host-transfer staging buffer");
-        }
-    }
-    if (plane > c->stage_cells && mem == PPM_MEM_HOST) {
-        // one plane exceeds the stage: fall back to row chunks is not needed for
-        // grids up to stage size; reject explicitly
-        return fail(c, PPM_EINVAL, "region plane of %lld cells exceeds the staging buffer", plane);
-    }
-    for (long long k0 = 0; k0 < b[2]; k0 += kchunk) {
-        const long long nk = std::min(kchunk, (long long)b[2] - k0);
-        const long long cnt = plane * nk;
-        for (int q = 0; q < nv; ++q)
-            ptab[q] = (mem == PPM_MEM_DEVICE) ? arrs[q] + k0 * plane : c->stage + (long long)q * c->stage_cells;
-        CK(c, cudaMemcpyAsync(dptab, ptab, nv * sizeof(double *), cudaMemcpyHostToDevice, c->stream));
-        if (to_dev && mem == PPM_MEM_HOST)
-            for (int q = 0; q < nv; ++q)
-                CK(c, cudaMemcpyAsync(c->stage + (long long)q * c->stage_cells, arrs[q] + k0 * plane,
-                                      cnt * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    auto convert = [&](const RegionPtrs &ptrs, int lz, int nk, long long cnt) -> int {
         const int g = grid_for(cnt, 256);
-        const int lz = lo[2] + (int)k0;
         if (to_dev) {
             if (c->prec == PPM_FP32_DEVIATION)
-                set_region_kernel<float, false><<<g, 256, 0, c->stream>>>(A, (float *)c->state, c->ncell, c->n[0], c->n[1], lo[0], lo[1], lz, b[0], b[1], (int)nk, dptab, 0, nv);
+                set_region_kernel<float, false><<<g, 256, 0, c->stream>>>(A, (float *)c->state, c->ncell, c->n[0], c->n[1], lo[0], lo[1], lz, b[0], b[1], nk, ptrs, 0, nv);
             else
-                set_region_kernel<double, true><<<g, 256, 0, c->stream>>>(A, (double *)c->state, c->ncell, c->n[0], c->n[1], lo[0], lo[1], lz, b[0], b[1], (int)nk, dptab, 0, nv);
+                set_region_kernel<double, true><<<g, 256, 0, c->stream>>>(A, (double *)c->state, c->ncell, c->n[0], c->n[1], lo[0], lo[1], lz, b[0], b[1], nk, ptrs, 0, nv);
         } else {
             if (c->prec == PPM_FP32_DEVIATION)
-                get_region_kernel<float, false><<<g, 256, 0, c->stream>>>(A, (const float *)c->state, c->ncell, c->n[0], c->n[1], lo[0], lo[1], lz, b[0], b[1], (int)nk, dptab, 0, nv);
+                get_region_kernel<float, false><<<g, 256, 0, c->stream>>>(A, (const float *)c->state, c->ncell, c->n[0], c->n[1], lo[0], lo[1], lz, b[0], b[1], nk, ptrs, 0, nv);
             else
-                get_region_kernel<double, true><<<g, 256, 0, c->stream>>>(A, (const double *)c->state, c->ncell, c->n[0], c->n[1], lo[0], lo[1], lz, b[0], b[1], (int)nk, dptab, 0, nv);
+                get_region_kernel<double, true><<<g, 256, 0, c->stream>>>(A, (const double *)c->state, c->ncell, c->n[0], c->n[1], lo[0], lo[1], lz, b[0], b[1], nk, ptrs, 0, nv);
         }
         c->launches++;
         CK(c, cudaGetLastError());
-        if (!to_dev && mem == PPM_MEM_HOST)
-            for (int q = 0; q < nv; ++q)
-                CK(c, cudaMemcpyAsync(arrs[q] + k0 * plane, c->stage + (long long)q * c->stage_cells,
-                                      cnt * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-        // the pinned pointer table is reused by the next chunk
+        return PPM_OK;
+    };
+    if (mem == PPM_MEM_DEVICE) {
+        RegionPtrs ptrs;
+        for (int q = 0; q < nv; ++q) ptrs.p[q] = arrs[q];
+        const int r = convert(ptrs, lo[2], b[2], plane * b[2]);
+        if (r != PPM_OK) return r;
         CK(c, cudaStreamSynchronize(c->stream));
+        if (to_dev) c->have_speed = false;
+        return PPM_OK;
     }
+    if (plane > c->stage_cells)
+        return fail(c, PPM_EINVAL, "region plane of %lld cells exceeds the staging buffer", plane);
+    if (!c->stage) {
+        if (cudaMalloc(&c->stage, 2 * (size_t)nv * c->stage_cells * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            c->stage = nullptr;
+            return fail(c, PPM_ENOMEM, "cannot allocate the host-transfer staging buffers");
+        }
+    }
+    if (!c->xstream) {
+        CK(c, cudaStreamCreateWithFlags(&c->xstream, cudaStreamNonBlocking));
+        for (int i = 0; i < 2; ++i) {
+            CK(c, cudaEventCreateWithFlags(&c->ev_copy[i], cudaEventDisableTiming));
+            CK(c, cudaEventCreateWithFlags(&c->ev_kern[i], cudaEventDisableTiming));
+        }
+    }
+    const long long kchunk = std::max(1LL, c->stage_cells / plane);
+    int chunk = 0;
+    for (long long k0 = 0; k0 < b[2]; k0 += kchunk, ++chunk) {
+        const int h = chunk & 1;
+        double *stage = c->stage + (long long)h * nv * c->stage_cells;
+        const long long nk = std::min(kchunk, (long long)b[2] - k0);
+        const long long cnt = plane * nk;
+        RegionPtrs ptrs;
+        for (int q = 0; q < nv; ++q) ptrs.p[q] = stage + (long long)q * c->stage_cells;
+        if (to_dev) {
+            if (chunk >= 2) CK(c, cudaStreamWaitEvent(c->xstream, c->ev_kern[h], 0));   // stage h converted
+            for (int q = 0; q < nv; ++q)
+                CK(c, cudaMemcpyAsync(ptrs.p[q], arrs[q] + k0 * plane, cnt * sizeof(double),
+                                      cudaMemcpyHostToDevice, c->xstream));
+            CK(c, cudaEventRecord(c->ev_copy[h], c->xstream));
+            CK(c, cudaStreamWaitEvent(c->stream, c->ev_copy[h], 0));
+            const int r = convert(ptrs, lo[2] + (int)k0, (int)nk, cnt);
+            if (r != PPM_OK) return r;
+            CK(c, cudaEventRecord(c->ev_kern[h], c->stream));
+        } else {
+            if (chunk >= 2) CK(c, cudaStreamWaitEvent(c->stream, c->ev_copy[h], 0));    // stage h drained
+            const int r = convert(ptrs, lo[2] + (int)k0, (int)nk, cnt);
+            if (r != PPM_OK) return r;
+            CK(c, cudaEventRecord(c->ev_kern[h], c->stream));
+            CK(c, cudaStreamWaitEvent(c->xstream, c->ev_kern[h], 0));
+            for (int q = 0; q < nv; ++q)
+                CK(c, cudaMemcpyAsync(arrs[q] + k0 * plane, ptrs.p[q], cnt * sizeof(double),
+                                      cudaMemcpyDeviceToHost, c->xstream));
+            CK(c, cudaEventRecord(c->ev_copy[h], c->xstream));
+        }
+    }
+    CK(c, cudaStreamSynchronize(c->xstream));
+    CK(c, cudaStreamSynchronize(c->stream));
     if (to_dev) c->have_speed = false;
     return PPM_OK;
 }
@@ -667,6 +705,14 @@ void release(ppm_ctx *c) {
     if (c->t32) cudaFree(c->t32);
     if (c->t4) cudaFree(c->t4);
     if (c->ds_dev) cudaFree(c->ds_dev);
+    if (c->xstream) {
+        cudaStreamSynchronize(c->xstream);
+        for (int i = 0; i < 2; ++i) {
+            if (c->ev_copy[i]) cudaEventDestroy(c->ev_copy[i]);
+            if (c->ev_kern[i]) cudaEventDestroy(c->ev_kern[i]);
+        }
+        cudaStreamDestroy(c->xstream);
+    }
     if (c->stage) cudaFree(c->stage);
     if (c->diag_acc) cudaFree(c->diag_acc);
     if (c->base64) cudaFree(c->base64);
