@@ -305,3 +305,18 @@ def test_full_size_sphere_sampled_pencils_fp32(variant):
     tot, _, mm = ctx.diagnostics()
     assert np.isfinite(tot).all() and 0 < mm < 1
     ctx.close()
+
+
+@pytest.mark.parametrize("shape,bc", [((4, 4, 4), 0), ((8, 4, 5), 1), ((16, 4, 4), 0), ((8, 8, 8), 1)])
+@pytest.mark.parametrize("precision", [ppm.FP64_PLAIN, ppm.FP32_DEVIATION])
+def test_smallest_grids(shape, bc, precision):
+    """Extents at the minimum (4, the stencil reach) and the smallest 16-byte
+    x path (8): ghosts reach the far end of the pencil, periodic or walls."""
+    p = workloads.periodic_box(shape=shape)
+    p.dx = 1.0 / max(shape)
+    p.bc = (bc,) * 6
+    qg, qo = _run_pair(p, precision, 5)
+    if precision == ppm.FP64_PLAIN:
+        _assert_f64(qg, qo)
+    else:
+        _assert_f32(qg, qo)
