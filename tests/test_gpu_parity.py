@@ -320,3 +320,20 @@ def test_smallest_grids(shape, bc, precision):
         _assert_f64(qg, qo)
     else:
         _assert_f32(qg, qo)
+
+
+@pytest.mark.parametrize("which", ["strat128", "sphere96"])
+@pytest.mark.parametrize("precision", [ppm.FP64_PLAIN, ppm.FP32_DEVIATION])
+def test_gravity_configs_20_steps(which, precision):
+    """The stratified box at its configured 128^3 and the sphere recipe at
+    96^3, 20 double steps: FP64 within 1e-10 relative L-inf, FP32 within
+    1e-5 relative L1 on rho and E and 1e-7 on FV."""
+    if which == "strat128":
+        p = workloads.strat_box(shape=(128, 128, 128))
+    else:
+        p = workloads.sphere(n=96)
+    qg, qo = _run_pair(p, precision, 20)
+    if precision == ppm.FP64_PLAIN:
+        _assert_f64(qg, qo)
+    else:
+        _assert_f32(qg, qo)
