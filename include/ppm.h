@@ -111,24 +111,28 @@ typedef struct {
 
 /* Create a context: nx, ny, nz >= 4; gamma > 1; bc[6] per face
  * (-x,+x,-y,+y,-z,+z), periodic faces must come in pairs; grav, opt not NULL.
- * Allocates the state (9 values per cell in the chosen precision) and copies
- * the tables to the device.  EINVAL / ENOMEM / ECUDA. */
+ * Allocates the state (6 + nmom values per cell in the chosen precision) and
+ * copies the tables to the device.  EINVAL / ENOMEM / ECUDA. */
 int ppm_create(ppm_ctx **out, int nx, int ny, int nz, double gamma, const int bc[6],
                const ppm_gravity *grav, const ppm_options *opt);
 
-/* Upload the whole state from host FP64 arrays (full variables, layout above).
- * FP32 form: rho - rho0 and E - p0/(gamma-1) are formed in FP64 on the device
- * before rounding.  Invalidates the device time step (call ppm_cfl_dt). */
-int ppm_set_state(ppm_ctx *ctx, const double *const q[9]);
+/* Upload the whole state from host FP64 arrays (full variables, layout above;
+ * 6 + nmom arrays).  FP32 form: rho - rho0 and E - p0/(gamma-1) are formed in
+ * FP64 on the device before rounding; FV and the moments are clipped to their
+ * bounds.  Host arrays go through two device staging buffers in turn (copies
+ * overlapping the conversion); the call returns when done.  Invalidates the
+ * device time step (call ppm_cfl_dt). */
+int ppm_set_state(ppm_ctx *ctx, const double *const q[]);
 
 /* Download the whole state to host FP64 arrays (full variables). */
-int ppm_get_state(ppm_ctx *ctx, double *const q[9]);
+int ppm_get_state(ppm_ctx *ctx, double *const q[]);
 
 /* Same for the sub-box lo <= (i,j,k) < hi; arrays are (hi-lo) boxes with x
  * fastest, on the host (mem = PPM_MEM_HOST) or on the context's device
- * (PPM_MEM_DEVICE). */
-int ppm_set_region(ppm_ctx *ctx, const int lo[3], const int hi[3], const double *const q[9], int mem);
-int ppm_get_region(ppm_ctx *ctx, const int lo[3], const int hi[3], double *const q[9], int mem);
+ * (PPM_MEM_DEVICE).  EINVAL for an empty or out-of-range box, a NULL array,
+ * or (host) a box whose x-y plane exceeds 2^24 cells. */
+int ppm_set_region(ppm_ctx *ctx, const int lo[3], const int hi[3], const double *const q[], int mem);
+int ppm_get_region(ppm_ctx *ctx, const int lo[3], const int hi[3], double *const q[], int mem);
 
 /* CFL time step: dt = cfl * dx / max over cells of
  * (max_d |u_d| + c), c = sqrt(gamma p / rho), reduced in FP64 on the device.
@@ -139,9 +143,10 @@ int ppm_cfl_dt(ppm_ctx *ctx, double cfl, double *dt_out);
 
 /* One Strang double step (Sec. 1 / Sec. 4 directional splitting):
  * passes X Y Z [heating/damping] Z Y X [heating/damping, rotation increment],
- * all with the same dt, as one CUDA graph launch.  dt > 0 uses that value; dt <= 0 uses the device value from
- * the last ppm_cfl_dt or, after a step, the CFL maximum fused into that
- * step's last pass (ESTATE if there is none).  Never waits for the device. */
+ * all with the same dt, as one CUDA graph launch.  dt > 0 uses that value;
+ * dt <= 0 uses the device value from the last ppm_cfl_dt or, after a step,
+ * the CFL maximum fused into that step's last pass (ESTATE if there is
+ * none).  Never waits for the device. */
 int ppm_step(ppm_ctx *ctx, double dt);
 
 /* One 1-D pass along axis (0=x, 1=y, 2=z) with time step dt > 0.

@@ -895,24 +895,24 @@ int ppm_create(ppm_ctx **out, int nx, int ny, int nz, double gamma, const int bc
     return PPM_OK;
 }
 
-int ppm_set_region(ppm_ctx *c, const int lo[3], const int hi[3], const double *const q[9], int mem) {
+int ppm_set_region(ppm_ctx *c, const int lo[3], const int hi[3], const double *const q[], int mem) {
     return region_io(c, lo, hi, const_cast<double *const *>(q), mem, true);
 }
 
-int ppm_get_region(ppm_ctx *c, const int lo[3], const int hi[3], double *const q[9], int mem) {
+int ppm_get_region(ppm_ctx *c, const int lo[3], const int hi[3], double *const q[], int mem) {
     if (!c) return PPM_EINVAL;
     int r = region_io(c, lo, hi, q, mem, false);
     if (r != PPM_OK) return r;
     return check_flags(c);
 }
 
-int ppm_set_state(ppm_ctx *c, const double *const q[9]) {
+int ppm_set_state(ppm_ctx *c, const double *const q[]) {
     if (!c) return PPM_EINVAL;
     const int lo[3] = {0, 0, 0};
     return ppm_set_region(c, lo, c->n, q, PPM_MEM_HOST);
 }
 
-int ppm_get_state(ppm_ctx *c, double *const q[9]) {
+int ppm_get_state(ppm_ctx *c, double *const q[]) {
     if (!c) return PPM_EINVAL;
     const int lo[3] = {0, 0, 0};
     return ppm_get_region(c, lo, c->n, q, PPM_MEM_HOST);
