@@ -28,7 +28,6 @@ using namespace ppm;
 
 namespace {
 
-constexpr int NVAR = 9;        // stored values per cell (first moments only)
 constexpr int NVAR_MAX = 15;   // with the ten-value PPB
 constexpr int SWEEP_BLOCK = ppm::SWEEP_NB;
 constexpr int MAX_BINS = 1024;
@@ -81,7 +80,6 @@ struct ppm_ctx {
     int ntab4;
     float s4_0, inv_ds4;
     DevScal *ds_dev;
-    double *h_pinned;          // 8 doubles of pinned host scratch
     double *stage;             // FP64 staging for host regions (two buffers)
     cudaStream_t xstream;      // host-region copies (created on first use)
     cudaEvent_t ev_copy[2], ev_kern[2];
@@ -716,7 +714,6 @@ void release(ppm_ctx *c) {
     if (c->stage) cudaFree(c->stage);
     if (c->diag_acc) cudaFree(c->diag_acc);
     if (c->base64) cudaFree(c->base64);
-    if (c->h_pinned) cudaFreeHost(c->h_pinned);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
 
@@ -875,10 +872,9 @@ int ppm_create(ppm_ctx **out, int nx, int ny, int nz, double gamma, const int bc
         cudaMalloc(&c->t4, h4.size() * sizeof(float4)) != cudaSuccess ||
         cudaMalloc(&c->t32, h32.size() * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&c->ds_dev, sizeof(DevScal)) != cudaSuccess ||
-        cudaMalloc(&c->diag_acc, (8 + 6 * MAX_BINS + 16) * sizeof(double)) != cudaSuccess ||
-        cudaMallocHost(&c->h_pinned, 64 * sizeof(double)) != cudaSuccess) {
+        cudaMalloc(&c->diag_acc, (8 + 6 * MAX_BINS) * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
-        fail(c, PPM_ENOMEM, "cannot allocate tables / staging");
+        fail(c, PPM_ENOMEM, "cannot allocate tables / accumulators");
         return bail(PPM_ENOMEM);
     }
     if (cudaMemcpy(c->t64, h64.data(), h64.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
