@@ -164,8 +164,8 @@ def _upload(ctx, p, torch, slab=64):
 
 
 def _cpu_baseline(n_cpu: int, steps: int, warmup: int):
-    """The oracle as it stands, on the host cores, on a 128^3 sample of the
-    same sphere recipe."""
+    """The oracle as it stands, on the host cores, on an n_cpu^3 sample of
+    the same sphere recipe."""
     import oracle
     import workloads
     oracle.build()
@@ -431,7 +431,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        cb = _cpu_baseline(args.cpu_n, 1, 1)
+        cb = _cpu_baseline(args.cpu_n, args.cpu_steps, 1)
         cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
 
     if rank == 0:
@@ -459,7 +459,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--fp64-steps", type=int, default=2)
-    ap.add_argument("--cpu-n", type=int, default=128)
+    ap.add_argument("--cpu-n", type=int, default=256,
+                    help="edge of the sphere sample the oracle runs for the CPU baseline")
+    ap.add_argument("--cpu-steps", type=int, default=6,
+                    help="timed oracle double steps of the CPU baseline (about 10 s on 16 cores)")
     ap.add_argument("--flops-per-cell", type=float, default=464.0,
                     help="algorithmic FP32 flops per cell and pass (oracle census)")
     ap.add_argument("--no-e2e", action="store_true")
