@@ -1,0 +1,337 @@
+"""A second, separately written statement of one pass of the four-value
+PPM+PPB method: whole-grid, array-at-a-time numpy (every pencil of the grid
+at once, the pass axis last), against which the pencil-by-pencil C++ oracle
+is checked.  Same readings of the paper, independent code: boundary ghosts
+by index arrays, base state by vectorised table lookups, every step as
+shifted-array arithmetic.  Plane-parallel or no gravity; no sources.
+"""
+import numpy as np
+
+G = 4
+C_SMOOTH, EPS_SMOOTH = 0.5, 1e-9
+EPS_SHOCK, OMEGA1, OMEGA2 = 0.33, 0.75, 10.0
+P_FLOOR = 1e-10
+
+
+def _lerp(tab, s0, ds, s):
+    u = (s - s0) / ds
+    i = np.clip(np.floor(u), 0, len(tab) - 2).astype(int)
+    w = u - i
+    return tab[i] + w * (tab[i + 1] - tab[i])
+
+
+def _ghost_index(n, periodic):
+    """Source cell and mirror flag of the n + 2G cells of a pencil."""
+    i = np.arange(-G, n + G)
+    if periodic:
+        return np.mod(i, n), np.zeros(i.shape, bool)
+    src = np.where(i < 0, -1 - i, np.where(i >= n, 2 * n - 1 - i, i))
+    return src, (i < 0) | (i >= n)
+
+
+def _face_pos(n, periodic):
+    """Position (cells from the low end) of faces j + 1/2, j in [-G, n+G)."""
+    P = np.arange(-G, n + G) + 1
+    if periodic:
+        return np.where((P >= n) | (P < 0), np.mod(P, n), P)
+    return np.where(P < 0, -P, np.where(P > n, 2 * n - P, P))
+
+
+def sweep(p, q, axis, dt):
+    """One pass along `axis` of the 9 full-variable arrays q (z, y, x)."""
+    t = p.tables
+    gam, gm1 = p.gamma, p.gamma - 1.0
+    n = p.shape[axis]
+    t1, t2 = (axis + 1) % 3, (axis + 2) % 3
+    assert p.bc[2 * axis] == p.bc[2 * axis + 1] and p.shape[axis] > G
+    periodic = p.bc[2 * axis] == 0
+    npax = 2 - axis
+    mv = lambda a: np.moveaxis(a, npax, -1)           # pass axis last
+    src, flip = _ghost_index(n, periodic)
+    sg = np.where(flip, -1.0, 1.0)
+    take = lambda a: np.take(mv(a), src, axis=-1)
+    rho_full = take(q[0])
+    mn = take(q[1 + axis]) * sg
+    m1 = take(q[1 + t1])
+    m2 = take(q[1 + t2])
+    E = take(q[4])
+    fv = take(q[5])
+    on = take(q[6 + axis]) * sg
+    o1 = take(q[6 + t1])
+    o2 = take(q[6 + t2])
+    # cell positions along every axis (for the base state: plane gravity in z)
+    shape = mv(q[0]).shape[:-1] + (n + 2 * G,)
+    coord = [p.origin[d] + (np.arange(p.shape[d]) + 0.5) * p.dx for d in range(3)]
+    if p.grav == 0:
+        rho0c = np.full(shape, t.rho0[0])
+        p0c = np.full(shape, t.p0[0])
+        gc = np.zeros(shape)
+        rho0f = np.full(shape, t.rho0[0])
+        p0f = np.full(shape, t.p0[0])
+    else:
+        assert p.grav == 1
+        if axis == 2:
+            z = coord[2][src]
+            zf = p.origin[2] + _face_pos(n, periodic) * p.dx
+        else:
+            # an x or y pass: z is the leading array axis, constant along the pencil
+            z = np.broadcast_to(coord[2][:, None, None], shape)
+            zf = z
+        rho0c = np.broadcast_to(_lerp(t.rho0, t.s0, t.ds, z), shape)
+        p0c = np.broadcast_to(_lerp(t.p0, t.s0, t.ds, z), shape)
+        gz = np.broadcast_to(_lerp(t.g, t.s0, t.ds, z), shape)
+        gc = gz * sg if axis == 2 else np.zeros(shape)
+        rho0f = np.broadcast_to(_lerp(t.rho0, t.s0, t.ds, zf), shape)
+        p0f = np.broadcast_to(_lerp(t.p0, t.s0, t.ds, zf), shape)
+    rd = rho_full - rho0c
+    ed = E - p0c / gm1
+    # primitives
+    rho = rho0c + rd
+    u, v, w = mn / rho, m1 / rho, m2 / rho
+    pd = gm1 * (ed - 0.5 * (mn * u + (m1 * v + m2 * w)))
+    pf = p0c + pd
+    c2 = gam * pf / rho
+    cs = np.sqrt(c2)
+    W = [rd, u, v, w, pd]
+    def at(a, k, lo, hi):
+        """a[i + k] for i in [lo, hi) (pencil indices, ghosts negative)."""
+        return a[..., G + lo + k:G + hi + k]
+    # interface values of faces j + 1/2, j in [-3, n+2)
+    jl, jh = -3, n + 2
+    af = [(7.0 * (at(a, 0, jl, jh) + at(a, 1, jl, jh)) - (at(a, -1, jl, jh) + at(a, 2, jl, jh))) * (1.0 / 12.0)
+          for a in W]
+    # smoothness weights, flattening, parabolas of cells i in [-2, n+2)
+    il, ih = -2, n + 2
+    scales = [at(rho, 0, il, ih), at(cs, 0, il, ih), at(cs, 0, il, ih), at(cs, 0, il, ih), at(pf, 0, il, ih)]
+    wgt = []
+    for a, sc in zip(W, scales):
+        d1m2 = at(a, -1, il, ih) - at(a, -2, il, ih)
+        d1m1 = at(a, 0, il, ih) - at(a, -1, il, ih)
+        d10 = at(a, 1, il, ih) - at(a, 0, il, ih)
+        d1p1 = at(a, 2, il, ih) - at(a, 1, il, ih)
+        d2m, d20, d2p = d1m1 - d1m2, d10 - d1m1, d1p1 - d10
+        T = np.maximum(np.abs(d20 - d2m), np.abs(d2p - d20))
+        S = np.maximum(np.maximum(np.abs(d1m1), np.abs(d10)),
+                       np.maximum(np.maximum(np.abs(d2m), np.abs(d20)), np.abs(d2p)))
+        fl = EPS_SMOOTH * sc
+        x = T - C_SMOOTH * S - fl
+        with np.errstate(divide="ignore", invalid="ignore"):
+            wgt.append(np.where(x > 0, np.minimum(1.0, x / ((1 - C_SMOOTH) * S + fl)), 0.0))
+    dp1 = at(pd, 1, il, ih) - at(pd, -1, il, ih)
+    dp2 = at(pd, 2, il, ih) - at(pd, -2, il, ih)
+    pmin = np.minimum(at(pf, 1, il, ih), at(pf, -1, il, ih))
+    shock = (np.abs(dp1) > EPS_SHOCK * pmin) & (at(u, -1, il, ih) - at(u, 1, il, ih) > 0)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        r = np.where(dp2 != 0, dp1 / dp2, 1.0)
+    flat = np.where(shock, np.clip(OMEGA2 * (r - OMEGA1), 0.0, 1.0), 0.0)
+    PL, PR, PD, P6 = [], [], [], []
+    for a, afv, wv in zip(W, af, wgt):
+        ac = at(a, 0, il, ih)
+        aL = afv[..., (il - 1) - jl:(ih - 1) - jl]
+        aR = afv[..., il - jl:ih - jl]
+        aL = np.where(flat > 0, aL + flat * (ac - aL), aL)
+        aR = np.where(flat > 0, aR + flat * (ac - aR), aR)
+        am, ap = at(a, -1, il, ih), at(a, 1, il, ih)
+        cL = np.clip(aL, np.minimum(am, ac), np.maximum(am, ac))
+        cR = np.clip(aR, np.minimum(ac, ap), np.maximum(ac, ap))
+        ext = (cR - ac) * (ac - cL) <= 0
+        da = cR - cL
+        dm = ac - 0.5 * (cL + cR)
+        d6 = da * da * (1.0 / 6.0)
+        fixL = da * dm > d6
+        fixR = ~fixL & (-d6 > da * dm)
+        nL = np.where(ext, ac, np.where(fixL, 3.0 * ac - 2.0 * cR, cL))
+        nR = np.where(ext, ac, np.where(fixR, 3.0 * ac - 2.0 * cL, cR))
+        aL = np.where(wv > 0, aL + wv * (nL - aL), aL)
+        aR = np.where(wv > 0, aR + wv * (nR - aR), aR)
+        PL.append(aL)
+        PR.append(aR)
+        PD.append(aR - aL)
+        P6.append(6.0 * (ac - 0.5 * (aL + aR)))
+    fR = lambda k, s: PR[k] - 0.5 * s * (PD[k] - (1.0 - (2.0 / 3.0) * s) * P6[k])
+    fL = lambda k, s: PL[k] + 0.5 * s * (PD[k] + (1.0 - (2.0 / 3.0) * s) * P6[k])
+    dtdx = dt / p.dx
+    uc, cc, c2c, rc = at(u, 0, il, ih), at(cs, 0, il, ih), at(c2, 0, il, ih), at(rho, 0, il, ih)
+    C = rc * cc
+    lm, l0, lp = uc - cc, uc, uc + cc
+    hg = 0.5 * dt * ((at(rd, 0, il, ih) / rc) * at(gc, 0, il, ih))
+    # right edges (left states of faces i + 1/2)
+    sp = np.maximum(lp, 0.0) * dtdx
+    WLs = [fR(k, sp) for k in range(5)]
+    ref = list(WLs)
+    s0 = l0 * dtdx
+    on0 = l0 > 0
+    WLs[0] = np.where(on0, WLs[0] - ((ref[0] - fR(0, s0)) - (ref[4] - fR(4, s0)) / c2c), WLs[0])
+    WLs[2] = np.where(on0, WLs[2] - (ref[2] - fR(2, s0)), WLs[2])
+    WLs[3] = np.where(on0, WLs[3] - (ref[3] - fR(3, s0)), WLs[3])
+    sm = lm * dtdx
+    onm = lm > 0
+    Am = 0.5 * ((ref[4] - fR(4, sm)) - C * (ref[1] - fR(1, sm)))
+    WLs[0] = np.where(onm, WLs[0] - Am / c2c, WLs[0])
+    WLs[1] = np.where(onm, WLs[1] + Am / C, WLs[1])
+    WLs[4] = np.where(onm, WLs[4] - Am, WLs[4])
+    WLs[1] = WLs[1] + hg
+    # left edges (right states of faces i - 1/2)
+    smm = np.maximum(-lm, 0.0) * dtdx
+    WRs = [fL(k, smm) for k in range(5)]
+    ref = list(WRs)
+    s0 = -l0 * dtdx
+    on0 = l0 < 0
+    WRs[0] = np.where(on0, WRs[0] - ((ref[0] - fL(0, s0)) - (ref[4] - fL(4, s0)) / c2c), WRs[0])
+    WRs[2] = np.where(on0, WRs[2] - (ref[2] - fL(2, s0)), WRs[2])
+    WRs[3] = np.where(on0, WRs[3] - (ref[3] - fL(3, s0)), WRs[3])
+    s1 = -lp * dtdx
+    onp = lp < 0
+    Ap_ = 0.5 * ((ref[4] - fL(4, s1)) + C * (ref[1] - fL(1, s1)))
+    WRs[0] = np.where(onp, WRs[0] - Ap_ / c2c, WRs[0])
+    WRs[1] = np.where(onp, WRs[1] - Ap_ / C, WRs[1])
+    WRs[4] = np.where(onp, WRs[4] - Ap_, WRs[4])
+    WRs[1] = WRs[1] + hg
+    # faces j + 1/2, j in [-2, n+1): left state from cell j, right from cell j+1
+    fl_, fh_ = -2, n + 1
+    L = [a[..., fl_ - il:fh_ - il] for a in WLs]
+    Rt = [a[..., fl_ + 1 - il:fh_ + 1 - il] for a in WRs]
+    r0 = at(rho0f, 0, fl_, fh_)
+    p0 = at(p0f, 0, fl_, fh_)
+    rdL, uL, pdL = L[0], L[1], L[4]
+    rdR, uR, pdR = Rt[0], Rt[1], Rt[4]
+    rL, pL, rR, pR = r0 + rdL, p0 + pdL, r0 + rdR, p0 + pdR
+    CL, CR = np.sqrt(gam * pL * rL), np.sqrt(gam * pR * rR)
+    pfl = P_FLOOR * np.minimum(pL, pR)
+    den = CL + CR
+    pst = pdL + CL * (CR * (uL - uR) + (pdR - pdL)) / den
+    pst = np.where(p0 + pst < pfl, pfl - p0, pst)
+    kk = (gam + 1.0) / (2.0 * gam)
+    WLi = CL * np.sqrt(1.0 + kk * (pst - pdL) / pL)
+    WRi = CR * np.sqrt(1.0 + kk * (pst - pdR) / pR)
+    den = WLi + WRi
+    pst = pdL + WLi * (WRi * (uL - uR) + (pdR - pdL)) / den
+    ust = uL + (WRi * (uR - uL) + (pdL - pdR)) / den
+    pst = np.where(p0 + pst < pfl, pfl - p0, pst)
+    if not periodic:
+        jj = np.arange(fl_, fh_)
+        ust = np.where((jj == -1) | (jj == n - 1), 0.0, ust)
+    left = ust >= 0
+    rds, pds = np.where(left, rdL, rdR), np.where(left, pdL, pdR)
+    rs, pss = np.where(left, rL, rR), np.where(left, pL, pR)
+    vst, wst = np.where(left, L[2], Rt[2]), np.where(left, L[3], Rt[3])
+    dps = pst - pds
+    rdst = rds + rs * dps / (gam * pss + 0.5 * gm1 * dps)
+    Fr = (r0 + rdst) * ust
+    gg1 = gam / gm1
+    Fn = Fr * ust + pst
+    Ft1, Ft2 = Fr * vst, Fr * wst
+    FE = ust * (gg1 * pst + gg1 * p0) + 0.5 * (ust * ust + (vst * vst + wst * wst)) * Fr
+    # cells i in [-1, n+1): faces i - 1/2 (index i-1) and i + 1/2 (index i)
+    cl_, ch_ = -1, n + 1
+    f_m = lambda F: F[..., (cl_ - 1) - fl_:(ch_ - 1) - fl_]
+    f_p = lambda F: F[..., cl_ - fl_:ch_ - fl_]
+    gcell = at(gc, 0, cl_, ch_)
+    rd0 = at(rd, 0, cl_, ch_)
+    rdn = rd0 - dtdx * (f_p(Fr) - f_m(Fr))
+    mnn = at(mn, 0, cl_, ch_) - dtdx * (f_p(Fn) - f_m(Fn)) + dt * gcell * (0.5 * (rd0 + rdn))
+    m1n = at(m1, 0, cl_, ch_) - dtdx * (f_p(Ft1) - f_m(Ft1))
+    m2n = at(m2, 0, cl_, ch_) - dtdx * (f_p(Ft2) - f_m(Ft2))
+    edn = at(ed, 0, cl_, ch_) - dtdx * (f_p(FE) - f_m(FE)) + dt * gcell * (0.5 * (f_m(Fr) + f_p(Fr)))
+    # PPB profiles of cells [-2, n+2): own FV and slope, curvature from neighbours
+    F = at(fv, 0, il, ih)
+    mm = at(on, 0, il, ih)
+    a2 = 0.25 * (at(on, 1, il, ih) - at(on, -1, il, ih))
+    ep = 0.5 * mm + a2 * (1.0 / 6.0)
+    em = a2 * (1.0 / 6.0) - 0.5 * mm
+    gmax, gmin = np.maximum(ep, em), np.minimum(ep, em)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        xv = np.where(a2 != 0, -mm / (2.0 * a2), 1.0)
+        gv = mm * xv + a2 * (xv * xv - 1.0 / 12.0)
+        inside = (a2 != 0) & (np.abs(xv) < 0.5)
+        gmax = np.where(inside, np.maximum(gmax, gv), gmax)
+        gmin = np.where(inside, np.minimum(gmin, gv), gmin)
+        th = np.ones_like(F)
+        th = np.where(F + gmax > 1.0, np.minimum(th, (1.0 - F) / gmax), th)
+        th = np.where(F + gmin < 0.0, np.minimum(th, F / (-gmin)), th)
+    me, ae = th * mm, th * a2
+    # transfers across faces [-2, n+1): donor = upwind cell (index j or j+1)
+    sig = ust * dtdx
+    phi = dtdx * Fr
+    fromleft = sig >= 0
+    s = np.abs(sig)
+    M1 = 0.5 - 0.5 * s
+    M2 = 0.25 - 0.5 * s + s * s * (1.0 / 3.0)
+    M3 = 0.125 - 0.375 * s + 0.5 * s * s - 0.25 * s * s * s
+    M1 = np.where(fromleft, M1, -M1)
+    M3 = np.where(fromleft, M3, -M3)
+    donor = lambda a: np.where(fromleft, a[..., fl_ - il:fh_ - il], a[..., fl_ + 1 - il:fh_ + 1 - il])
+    Fd, med, aed = donor(F), donor(me), donor(ae)
+    o1d, o2d = donor(at(o1, 0, il, ih)), donor(at(o2, 0, il, ih))
+    phibar = Fd + med * M1 + aed * (M2 - 1.0 / 12.0)
+    psibar = Fd * M1 + med * M2 + aed * (M3 - M1 * (1.0 / 12.0))
+    GL, GH = phi * Fd, phi * phibar
+    KL, KH = phi * Fd * M1, phi * psibar
+    T1, T2 = phi * o1d, phi * o2d
+    PHI, KM = phi, phi * M1
+    # FCT factors of cells [-1, n+1)
+    rold = at(rho0c, 0, cl_, ch_) + rd0
+    rnew = at(rho0c, 0, cl_, ch_) + rdn
+    fvc = at(fv, 0, cl_, ch_)
+    cLo = rold * fvc - (f_p(GL) - f_m(GL))
+    FVL = cLo / rnew
+    Apl, Amn = f_p(GH) - f_p(GL), f_m(GH) - f_m(GL)
+    Pp = np.maximum(0.0, Amn) - np.minimum(0.0, Apl)
+    Pm = np.maximum(0.0, Apl) - np.minimum(0.0, Amn)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        Rp = np.where(Pp > 0, np.clip((1.0 - FVL) * rnew / Pp, 0.0, 1.0), 0.0)
+        Rm = np.where(Pm > 0, np.clip(FVL * rnew / Pm, 0.0, 1.0), 0.0)
+    # limited transfers of faces [-1, n): cells j (index j+1 in [-1, n+1)) and j+1
+    ff = slice(-1 - fl_, n - fl_)
+    A = GH[..., ff] - GL[..., ff]
+    Rp_j, Rm_j = Rp[..., 0:n + 1], Rm[..., 0:n + 1]
+    Rp_j1, Rm_j1 = Rp[..., 1:n + 2], Rm[..., 1:n + 2]
+    Cf = np.where(A >= 0, np.minimum(Rp_j1, Rm_j), np.minimum(Rp_j, Rm_j1))
+    Gf = GL[..., ff] + Cf * A
+    Kf = KL[..., ff] + Cf * (KH[..., ff] - KL[..., ff])
+    T1f, T2f, PHIf, KMf = T1[..., ff], T2[..., ff], PHI[..., ff], KM[..., ff]
+    sgf = sig[..., ff]
+    # update of cells [0, n): faces i - 1/2 (index i in [-1,n) -> i) and i + 1/2 (i+1)
+    q_ = lambda a: a[..., 0:n]        # face i - 1/2
+    p_ = lambda a: a[..., 1:n + 1]    # face i + 1/2
+    ro = rold[..., 1:n + 1]
+    rn = rnew[..., 1:n + 1]
+    fc = fvc[..., 1:n + 1]
+    smv, spv = q_(sgf), p_(sgf)
+    cold = ro * fc
+    outp = spv >= 0
+    inm = smv >= 0
+    shp, shm = spv + 1.0, smv - 1.0
+    c_out = np.where(outp, p_(Gf), 0.0) + np.where(inm, 0.0, -q_(Gf))
+    z_out = np.where(outp, p_(Kf), 0.0) + np.where(inm, 0.0, -q_(Kf))
+    m_out = np.where(outp, p_(PHIf), 0.0) + np.where(inm, 0.0, -q_(PHIf))
+    zr_out = np.where(outp, p_(KMf), 0.0) + np.where(inm, 0.0, -q_(KMf))
+    z_in = np.where(outp, 0.0, -p_(Kf) - p_(Gf) * shp) + np.where(inm, q_(Kf) + q_(Gf) * shm, 0.0)
+    zr_in = np.where(outp, 0.0, -p_(KMf) - p_(PHIf) * shp) + np.where(inm, q_(KMf) + q_(PHIf) * shm, 0.0)
+    sbar = 0.5 * (smv + spv)
+    dZc = (cold - c_out) * sbar + z_in - z_out
+    Zr = (ro - m_out) * sbar + zr_in - zr_out
+    dPhi = p_(PHIf) - q_(PHIf)
+    dG = p_(Gf) - q_(Gf)
+    fvn = np.clip(fc + (fc * dPhi - dG) / rn, 0.0, 1.0)
+    onc, o1c, o2c = on[..., G:G + n], o1[..., G:G + n], o2[..., G:G + n]
+    onn = onc + (onc * dPhi + 12.0 * (dZc - fvn * Zr)) / rn
+    o1n = o1c + (o1c * dPhi - (p_(T1f) - q_(T1f))) / rn
+    o2n = o2c + (o2c * dPhi - (p_(T2f) - q_(T2f))) / rn
+    bnd = 6.0 * fvn * (1.0 - fvn)
+    onn, o1n, o2n = (np.clip(a, -bnd, bnd) for a in (onn, o1n, o2n))
+    # back to full variables, physical frame
+    inner = lambda a: a[..., 1:n + 1]
+    out = [None] * 9
+    r0c = rho0c[..., G:G + n]
+    p0cc = p0c[..., G:G + n]
+    out[0] = r0c + inner(rdn)
+    out[1 + axis] = inner(mnn)
+    out[1 + t1] = inner(m1n)
+    out[1 + t2] = inner(m2n)
+    out[4] = p0cc / gm1 + inner(edn)
+    out[5] = fvn
+    out[6 + axis] = onn
+    out[6 + t1] = o1n
+    out[6 + t2] = o2n
+    return [np.ascontiguousarray(np.moveaxis(a, -1, npax)) for a in out]
