@@ -85,9 +85,10 @@ struct ppm_ctx {
     cudaEvent_t ev_copy[2], ev_kern[2];
     long long stage_cells;
     double *diag_acc;          // diagnostics accumulators
-    double *base64;            // FP32 form: FP64 rho0 and p0/(gamma-1) of every cell, made by the
-                               // first diagnostics call (NULL: not yet, or no memory for it)
-    bool base64_tried;
+    float *base32;             // FP32 form, made by the first diagnostics call (NULL: not yet, or
+                               // no memory for it): per cell rho0 as two floats hi + lo, and p0
+    bool base32_tried;
+    double base_sum[2];        // FP64 grid sums of rho0 and p0/(gamma-1) (with base32)
     cudaGraph_t graph;
     cudaGraphExec_t gexec;
     cudaGraphNode_t dt_node;   // first node of the step graph (dt_kernel)
@@ -378,32 +379,186 @@ __global__ void rotate_kernel(SweepArgs<R> A, R *st, long long ncell, int nx, in
 
 // FP64 diagnostics: totals and shell averages.  acc layout: [0..6] totals,
 // [8..8+6*nbins) per bin (count, rho, p, FV, |u|, u_r^2), [7] max Mach bits.
-// FP64 base state of every cell for the diagnostics of the FP32 form:
-// rho0 and p0/(gamma-1), exactly as the state download forms them.
-__global__ void base_fill_kernel(SweepArgs<double> A64, double *b, long long ncell, int nx, int ny) {
+
+// Base state of every cell for the diagnostics of the FP32 form: rho0 as an
+// unevaluated sum hi + lo of two floats (hi = rho0 rounded to float, lo = the
+// remainder rounded: 48 significant bits together), p0 rounded to float (the
+// Mach number and shell pressures only), and the FP64 grid sums of rho0 and
+// of p0/(gamma-1) as the state download forms them (sums[0], sums[1]).
+__global__ void base_fill_kernel(SweepArgs<double> A64, float *hi, float *lo, float *p0f, double *sums,
+                                 long long ncell, int nx, int ny) {
     const double gm1 = A64.gamma - 1.0;
+    double sr = 0.0, se = 0.0;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < ncell;
          t += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(t % nx), j = (int)((t / nx) % ny), k = (int)(t / ((long long)nx * ny));
         const Base<double> bb = cell_base(A64, i, j, k);
-        b[t] = bb.rho0;
-        b[ncell + t] = xdiv(bb.p0, gm1);
+        const float h = (float)bb.rho0;
+        hi[t] = h;
+        lo[t] = (float)(bb.rho0 - (double)h);
+        p0f[t] = (float)bb.p0;
+        sr += bb.rho0;
+        se += xdiv(bb.p0, gm1);
+    }
+    __shared__ double red[2][32];
+    for (int o = 16; o > 0; o >>= 1) {
+        sr += __shfl_xor_sync(0xffffffffu, sr, o);
+        se += __shfl_xor_sync(0xffffffffu, se, o);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        red[0][w] = sr;
+        red[1][w] = se;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        double v = 0.0;
+        for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) v += red[threadIdx.x][ww];
+        atomicAdd(sums + threadIdx.x, v);
     }
 }
 
-template <typename R, bool PLAIN>
-__global__ void diag_kernel(SweepArgs<double> A64, const R *st, long long ncell, int nx, int ny,
-                            int nbins, double rmax_, double *acc, const double *base) {
-    extern __shared__ double sbin[];
+// A float pair (s, c) standing for s + c, summed with Knuth's TwoSum: the
+// rounding error of every addition is kept exactly and collected in c.
+struct Sum2 {
+    float s, c;
+};
+__device__ __forceinline__ void sum2_add(Sum2 &a, float x) {
+    const float t = a.s + x;
+    const float bp = t - a.s;
+    a.c += (a.s - (t - bp)) + (x - bp);
+    a.s = t;
+}
+
+// Totals of every cell's bin (shell averages): FP64 per cell, shared by both
+// diagnostics kernels.
+__device__ __forceinline__ void bin_cell(double *sbin, int nbins, double rmax_, double x, double y, double z,
+                                         double r, double rho, double p, double fv, double mx, double my,
+                                         double mz) {
+    if (r < 0.0) r = sqrt(x * x + y * y + z * z);
+    const int bin = (int)floor(r / rmax_ * nbins);
+    if (bin >= 0 && bin < nbins) {
+        const double rinv = 1.0 / rho;
+        const double spd = sqrt(mx * mx + my * my + mz * mz) * rinv;
+        const double ur = r > 0.0 ? (mx * x + my * y + mz * z) * rinv / r : 0.0;
+        double *a = sbin + 6 * bin;
+        atomicAdd(a + 0, 1.0);
+        atomicAdd(a + 1, rho);
+        atomicAdd(a + 2, p);
+        atomicAdd(a + 3, fv);
+        atomicAdd(a + 4, spd);
+        atomicAdd(a + 5, ur * ur);
+    }
+}
+
+// Block reduction of the seven totals, the Mach maximum and the bins into acc.
+__device__ __forceinline__ void diag_flush_block(const double tot[7], double m2max, double *sbin, int nbins,
+                                                 double *acc) {
     __shared__ double stot[7][32];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    for (int m = 0; m < 7; ++m) {
+        double v = tot[m];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (l == 0) stot[m][w] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 7) {
+        double v = 0.0;
+        for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) v += stot[threadIdx.x][ww];
+        atomicAdd(acc + threadIdx.x, v);
+    }
+    for (int b = threadIdx.x; b < 6 * nbins; b += blockDim.x)
+        if (sbin[b] != 0.0) atomicAdd(acc + 8 + b, sbin[b]);
+    block_max_atomic(m2max, reinterpret_cast<unsigned long long *>(acc + 7));
+}
+
+// Diagnostics of the FP32 form with the cached base state.  The totals keep
+// FP64 accuracy without FP64 arithmetic per cell (FP64 is slow on this part):
+// each thread sums its cells in float pairs (Sum2), products of two floats
+// enter as exact pairs (p = a*b rounded, e = fma(a, b, -p)), and every 32
+// cells the pairs are added into FP64.  Totals 0 and 4 are the sums of rho'
+// and E': the host adds the base sums.  FV near 1 is stored as FV - 1 (a
+// negative value s): FV = a + s with a = 1 for such a cell, 0 otherwise, so
+// that both FV sums keep the folded value's precision.  The Mach number is
+// taken in FP32; shell averages (nbins > 0) stay FP64 per cell.
+__global__ void diag32_kernel(SweepArgs<double> A64, const float *st, long long ncell, int nx, int ny,
+                              int nbins, double rmax_, double *acc, const float *bhi, const float *blo,
+                              const float *bp0) {
+    extern __shared__ double sbin[];
     for (int b = threadIdx.x; b < 6 * nbins; b += blockDim.x) sbin[b] = 0.0;
     __syncthreads();
-    // FP64 is slow on this part: per cell one square root (r, central
-    // gravity only) and two divisions; the table lookup multiplies by 1/ds
-    // and the Mach number is maximised as its square.  Results agree with
-    // the exact-lookup formulas to rounding.  With the cached base state
-    // (FP32 form) a cell needs neither its position nor a lookup unless
-    // shell averages are asked for.
+    const double gm1 = A64.gamma - 1.0;
+    const float gm1f = (float)gm1, gamf = (float)A64.gamma;
+    double tot[7] = {0, 0, 0, 0, 0, 0, 0};
+    Sum2 s[7];
+    for (int m = 0; m < 7; ++m) s[m] = Sum2{0.0f, 0.0f};
+    float small5 = 0.0f, ones6 = 0.0f;   // tiny product terms of rho*FV; folded-cell count
+    float m2max = 0.0f;
+    auto flush = [&]() {
+        for (int m = 0; m < 7; ++m) {
+            tot[m] += (double)s[m].s + (double)s[m].c;
+            s[m] = Sum2{0.0f, 0.0f};
+        }
+        tot[5] += (double)small5;
+        tot[6] += (double)ones6;
+        small5 = ones6 = 0.0f;
+    };
+    int k = 0;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < ncell;
+         t += (long long)gridDim.x * blockDim.x) {
+        const float rd = st[t], mx = st[ncell + t], my = st[2 * ncell + t], mz = st[3 * ncell + t];
+        const float ed = st[4 * ncell + t], fs = st[5 * ncell + t];
+        const float h = bhi[t], l = blo[t], p0 = bp0[t];
+        sum2_add(s[0], rd);
+        sum2_add(s[1], mx);
+        sum2_add(s[2], my);
+        sum2_add(s[3], mz);
+        sum2_add(s[4], ed);
+        const float a = signbit(fs) ? 1.0f : 0.0f;
+        sum2_add(s[6], fs);
+        ones6 += a;
+        // rho FV = a (h + l + rho') + (h + l + rho') s
+        const float p1 = h * fs, e1 = fmaf(h, fs, -p1);
+        const float p2 = rd * fs, e2 = fmaf(rd, fs, -p2);
+        sum2_add(s[5], a * h);
+        sum2_add(s[5], a * rd);
+        sum2_add(s[5], p1);
+        sum2_add(s[5], p2);
+        small5 += (e1 + e2) + l * (a + fs);
+        const float rf = h + rd;
+        const float m2 = fmaf(mx, mx, fmaf(my, my, mz * mz));
+        const float pf = p0 + gm1f * (ed - 0.5f * __fdividef(m2, rf));
+        m2max = fmaxf(m2max, __fdividef(m2, gamf * pf * rf));
+        if (nbins > 0) {
+            const int i = (int)(t % nx), j = (int)((t / nx) % ny), kz = (int)(t / ((long long)nx * ny));
+            const double x = coord(A64, 0, i), y = coord(A64, 1, j), z = coord(A64, 2, kz);
+            const double rho = ((double)h + (double)l) + (double)rd;
+            const double md[3] = {(double)mx, (double)my, (double)mz};
+            const double p = (double)p0 +
+                             gm1 * ((double)ed - 0.5 * (md[0] * md[0] + md[1] * md[1] + md[2] * md[2]) / rho);
+            bin_cell(sbin, nbins, rmax_, x, y, z, -1.0, rho, p, (double)a + (double)fs, md[0], md[1], md[2]);
+        }
+        if (++k == 32) {
+            flush();
+            k = 0;
+        }
+    }
+    flush();
+    diag_flush_block(tot, (double)m2max, sbin, nbins, acc);
+}
+
+// Diagnostics with the base state looked up per cell: the FP64 form, and
+// the FP32 form when there was no room for the cached base state.  FP64 is
+// slow on this part: per cell one square root (r, central gravity only) and
+// two divisions; the table lookup multiplies by 1/ds and the Mach number is
+// maximised as its square.  Results agree with the exact-lookup formulas to
+// rounding.
+template <typename R, bool PLAIN>
+__global__ void diag_kernel(SweepArgs<double> A64, const R *st, long long ncell, int nx, int ny,
+                            int nbins, double rmax_, double *acc) {
+    extern __shared__ double sbin[];
+    for (int b = threadIdx.x; b < 6 * nbins; b += blockDim.x) sbin[b] = 0.0;
+    __syncthreads();
     const double gam = A64.gamma, gm1 = A64.gamma - 1.0, igm1 = 1.0 / gm1;
     const double inv_ds = 1.0 / A64.ds;
     const double *t_r = A64.t_rho0, *t_p = A64.t_p0;
@@ -411,20 +566,10 @@ __global__ void diag_kernel(SweepArgs<double> A64, const R *st, long long ncell,
     double m2max = 0.0;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < ncell;
          t += (long long)gridDim.x * blockDim.x) {
-        double x = 0.0, y = 0.0, z = 0.0;
-        if (!base || nbins > 0) {
-            const int i = (int)(t % nx), j = (int)((t / nx) % ny), k = (int)(t / ((long long)nx * ny));
-            x = coord(A64, 0, i);
-            y = coord(A64, 1, j);
-            z = coord(A64, 2, k);
-        }
-        double rho0, p0, r = -1.0, E0 = 0.0;
-        if (base) {
-            // stored per cell (FP32 form): two loads instead of the lookup
-            rho0 = base[t];
-            E0 = base[ncell + t];
-            p0 = E0 * gm1;
-        } else if (A64.grav == 0) {
+        const int i = (int)(t % nx), j = (int)((t / nx) % ny), k = (int)(t / ((long long)nx * ny));
+        const double x = coord(A64, 0, i), y = coord(A64, 1, j), z = coord(A64, 2, k);
+        double rho0, p0, r = -1.0;
+        if (A64.grav == 0) {
             rho0 = A64.rho0_c;
             p0 = A64.p0_c;
         } else {
@@ -448,7 +593,7 @@ __global__ void diag_kernel(SweepArgs<double> A64, const R *st, long long ncell,
         } else {
             rho = rho0 + (double)st[t];
             Ed = (double)st[4 * ncell + t];
-            E = (base ? E0 : p0 * igm1) + Ed;
+            E = p0 * igm1 + Ed;
         }
         const double mx = st[ncell + t], my = st[2 * ncell + t], mz = st[3 * ncell + t];
         double fv = st[5 * ncell + t];
@@ -461,50 +606,18 @@ __global__ void diag_kernel(SweepArgs<double> A64, const R *st, long long ncell,
         tot[5] += rho * fv;
         tot[6] += fv;
         const double m2 = mx * mx + my * my + mz * mz;
-        double rinv = 0.0, p = 0.0;
-        if (PLAIN || nbins > 0) {
-            rinv = 1.0 / rho;
-            p = p0 + gm1 * (Ed - 0.5 * m2 * rinv);
-        }
+        const double p = p0 + gm1 * (Ed - 0.5 * m2 / rho);
         if (PLAIN) {
             m2max = fmax(m2max, m2 / (gam * p * rho));   // |u|^2 / c^2
         } else {
-            // FP32 state: its Mach number to FP32 accuracy, without FP64 divisions
+            // FP32 state: its Mach number to FP32 accuracy
             const float rf = (float)rho, m2f = (float)m2;
             const float pf = (float)p0 + (float)gm1 * ((float)Ed - 0.5f * m2f / rf);
             m2max = fmax(m2max, (double)(m2f / ((float)gam * pf * rf)));
         }
-        if (nbins > 0) {
-            if (r < 0.0) r = sqrt(x * x + y * y + z * z);
-            const int bin = (int)floor(r / rmax_ * nbins);
-            if (bin >= 0 && bin < nbins) {
-                const double spd = sqrt(m2) * rinv;
-                const double ur = r > 0.0 ? (mx * x + my * y + mz * z) * rinv / r : 0.0;
-                double *a = sbin + 6 * bin;
-                atomicAdd(a + 0, 1.0);
-                atomicAdd(a + 1, rho);
-                atomicAdd(a + 2, p);
-                atomicAdd(a + 3, fv);
-                atomicAdd(a + 4, spd);
-                atomicAdd(a + 5, ur * ur);
-            }
-        }
+        if (nbins > 0) bin_cell(sbin, nbins, rmax_, x, y, z, r, rho, p, fv, mx, my, mz);
     }
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    for (int m = 0; m < 7; ++m) {
-        double v = tot[m];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (l == 0) stot[m][w] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < 7) {
-        double v = 0.0;
-        for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) v += stot[threadIdx.x][ww];
-        atomicAdd(acc + threadIdx.x, v);
-    }
-    for (int b = threadIdx.x; b < 6 * nbins; b += blockDim.x)
-        if (sbin[b] != 0.0) atomicAdd(acc + 8 + b, sbin[b]);
-    block_max_atomic(m2max, reinterpret_cast<unsigned long long *>(acc + 7));
+    diag_flush_block(tot, m2max, sbin, nbins, acc);
 }
 
 int grid_for(long long n, int block) {
@@ -596,10 +709,35 @@ int check_flags(ppm_ctx *c) {
     return PPM_OK;
 }
 
-// Host regions go through two device staging buffers in turn: the copies of
-// one chunk (on the context's copy stream) overlap the conversion kernel of
-// the previous chunk (on the context's stream), ordered by events.  Device
-// regions are converted in place by one kernel.  Both return when done.
+// Device address of a host array of `count` doubles that lies in page-locked
+// memory this device can address (cudaHostAlloc / cudaHostRegister), or NULL.
+// The first and the last element must both be in such memory, at device
+// addresses `count - 1` doubles apart.
+double *mapped_host(const ppm_ctx *c, double *p, long long count) {
+    cudaPointerAttributes a, b;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer || a.device != c->device) return nullptr;
+    if (cudaPointerGetAttributes(&b, p + (count - 1)) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (b.type != cudaMemoryTypeHost || !b.devicePointer) return nullptr;
+    const long long span = (const char *)b.devicePointer - (const char *)a.devicePointer;
+    if (span != (count - 1) * (long long)sizeof(double)) return nullptr;
+    return static_cast<double *>(a.devicePointer);
+}
+
+// Host regions to upload that lie in page-locked memory are read in place by
+// one conversion kernel over the host link (at the link's rate, with no
+// staging pass).  Downloads, and uploads from other host memory, go through
+// two device staging buffers in turn: the copies of one chunk (on the
+// context's copy stream) overlap the conversion kernel of the previous chunk
+// (on the context's stream), ordered by events.  (A kernel writing tens of GB
+// of host memory directly ran at a fifth of the copy engines' rate.)  Device
+// regions are converted in place by one kernel.  All return when done.
 int region_io(ppm_ctx *c, const int lo[3], const int hi[3], double *const *arrs, int mem, bool to_dev) {
     if (!c || !lo || !hi || !arrs) return fail(c, PPM_EINVAL, "null argument");
     int b[3];
@@ -631,10 +769,19 @@ int region_io(ppm_ctx *c, const int lo[3], const int hi[3], double *const *arrs,
         CK(c, cudaGetLastError());
         return PPM_OK;
     };
-    if (mem == PPM_MEM_DEVICE) {
-        RegionPtrs ptrs;
-        for (int q = 0; q < nv; ++q) ptrs.p[q] = arrs[q];
-        const int r = convert(ptrs, lo[2], b[2], plane * b[2]);
+    RegionPtrs mapped;
+    bool direct = (mem == PPM_MEM_DEVICE);
+    if (direct) {
+        for (int q = 0; q < nv; ++q) mapped.p[q] = arrs[q];
+    } else if (to_dev) {
+        direct = true;
+        for (int q = 0; q < nv && direct; ++q) {
+            mapped.p[q] = mapped_host(c, arrs[q], plane * b[2]);
+            direct = mapped.p[q] != nullptr;
+        }
+    }
+    if (direct) {
+        const int r = convert(mapped, lo[2], b[2], plane * b[2]);
         if (r != PPM_OK) return r;
         CK(c, cudaStreamSynchronize(c->stream));
         if (to_dev) c->have_speed = false;
@@ -713,7 +860,7 @@ void release(ppm_ctx *c) {
     }
     if (c->stage) cudaFree(c->stage);
     if (c->diag_acc) cudaFree(c->diag_acc);
-    if (c->base64) cudaFree(c->base64);
+    if (c->base32) cudaFree(c->base32);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
 
@@ -872,7 +1019,7 @@ int ppm_create(ppm_ctx **out, int nx, int ny, int nz, double gamma, const int bc
         cudaMalloc(&c->t4, h4.size() * sizeof(float4)) != cudaSuccess ||
         cudaMalloc(&c->t32, h32.size() * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&c->ds_dev, sizeof(DevScal)) != cudaSuccess ||
-        cudaMalloc(&c->diag_acc, (8 + 6 * MAX_BINS) * sizeof(double)) != cudaSuccess) {
+        cudaMalloc(&c->diag_acc, (8 + 6 * MAX_BINS + 2) * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         fail(c, PPM_ENOMEM, "cannot allocate tables / accumulators");
         return bail(PPM_ENOMEM);
@@ -1035,23 +1182,38 @@ int ppm_diagnostics(ppm_ctx *c, double totals[7], int nbins, double rmax, double
     const int g = grid_for(c->ncell, 256);
     const size_t shm = 6 * (size_t)nbins * sizeof(double);
     const SweepArgs<double> A = args64(c);
+    bool cached = false;
     if (c->prec == PPM_FP32_DEVIATION) {
-        if (shm > 48 * 1024) CK(c, cudaFuncSetAttribute(diag_kernel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-        if (!c->base64 && !c->base64_tried) {
-            c->base64_tried = true;
-            if (cudaMalloc(&c->base64, 2 * (size_t)c->ncell * sizeof(double)) != cudaSuccess) {
+        if (!c->base32 && !c->base32_tried) {
+            c->base32_tried = true;
+            if (cudaMalloc(&c->base32, 3 * (size_t)c->ncell * sizeof(float)) != cudaSuccess) {
                 cudaGetLastError();   // no room: the kernel looks the base state up instead
-                c->base64 = nullptr;
+                c->base32 = nullptr;
             } else {
-                base_fill_kernel<<<g, 256, 0, c->stream>>>(A, c->base64, c->ncell, c->n[0], c->n[1]);
+                double *sums = c->diag_acc + 8 + 6 * MAX_BINS;
+                CK(c, cudaMemsetAsync(sums, 0, 2 * sizeof(double), c->stream));
+                base_fill_kernel<<<g, 256, 0, c->stream>>>(A, c->base32, c->base32 + c->ncell,
+                                                           c->base32 + 2 * c->ncell, sums, c->ncell, c->n[0],
+                                                           c->n[1]);
                 c->launches++;
                 CK(c, cudaGetLastError());
+                CK(c, cudaMemcpyAsync(c->base_sum, sums, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+                CK(c, cudaStreamSynchronize(c->stream));
             }
         }
-        diag_kernel<float, false><<<g, 256, shm, c->stream>>>(A, (const float *)c->state, c->ncell, c->n[0], c->n[1], nbins, rmax, c->diag_acc, c->base64);
+        cached = c->base32 != nullptr;
+        if (cached) {
+            if (shm > 48 * 1024) CK(c, cudaFuncSetAttribute(diag32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+            diag32_kernel<<<g, 256, shm, c->stream>>>(A, (const float *)c->state, c->ncell, c->n[0], c->n[1], nbins,
+                                                      rmax, c->diag_acc, c->base32, c->base32 + c->ncell,
+                                                      c->base32 + 2 * c->ncell);
+        } else {
+            if (shm > 48 * 1024) CK(c, cudaFuncSetAttribute(diag_kernel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+            diag_kernel<float, false><<<g, 256, shm, c->stream>>>(A, (const float *)c->state, c->ncell, c->n[0], c->n[1], nbins, rmax, c->diag_acc);
+        }
     } else {
         if (shm > 48 * 1024) CK(c, cudaFuncSetAttribute(diag_kernel<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-        diag_kernel<double, true><<<g, 256, shm, c->stream>>>(A, (const double *)c->state, c->ncell, c->n[0], c->n[1], nbins, rmax, c->diag_acc, nullptr);
+        diag_kernel<double, true><<<g, 256, shm, c->stream>>>(A, (const double *)c->state, c->ncell, c->n[0], c->n[1], nbins, rmax, c->diag_acc);
     }
     c->launches++;
     CK(c, cudaGetLastError());
@@ -1059,6 +1221,10 @@ int ppm_diagnostics(ppm_ctx *c, double totals[7], int nbins, double rmax, double
     CK(c, cudaMemcpyAsync(h.data(), c->diag_acc, nacc * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
     const double dV = c->dx * c->dx * c->dx;
+    if (cached) {   // the kernel summed rho' and E'
+        h[0] += c->base_sum[0];
+        h[4] += c->base_sum[1];
+    }
     for (int m = 0; m < 7; ++m) totals[m] = h[m] * dV;
     for (int b = 0; b < nbins; ++b) {
         const double *a = &h[8 + 6 * b];

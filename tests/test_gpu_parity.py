@@ -207,6 +207,34 @@ def test_cfl_and_diagnostics_match_oracle(precision):
     assert abs(mg - mo) <= (1e-12 if precision == ppm.FP64_PLAIN else 1e-5) * mo
 
 
+@pytest.mark.parametrize("make", [lambda: workloads.sphere(shape=(40, 36, 44)),
+                                  lambda: workloads.strat_box(shape=(24, 20, 32))],
+                         ids=["sphere", "strat"])
+def test_fp32_diagnostics_totals_after_steps(make):
+    """FP32 form after a few steps (folded FV near 1, moving gas): totals to
+    1e-12 of the FP64 sums of the downloaded state, with and without shell
+    bins, on the first call (which builds the cached base state) and on later
+    calls."""
+    p = make()
+    q = workloads.build(p)
+    ctx = ppm.Context.from_problem(p, precision=ppm.FP32_DEVIATION)
+    ctx.set_state(q)
+    o = oracle.Oracle(p)
+    for it in range(3):
+        dt = ctx.cfl_dt(p.cfl)
+        ctx.step(dt)
+        qs = ctx.get_state()
+        for nb in ((0, 8) if it != 1 else (8, 0)):
+            tg, pg, mg = ctx.diagnostics(nb, 1.0)
+            to, po, mo = o.diagnostics(qs, nb, 1.0)
+            np.testing.assert_allclose(tg, to, rtol=1e-12, atol=1e-14 * np.abs(to).max())
+            if nb:
+                np.testing.assert_allclose(pg, po, rtol=1e-5, atol=1e-12)
+            assert abs(mg - mo) <= 1e-5 * mo
+    assert (qs[5] > 0.5).any() and (qs[5] < 0.5).any()
+    ctx.close()
+
+
 def test_nonphysical_state_is_reported():
     p = workloads.periodic_box(16)
     q = workloads.build(p)
@@ -238,6 +266,45 @@ def test_region_roundtrip_host_and_device():
     torch.cuda.synchronize()
     for v in range(9):
         assert np.array_equal(out[v].cpu().numpy(), sub[v])
+
+
+@pytest.mark.parametrize("precision", [ppm.FP64_PLAIN, ppm.FP32_DEVIATION])
+def test_pinned_host_transfers_match_pageable(precision):
+    """Uploads from page-locked host arrays are converted in place over the
+    host link, other transfers go through the staging buffers: identical
+    results, for the whole state, a sub-box, and a pinned array of which only
+    a part holds the region (a pinned view in the middle of a larger pinned
+    buffer, whose other parts stay untouched)."""
+    p = workloads.sphere(shape=(20, 18, 22))
+    q = workloads.build(p)
+    pin = [torch.from_numpy(a.copy()).pin_memory() for a in q]
+    a = ppm.Context.from_problem(p, precision=precision)
+    b = ppm.Context.from_problem(p, precision=precision)
+    a.set_state(q)
+    b.set_state([t.numpy() for t in pin])
+    qa = a.get_state()
+    qb = [torch.empty(t.shape, dtype=torch.float64).pin_memory() for t in pin]
+    b.get_state_into([t.numpy() for t in qb])
+    for v in range(9):
+        assert np.array_equal(qb[v].numpy(), qa[v]), v
+    lo, hi = (3, 2, 5), (17, 11, 20)
+    n = (hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2])
+    big = [torch.zeros(3 * n, dtype=torch.float64).pin_memory() for _ in range(9)]
+    mid = [t[n:2 * n].view(hi[2] - lo[2], hi[1] - lo[1], hi[0] - lo[0]) for t in big]
+    b.get_region(lo, hi, [m.numpy() for m in mid])
+    sub = a.get_region(lo, hi)
+    for v in range(9):
+        assert np.array_equal(mid[v].numpy(), sub[v]), v
+        assert not big[v][:n].any() and not big[v][2 * n:].any(), v
+    for m in mid:
+        m.mul_(1.0 + 1e-3)
+    a.set_region(lo, hi, [m.numpy().copy() for m in mid])
+    b.set_region(lo, hi, [m.numpy() for m in mid])
+    qa, qb2 = a.get_state(), b.get_state()
+    for v in range(9):
+        assert np.array_equal(qa[v], qb2[v]), v
+    a.close()
+    b.close()
 
 
 # --------------------------------------------------------------------------
