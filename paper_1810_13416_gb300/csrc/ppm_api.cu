@@ -730,14 +730,13 @@ double *mapped_host(const ppm_ctx *c, double *p, long long count) {
     return static_cast<double *>(a.devicePointer);
 }
 
-// Host regions to upload that lie in page-locked memory are read in place by
-// one conversion kernel over the host link (at the link's rate, with no
-// staging pass).  Downloads, and uploads from other host memory, go through
-// two device staging buffers in turn: the copies of one chunk (on the
-// context's copy stream) overlap the conversion kernel of the previous chunk
-// (on the context's stream), ordered by events.  (A kernel writing tens of GB
-// of host memory directly ran at a fifth of the copy engines' rate.)  Device
-// regions are converted in place by one kernel.  All return when done.
+// Host regions in page-locked memory are read or written in place by the
+// conversion kernel over the host link (at the link's rate, with no staging
+// pass and no copy engine).  Other host regions go through two device
+// staging buffers in turn: the copies of one chunk (on the context's copy
+// stream) overlap the conversion kernel of the previous chunk (on the
+// context's stream), ordered by events.  Device regions are converted in
+// place by one kernel.  All return when done.
 int region_io(ppm_ctx *c, const int lo[3], const int hi[3], double *const *arrs, int mem, bool to_dev) {
     if (!c || !lo || !hi || !arrs) return fail(c, PPM_EINVAL, "null argument");
     int b[3];
@@ -771,18 +770,29 @@ int region_io(ppm_ctx *c, const int lo[3], const int hi[3], double *const *arrs,
     };
     RegionPtrs mapped;
     bool direct = (mem == PPM_MEM_DEVICE);
+    bool host_mapped = false;
     if (direct) {
         for (int q = 0; q < nv; ++q) mapped.p[q] = arrs[q];
-    } else if (to_dev) {
-        direct = true;
-        for (int q = 0; q < nv && direct; ++q) {
+    } else {
+        host_mapped = true;
+        for (int q = 0; q < nv && host_mapped; ++q) {
             mapped.p[q] = mapped_host(c, arrs[q], plane * b[2]);
-            direct = mapped.p[q] != nullptr;
+            host_mapped = mapped.p[q] != nullptr;
         }
+        direct = host_mapped;
     }
     if (direct) {
-        const int r = convert(mapped, lo[2], b[2], plane * b[2]);
-        if (r != PPM_OK) return r;
+        // host memory in slabs of about 2^26 cells per launch (one launch
+        // over a 77 GB download ran at a fifth of the link's rate, slabs at
+        // the full rate); device memory in one launch
+        const long long kstep = host_mapped ? std::max(1LL, (1LL << 26) / plane) : (long long)b[2];
+        for (long long k0 = 0; k0 < b[2]; k0 += kstep) {
+            const long long nk = std::min(kstep, (long long)b[2] - k0);
+            RegionPtrs part;
+            for (int q = 0; q < nv; ++q) part.p[q] = mapped.p[q] + k0 * plane;
+            const int r = convert(part, lo[2] + (int)k0, (int)nk, plane * nk);
+            if (r != PPM_OK) return r;
+        }
         CK(c, cudaStreamSynchronize(c->stream));
         if (to_dev) c->have_speed = false;
         return PPM_OK;

@@ -270,11 +270,11 @@ def test_region_roundtrip_host_and_device():
 
 @pytest.mark.parametrize("precision", [ppm.FP64_PLAIN, ppm.FP32_DEVIATION])
 def test_pinned_host_transfers_match_pageable(precision):
-    """Uploads from page-locked host arrays are converted in place over the
-    host link, other transfers go through the staging buffers: identical
-    results, for the whole state, a sub-box, and a pinned array of which only
-    a part holds the region (a pinned view in the middle of a larger pinned
-    buffer, whose other parts stay untouched)."""
+    """Page-locked host arrays are read and written in place over the host
+    link, pageable ones go through the staging buffers: identical results,
+    for the whole state, a sub-box, and a pinned array of which only a part
+    holds the region (a pinned view in the middle of a larger pinned buffer,
+    whose other parts stay untouched)."""
     p = workloads.sphere(shape=(20, 18, 22))
     q = workloads.build(p)
     pin = [torch.from_numpy(a.copy()).pin_memory() for a in q]
@@ -303,6 +303,30 @@ def test_pinned_host_transfers_match_pageable(precision):
     qa, qb2 = a.get_state(), b.get_state()
     for v in range(9):
         assert np.array_equal(qa[v], qb2[v]), v
+    a.close()
+    b.close()
+
+
+def test_pinned_host_transfers_in_several_slabs():
+    """A state of 512 x 512 x 300 cells (2^26 cells and more): in-place host
+    transfers run in slabs of 256 planes; pinned and pageable uploads and
+    downloads agree bit for bit."""
+    p = workloads.periodic_box(shape=(512, 512, 300))
+    rng = np.random.default_rng(7)
+    shape = (300, 512, 512)
+    q = [1.0 + 0.1 * rng.random(shape)] + [0.05 * rng.standard_normal(shape) for _ in range(3)]
+    q += [2.0 + 0.1 * rng.random(shape), rng.random(shape)] + [np.zeros(shape) for _ in range(3)]
+    pin = [torch.from_numpy(a).pin_memory() for a in q]
+    a = ppm.Context.from_problem(p, precision=ppm.FP32_DEVIATION)
+    b = ppm.Context.from_problem(p, precision=ppm.FP32_DEVIATION)
+    a.set_state(q)                              # staging
+    b.set_state([t.numpy() for t in pin])       # in place, two slabs
+    qa = a.get_state()                          # staging
+    for t in pin:                               # reuse the pinned buffers for b's download
+        t.zero_()
+    b.get_state_into([t.numpy() for t in pin])  # in place, two slabs
+    for v in range(9):
+        assert np.array_equal(pin[v].numpy(), qa[v]), v
     a.close()
     b.close()
 
