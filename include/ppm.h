@@ -119,12 +119,16 @@ int ppm_create(ppm_ctx **out, int nx, int ny, int nz, double gamma, const int bc
 /* Upload the whole state from host FP64 arrays (full variables, layout above;
  * 6 + nmom arrays).  FP32 form: rho - rho0 and E - p0/(gamma-1) are formed in
  * FP64 on the device before rounding; FV and the moments are clipped to their
- * bounds.  Host arrays go through two device staging buffers in turn (copies
- * overlapping the conversion); the call returns when done.  Invalidates the
- * device time step (call ppm_cfl_dt). */
+ * bounds.  Host arrays in page-locked memory that the device can address
+ * (cudaHostAlloc / cudaHostRegister) are read in place by the conversion
+ * kernel, in slabs of about 2^26 cells; other host arrays go through two
+ * device staging buffers in turn (copies overlapping the conversion).  The
+ * call returns when done.  Invalidates the device time step (call
+ * ppm_cfl_dt). */
 int ppm_set_state(ppm_ctx *ctx, const double *const q[]);
 
-/* Download the whole state to host FP64 arrays (full variables). */
+/* Download the whole state to host FP64 arrays (full variables); page-locked
+ * host arrays are written in place, others through the staging buffers. */
 int ppm_get_state(ppm_ctx *ctx, double *const q[]);
 
 /* Same for the sub-box lo <= (i,j,k) < hi; arrays are (hi-lo) boxes with x
@@ -136,8 +140,11 @@ int ppm_get_region(ppm_ctx *ctx, const int lo[3], const int hi[3], double *const
 
 /* CFL time step: dt = cfl * dx / max over cells of
  * (max_d |u_d| + c), c = sqrt(gamma p / rho), reduced in FP64 on the device.
- * 0 < cfl <= 1 (else ECFL).  dt_out may be NULL: the value then stays on the
- * device for ppm_step(ctx, 0).  Returns ENONPHYS if a previous pass flagged a
+ * After ppm_step the maximum taken by the step's last pass (or rotation
+ * increment) on the final values is used; after an upload, a single pass or
+ * context creation one grid pass takes it afresh.  0 < cfl <= 1 (else ECFL).
+ * dt_out may be NULL: the value then stays on the device for
+ * ppm_step(ctx, 0).  Returns ENONPHYS if a previous pass flagged a
  * non-physical cell. */
 int ppm_cfl_dt(ppm_ctx *ctx, double cfl, double *dt_out);
 

@@ -1075,17 +1075,22 @@ int ppm_cfl_dt(ppm_ctx *c, double cfl, double *dt_out) {
     if (!c) return PPM_EINVAL;
     if (!(cfl > 0.0)) return fail(c, PPM_EINVAL, "cfl must be positive");
     if (cfl > 1.0) return fail(c, PPM_ECFL, "cfl %.3g exceeds 1", cfl);
-    CK(c, cudaMemsetAsync(&c->ds_dev->smax, 0, sizeof(unsigned long long), c->stream));
     set_scalar_kernel<<<1, 32, 0, c->stream>>>(&c->ds_dev->cfl, cfl);
     c->launches++;
-    const int g = grid_for(c->ncell, 256);
-    if (c->prec == PPM_FP32_DEVIATION)
-        cfl_kernel<float, false><<<g, 256, 0, c->stream>>>(make_args<float>(c, 0), (const float *)c->state, c->ncell, c->n[0], c->n[1], &c->ds_dev->smax);
-    else
-        cfl_kernel<double, true><<<g, 256, 0, c->stream>>>(make_args<double>(c, 0), (const double *)c->state, c->ncell, c->n[0], c->n[1], &c->ds_dev->smax);
-    c->launches++;
-    CK(c, cudaGetLastError());
-    c->have_speed = true;
+    // After a double step the last pass (or the rotation increment) has
+    // already taken the maximum signal speed of the new state, and nothing
+    // has changed the state since: no pass over the grid is needed.
+    if (!c->have_speed) {
+        CK(c, cudaMemsetAsync(&c->ds_dev->smax, 0, sizeof(unsigned long long), c->stream));
+        const int g = grid_for(c->ncell, 256);
+        if (c->prec == PPM_FP32_DEVIATION)
+            cfl_kernel<float, false><<<g, 256, 0, c->stream>>>(make_args<float>(c, 0), (const float *)c->state, c->ncell, c->n[0], c->n[1], &c->ds_dev->smax);
+        else
+            cfl_kernel<double, true><<<g, 256, 0, c->stream>>>(make_args<double>(c, 0), (const double *)c->state, c->ncell, c->n[0], c->n[1], &c->ds_dev->smax);
+        c->launches++;
+        CK(c, cudaGetLastError());
+        c->have_speed = true;
+    }
     if (dt_out) {
         int r = check_flags(c);
         if (r != PPM_OK) return r;

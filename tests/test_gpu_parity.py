@@ -189,6 +189,34 @@ def test_device_dt_path_matches_explicit_dt():
 
 
 @pytest.mark.parametrize("precision", [ppm.FP64_PLAIN, ppm.FP32_DEVIATION])
+@pytest.mark.parametrize("confine", [False, True])
+def test_cfl_after_step_matches_a_fresh_maximum(precision, confine):
+    """After a double step the time step comes from the maximum the last
+    pass took (no pass over the grid); it equals the maximum taken afresh
+    from the stored state (after a re-upload) and the oracle's."""
+    p = workloads.sphere(shape=(30, 26, 34), confine=confine)
+    q = workloads.build(p)
+    ctx = ppm.Context.from_problem(p, precision=precision)
+    ctx.set_state(q)
+    o = oracle.Oracle(p)
+    for _ in range(2):
+        ctx.step(ctx.cfl_dt(p.cfl))
+    n0 = ctx.launch_count
+    dt_fused = ctx.cfl_dt(p.cfl)
+    assert ctx.launch_count - n0 == 1          # the cfl scalar only
+    qs = ctx.get_state()
+    ctx.set_state(qs)
+    n0 = ctx.launch_count
+    dt_fresh = ctx.cfl_dt(p.cfl)
+    assert ctx.launch_count - n0 == 2          # the cfl scalar and the grid pass
+    dt_orc = o.cfl_dt(qs, p.cfl)
+    tol = 1e-13 if precision == ppm.FP64_PLAIN else 1e-6
+    assert abs(dt_fused - dt_fresh) <= tol * dt_fresh
+    assert abs(dt_fused - dt_orc) <= tol * dt_orc
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision", [ppm.FP64_PLAIN, ppm.FP32_DEVIATION])
 def test_cfl_and_diagnostics_match_oracle(precision):
     p = workloads.sphere(shape=(32, 28, 36))
     q = workloads.build(p)
