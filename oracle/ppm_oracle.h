@@ -9,10 +9,11 @@
  *
  * Every function works on full (not base-subtracted) FP64 state arrays
  * q[9] = (rho, rho*u, rho*v, rho*w, E, FV, m_x, m_y, m_z), each nx*ny*nz with
- * x fastest (q[15] with the second and mixed moments when nmom == 9).  Internally each 1-D pass gathers one pencil at a time, subtracts
- * the hydrostatic base state (Sec. 1: the stored initial state is removed
- * from the scheme with care),
- * runs the pass step by step on whole-pencil arrays, and scatters back.
+ * x fastest (q[15] with the second and mixed moments when nmom == 9).
+ * Internally each 1-D pass gathers one pencil at a time, subtracts the
+ * hydrostatic base state (Sec. 1: the stored initial state is removed from
+ * the scheme with care), runs the pass step by step on whole-pencil arrays,
+ * and scatters back.
  *
  * Parity status of each step (what pins it, besides the CUDA path agreeing):
  *   interface values, parabolas, tracing, Riemann, fluxes, update: pinned by
@@ -21,6 +22,9 @@
  *     measured convergence order on smooth advection;
  *   PPB advection: pinned by bounds, conservation, exact transport of linear
  *     and quadratic profiles and of the first moment at constant velocity;
+ *   the pencil machinery (gather, ghost and face mapping, base state at
+ *     faces, stencil offsets): pinned bit for bit by a separately written
+ *     whole-grid, array-at-a-time statement of one four-value pass;
  *   smoothness-detector constants, flattening constants, PPB curvature and
  *     FCT limiter details: parity unpinned against the paper (it prints no
  *     formulas for them); pinned only through the invariants above.
