@@ -382,11 +382,18 @@ constexpr int SWEEP_NB = PPM_SWEEP_NB;   // threads per block
 constexpr int RING = 8;         // scalar prefetch ring slots per thread
 constexpr int PREF = 4;         // scalar prefetch distance (cells)
 
+// x pass (VEC): groups of 4 cells in flight per thread (the one being read
+// and two ahead; a fourth slot for 9 values), and cells staged per output
+// flush (8 = one 32-byte sector per value; 4 for 15 values, so that three
+// 64-thread blocks fit on an SM instead of two).
+__host__ __device__ constexpr int vec_slots(int NV) { return NV > 9 ? 3 : 4; }
+__host__ __device__ constexpr int vec_stage(int NV) { return NV > 9 ? 4 : 8; }
+
 // Dynamic shared memory of one block of the pass (NV stored values per cell:
 // 9, or 15 with the ten-value PPB).
 template <typename R, bool VEC, int NB = SWEEP_NB, int NV = 9>
 constexpr int sweep_smem_bytes() {
-    return VEC ? (4 * NV * NB * 16 + NV * NB * 32) : (RING * NV * NB * (int)sizeof(R));
+    return VEC ? (vec_slots(NV) * NV * NB * 16 + NV * NB * 4 * vec_stage(NV)) : (RING * NV * NB * (int)sizeof(R));
 }
 
 #ifndef PPM_SWEEP_UNROLL
@@ -579,7 +586,9 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
     // prefetch rings (shared memory, private to each thread)
     R *ring = reinterpret_cast<R *>(smem_raw);
     float *ringv = reinterpret_cast<float *>(smem_raw);
-    float *outv = reinterpret_cast<float *>(smem_raw) + 4 * NV * SWEEP_NB * 4;
+    constexpr int VSLOT = vec_slots(NV), VSTAGE = vec_stage(NV);
+    auto vslot = [](int g) { return VSLOT == 4 ? (g & 3) : (g % VSLOT); };
+    float *outv = reinterpret_cast<float *>(smem_raw) + VSLOT * NV * SWEEP_NB * 4;
     auto fetch = [&](int cf) {
         if (cf < n) {
             bool fl;
@@ -596,7 +605,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
         if (c0 < n) {
             const int m0 = (c0 < 0) ? ((bcl == 0) ? n - 4 : 0) : c0;
             const float *src = reinterpret_cast<const float *>(q) + m0;
-            float *dst = ringv + (((g & 3) * NV) * SWEEP_NB + tid) * 4;
+            float *dst = ringv + ((vslot(g) * NV) * SWEEP_NB + tid) * 4;
 #pragma unroll
             for (int v = 0; v < NV; ++v) cp_async<16>(dst + v * SWEEP_NB * 4, src + voff(v));
         }
@@ -674,7 +683,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
             if constexpr (VEC) {
                 const int sub = (c + G) & 3;
                 const int idx = (c < 0 && bcl == 1) ? 3 - sub : sub;
-                const float *src = ringv + ((((c + G) >> 2) & 3) * NV * SWEEP_NB + tid) * 4 + idx;
+                const float *src = ringv + ((vslot((c + G) >> 2) * NV) * SWEEP_NB + tid) * 4 + idx;
 #pragma unroll
                 for (int v = 0; v < NV; ++v) raw[v] = src[v * SWEEP_NB * 4];
             } else {
@@ -1251,20 +1260,21 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
                 outc[14] = cn2n;
             }
             if constexpr (VEC) {
-                // stage 8 cells ([var][cell][thread]: conflict-free), then one
-                // whole 32-byte sector per variable
-                float *st = outv + (size_t)(i & 7) * SWEEP_NB + tid;
+                // stage VSTAGE cells ([var][cell][thread]: conflict-free), then
+                // VSTAGE / 4 16-byte stores per variable
+                float *st = outv + (size_t)(i & (VSTAGE - 1)) * SWEEP_NB + tid;
 #pragma unroll
-                for (int vv = 0; vv < NV; ++vv) st[vv * SWEEP_NB * 8] = outc[vv];
-                if ((i & 7) == 7) {
-                    float *g = reinterpret_cast<float *>(q) + (i - 7);
+                for (int vv = 0; vv < NV; ++vv) st[vv * SWEEP_NB * VSTAGE] = outc[vv];
+                if ((i & (VSTAGE - 1)) == VSTAGE - 1) {
+                    float *g = reinterpret_cast<float *>(q) + (i - (VSTAGE - 1));
                     const float *sv = outv + tid;
 #pragma unroll
                     for (int vv = 0; vv < NV; ++vv) {
-                        const float *r = sv + vv * SWEEP_NB * 8;
+                        const float *r = sv + vv * SWEEP_NB * VSTAGE;
                         float4 *d = reinterpret_cast<float4 *>(g + voff(vv));
                         d[0] = make_float4(r[0], r[SWEEP_NB], r[2 * SWEEP_NB], r[3 * SWEEP_NB]);
-                        d[1] = make_float4(r[4 * SWEEP_NB], r[5 * SWEEP_NB], r[6 * SWEEP_NB], r[7 * SWEEP_NB]);
+                        if constexpr (VSTAGE == 8)
+                            d[1] = make_float4(r[4 * SWEEP_NB], r[5 * SWEEP_NB], r[6 * SWEEP_NB], r[7 * SWEEP_NB]);
                     }
                 }
             } else {

@@ -37,7 +37,7 @@ void launch_sweep_f32(const SweepArgs<float> &a, dim3 grid, dim3 block, cudaStre
         else
             sweep_kernel<float, false, false, false, false, true><<<grid, block, sweep_smem_bytes<float, false>(), st>>>(a);
     } else if (a.ten && a.vec_x) {
-        // 64-thread blocks: two fit with their 15-value 16-byte rings
+        // 64-thread blocks: three fit with their 15-value 16-byte rings
         const dim3 g((a.nlane + TEN_VEC_NB - 1) / TEN_VEC_NB, a.nblk);
         sweep_kernel<float, false, true, false, true, false, TEN_VEC_NB>
             <<<g, dim3(TEN_VEC_NB), sweep_smem_bytes<float, true, TEN_VEC_NB, 15>(), st>>>(a);
