@@ -45,3 +45,48 @@ def test_fp32_shell_averages_follow_fp64_over_200_steps():
         rel = np.abs(pr32[:, k] - pr64[:, k]) / np.abs(pr64[:, k])
         assert rel.max() <= 1e-3, (k, rel.max())
     assert np.abs(pr32[:, 2] - pr64[:, 2]).max() <= 1e-3
+
+
+def _device_upload(ctx, p, slab=64):
+    n = p.shape[2]
+    for z0 in range(0, n, slab):
+        z1 = min(n, z0 + slab)
+        qs = [t.contiguous() for t in workloads.initial_state(p, device="cuda", z_lo=z0, z_hi=z1)]
+        ctx.set_region((0, 0, z0), (p.shape[0], p.shape[1], z1), qs, device=True)
+
+
+def test_fp32_shell_averages_sphere256_100_steps():
+    """The sphere workload at 256^3 (the benchmark's recipe), 100 double
+    steps in both forms with one dt sequence: shell averages of rho and p to
+    1e-5 relative, FV to 1e-6 absolute, the rms velocity per shell to 1e-4
+    of its maximum; mass conserved to 1e-11 in both forms, rho*FV to 1e-12
+    in FP64 and 1e-9 in FP32 (its FV update rounds in FP32; measured 8e-11
+    at 512^3 after 100 double steps)."""
+    n = 256
+    p = workloads.sphere(n=n)
+    c64 = ppm.Context.from_problem(p, precision=ppm.FP64_PLAIN)
+    c32 = ppm.Context.from_problem(p, precision=ppm.FP32_DEVIATION)
+    _device_upload(c64, p)
+    _device_upload(c32, p)
+    nb = n // 2
+    t64, _, _ = c64.diagnostics(nb, 1.0)
+    t32, _, _ = c32.diagnostics(nb, 1.0)
+    for _ in range(100):
+        dt = c64.cfl_dt(p.cfl)
+        c64.step(dt)
+        c32.step(dt)
+    e64, pr64, m64 = c64.diagnostics(nb, 1.0)
+    e32, pr32, m32 = c32.diagnostics(nb, 1.0)
+    c64.close()
+    c32.close()
+    assert 0.0 < m64 < 0.5 and abs(m32 - m64) <= 1e-4 * m64
+    sel = pr64[:, 0] > 0
+    for k in (0, 1):                 # rho, p
+        rel = np.abs(pr32[sel, k] - pr64[sel, k]) / np.abs(pr64[sel, k])
+        assert rel.max() <= 1e-5, (k, rel.max())
+    assert np.abs(pr32[sel, 2] - pr64[sel, 2]).max() <= 1e-6
+    urms32, urms64 = np.sqrt(pr32[sel, 4]), np.sqrt(pr64[sel, 4])
+    assert np.abs(urms32 - urms64).max() <= 1e-4 * urms64.max()
+    for t0, t1, tol_fv in ((t64, e64, 1e-12), (t32, e32, 1e-9)):
+        assert abs(t1[0] - t0[0]) <= 1e-11 * t0[0]
+        assert abs(t1[5] - t0[5]) <= tol_fv * t0[5]
