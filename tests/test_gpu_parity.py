@@ -103,6 +103,20 @@ def test_gravity_problems_fp32(maker):
     _assert_f32(qg, qo)
 
 
+@pytest.mark.parametrize("precision", [ppm.FP64_PLAIN, ppm.FP32_DEVIATION])
+def test_stratified_box_128_full_size_20_steps(precision):
+    """The stratified convection box at its full 128^3 size (plane gravity,
+    reflecting z walls, heating, the light-fluid layer): 20 double steps,
+    whole grid against the oracle (FP64 1e-10 relative L-inf; FP32 1e-5
+    relative L1 on rho and E, 1e-7 mean on FV)."""
+    p = workloads.strat_box(shape=(128, 128, 128))
+    qg, qo = _run_pair(p, precision, 20)
+    if precision == ppm.FP64_PLAIN:
+        _assert_f64(qg, qo)
+    else:
+        _assert_f32(qg, qo)
+
+
 @pytest.mark.parametrize("kind", ["sod", "lax"])
 @pytest.mark.parametrize("axis", [0, 1, 2])
 def test_shock_tubes_fp64(kind, axis):
