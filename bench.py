@@ -388,6 +388,30 @@ def run_ours(args):
         del ct
         torch.cuda.empty_cache()
 
+    # ---------------- 3-D shock dissipation on (FP32, same grid) -----------
+    shock = None
+    if not args.no_shock:
+        import copy as _copy
+        ps = _copy.copy(p)
+        ps.shock_k = 0.1
+        cs = ppm.Context.from_problem(ps, precision=ppm.FP32_DEVIATION, stream=stream, device=local)
+        _upload(cs, ps, torch)
+        cs.cfl_dt(ps.cfl, fetch=False)
+        for _ in range(args.warmup):
+            cs.step(0.0)
+        barrier()
+        l0s = cs.launch_count
+        tsk = max_over_ranks(_time_steps(cs, torch, stream, args.shock_steps))
+        shock = {"workload": f"sphere-in-cube {n}^3, FP32, 3-D shock dissipation on (K = 0.1; inactive in "
+                             f"this Mach-0.03 flow: the cost of the divergence pass and the dissipative "
+                             f"flux terms)", "cells": ncell,
+                 "value": 2.0 * ncell * args.shock_steps * ws / tsk, "unit": UNIT,
+                 "ms_per_step": 1e3 * tsk / args.shock_steps, "steps": args.shock_steps,
+                 "launches_per_step": (cs.launch_count - l0s) / args.shock_steps}
+        cs.close()
+        del cs
+        torch.cuda.empty_cache()
+
     # ---------------- batched ensemble of uneven boxes (FP32) -------------
     ens_out = None
     if not args.no_ensemble:
@@ -443,7 +467,7 @@ def run_ours(args):
                            "step": "Strang double step X Y Z [src] Z Y X [src] = 2 3-D steps",
                            "l2": f"inputs larger than L2 ({9 * 4 * ncell / 1e9:.2f} GB vs 129 MB); no flush"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clocks, "fp64": fp64, "confined": conf, "ppb10": ten, "ensemble": ens_out,
+                "clocks": clocks, "fp64": fp64, "confined": conf, "ppb10": ten, "shock": shock, "ensemble": ens_out,
                 "state_ok": ok_state}
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -473,6 +497,8 @@ def main():
     ap.add_argument("--no-ppb10", action="store_true")
     ap.add_argument("--ppb10-steps", type=int, default=3)
     ap.add_argument("--confined-steps", type=int, default=3)
+    ap.add_argument("--no-shock", action="store_true")
+    ap.add_argument("--shock-steps", type=int, default=3)
     ap.add_argument("--ens-boxes", type=int, default=24)
     args = ap.parse_args()
     if args.warmup < 3:
