@@ -277,6 +277,23 @@ def test_fp32_diagnostics_totals_after_steps(make):
     ctx.close()
 
 
+@pytest.mark.parametrize("precision", [ppm.FP64_PLAIN, ppm.FP32_DEVIATION])
+def test_state_larger_than_the_device_is_refused(precision):
+    """A grid whose state cannot be allocated (4096^3: 2.4 TB in FP32) is
+    refused with PPM_ENOMEM and leaves nothing behind: a context of a usable
+    size then works as before."""
+    p = workloads.periodic_box(shape=(4096, 4096, 4096))
+    with pytest.raises(ppm.PpmError) as e:
+        ppm.Context.from_problem(p, precision=precision)
+    assert e.value.code == -2
+    q_p = workloads.periodic_box(shape=(16, 16, 16))
+    qg, qo = _run_pair(q_p, precision, 2)
+    if precision == ppm.FP64_PLAIN:
+        _assert_f64(qg, qo)
+    else:
+        _assert_f32(qg, qo)
+
+
 def test_nonphysical_state_is_reported():
     p = workloads.periodic_box(16)
     q = workloads.build(p)
