@@ -294,6 +294,37 @@ def test_state_larger_than_the_device_is_refused(precision):
         _assert_f32(qg, qo)
 
 
+@pytest.mark.parametrize("precision", [ppm.FP64_PLAIN, ppm.FP32_DEVIATION])
+@pytest.mark.parametrize("var", [0, 1, 4])
+def test_nan_in_host_input_is_reported(precision, var):
+    """A NaN planted in the host state (density, a momentum, the energy)
+    makes the next pass report PPM_ENONPHYS; a clean upload afterwards runs
+    normally and matches the oracle."""
+    p = workloads.periodic_box(16)
+    q = workloads.build(p)
+    bad = [a.copy() for a in q]
+    bad[var][5, 6, 7] = np.nan
+    ctx = ppm.Context.from_problem(p, precision=precision)
+    ctx.set_state(bad)
+    ctx.sweep(0, 1e-4)
+    with pytest.raises(ppm.PpmError) as e:
+        ctx.sync()
+    assert e.value.code == -4
+    ctx.set_state(q)
+    o = oracle.Oracle(p)
+    qo = [a.copy() for a in q]
+    for _ in range(2):
+        dt = o.cfl_dt(qo, p.cfl)
+        o.double_step(qo, dt)
+        ctx.step(dt)
+    qg = ctx.get_state()
+    ctx.close()
+    if precision == ppm.FP64_PLAIN:
+        _assert_f64(qg, qo)
+    else:
+        _assert_f32(qg, qo)
+
+
 def test_nonphysical_state_is_reported():
     p = workloads.periodic_box(16)
     q = workloads.build(p)
