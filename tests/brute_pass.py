@@ -1,9 +1,10 @@
-"""A second, separately written statement of one pass of the four-value
-PPM+PPB method: whole-grid, array-at-a-time numpy (every pencil of the grid
-at once, the pass axis last), against which the pencil-by-pencil C++ oracle
-is checked.  Same readings of the paper, independent code: boundary ghosts
-by index arrays, base state by vectorised table lookups, every step as
-shifted-array arithmetic.  Plane-parallel or no gravity; no sources.
+"""A second, separately written statement of one pass of the PPM+PPB method
+(four-value and ten-value forms): whole-grid, array-at-a-time numpy (every
+pencil of the grid at once, the pass axis last), against which the
+pencil-by-pencil C++ oracle is checked.  Same readings of the paper,
+independent code: boundary ghosts by index arrays, base state by vectorised
+table lookups, every step as shifted-array arithmetic.  Plane-parallel or no
+gravity; no sources.
 """
 import numpy as np
 
@@ -59,6 +60,13 @@ def sweep(p, q, axis, dt):
     on = take(q[6 + axis]) * sg
     o1 = take(q[6 + t1])
     o2 = take(q[6 + t2])
+    ten = len(q) == 15
+    if ten:
+        # second moments along (n, t1, t2); mixed moments: c12 of the two
+        # transverse axes, c_n1 / c_n2 of the normal with t1 / t2 (odd in n)
+        qn, q1, q2 = take(q[9 + axis]), take(q[9 + t1]), take(q[9 + t2])
+        c12 = take(q[12 + axis])
+        cn1, cn2 = take(q[12 + t2]) * sg, take(q[12 + t1]) * sg
     # cell positions along every axis (for the base state: plane gravity in z)
     shape = mv(q[0]).shape[:-1] + (n + 2 * G,)
     coord = [p.origin[d] + (np.arange(p.shape[d]) + 0.5) * p.dx for d in range(3)]
@@ -236,7 +244,7 @@ def sweep(p, q, axis, dt):
     # PPB profiles of cells [-2, n+2): own FV and slope, curvature from neighbours
     F = at(fv, 0, il, ih)
     mm = at(on, 0, il, ih)
-    a2 = 0.25 * (at(on, 1, il, ih) - at(on, -1, il, ih))
+    a2 = at(qn, 0, il, ih) if ten else 0.25 * (at(on, 1, il, ih) - at(on, -1, il, ih))
     ep = 0.5 * mm + a2 * (1.0 / 6.0)
     em = a2 * (1.0 / 6.0) - 0.5 * mm
     gmax, gmin = np.maximum(ep, em), np.minimum(ep, em)
@@ -267,8 +275,19 @@ def sweep(p, q, axis, dt):
     psibar = Fd * M1 + med * M2 + aed * (M3 - M1 * (1.0 / 12.0))
     GL, GH = phi * Fd, phi * phibar
     KL, KH = phi * Fd * M1, phi * psibar
-    T1, T2 = phi * o1d, phi * o2d
     PHI, KM = phi, phi * M1
+    if ten:
+        M4 = 0.0625 - 0.25 * s + 0.5 * s * s - 0.5 * s * s * s + 0.2 * s * s * s * s
+        M2r = 0.25 - 0.5 * s + s * s * (1.0 / 3.0)
+        chibar = Fd * M2r + med * M3 + aed * (M4 - M2r * (1.0 / 12.0))
+        K2L, K2H, KM2 = phi * Fd * M2r, phi * chibar, phi * M2r
+        cn1d, cn2d = donor(at(cn1, 0, il, ih)), donor(at(cn2, 0, il, ih))
+        T1, T2 = phi * (o1d + cn1d * M1), phi * (o2d + cn2d * M1)
+        U1, U2 = phi * (o1d * M1 + cn1d * M2r), phi * (o2d * M1 + cn2d * M2r)
+        Q1, Q2 = phi * donor(at(q1, 0, il, ih)), phi * donor(at(q2, 0, il, ih))
+        C12 = phi * donor(at(c12, 0, il, ih))
+    else:
+        T1, T2 = phi * o1d, phi * o2d
     # FCT factors of cells [-1, n+1)
     rold = at(rho0c, 0, cl_, ch_) + rd0
     rnew = at(rho0c, 0, cl_, ch_) + rdn
@@ -289,6 +308,8 @@ def sweep(p, q, axis, dt):
     Cf = np.where(A >= 0, np.minimum(Rp_j1, Rm_j), np.minimum(Rp_j, Rm_j1))
     Gf = GL[..., ff] + Cf * A
     Kf = KL[..., ff] + Cf * (KH[..., ff] - KL[..., ff])
+    if ten:
+        K2f = K2L[..., ff] + Cf * (K2H[..., ff] - K2L[..., ff])
     T1f, T2f, PHIf, KMf = T1[..., ff], T2[..., ff], PHI[..., ff], KM[..., ff]
     sgf = sig[..., ff]
     # update of cells [0, n): faces i - 1/2 (index i in [-1,n) -> i) and i + 1/2 (i+1)
@@ -319,10 +340,49 @@ def sweep(p, q, axis, dt):
     o1n = o1c + (o1c * dPhi - (p_(T1f) - q_(T1f))) / rn
     o2n = o2c + (o2c * dPhi - (p_(T2f) - q_(T2f))) / rn
     bnd = 6.0 * fvn * (1.0 - fvn)
+    if ten:
+        sel = lambda cond, a: np.where(cond, a, 0.0)
+        K2ff, KM2f = K2f, KM2[..., ff]
+        U1f, U2f = U1[..., ff], U2[..., ff]
+        hp_, hm_ = shp, shm
+        z2_out = sel(outp, p_(K2ff)) - sel(~inm, q_(K2ff))
+        zr2_out = sel(outp, p_(KM2f)) - sel(~inm, q_(KM2f))
+        t1_out = sel(outp, p_(T1f)) - sel(~inm, q_(T1f))
+        t2_out = sel(outp, p_(T2f)) - sel(~inm, q_(T2f))
+        u1_out = sel(outp, p_(U1f)) - sel(~inm, q_(U1f))
+        u2_out = sel(outp, p_(U2f)) - sel(~inm, q_(U2f))
+        z2_in = (-sel(~outp, p_(K2ff) + 2.0 * hp_ * p_(Kf) + hp_ * hp_ * p_(Gf))
+                 + sel(inm, q_(K2ff) + 2.0 * hm_ * q_(Kf) + hm_ * hm_ * q_(Gf)))
+        zr2_in = (-sel(~outp, p_(KM2f) + 2.0 * hp_ * p_(KMf) + hp_ * hp_ * p_(PHIf))
+                  + sel(inm, q_(KM2f) + 2.0 * hm_ * q_(KMf) + hm_ * hm_ * q_(PHIf)))
+        u1_in = -sel(~outp, p_(U1f) + p_(T1f) * hp_) + sel(inm, q_(U1f) + q_(T1f) * hm_)
+        u2_in = -sel(~outp, p_(U2f) + p_(T2f) * hp_) + sel(inm, q_(U2f) + q_(T2f) * hm_)
+        S0 = cold - c_out
+        S1 = ro * onc * (1.0 / 12.0) - z_out
+        dZc2 = 2.0 * sbar * S1 + sbar * sbar * S0 + z2_in - z2_out
+        Zr2 = -2.0 * sbar * zr_out + sbar * sbar * (ro - m_out) + zr2_in - zr2_out + (ro - rn) * (1.0 / 12.0)
+        dC2p = dZc2 + dG * (1.0 / 12.0)
+        qnc, q1c, q2c = qn[..., G:G + n], q1[..., G:G + n], q2[..., G:G + n]
+        cn1c, cn2c, c12c = cn1[..., G:G + n], cn2[..., G:G + n], c12[..., G:G + n]
+        qnn = qnc + (qnc * dPhi + 180.0 * (dC2p - fvn * Zr2) - 12.0 * onn * Zr) / rn
+        dY1 = (ro * o1c - t1_out) * sbar + u1_in - u1_out
+        dY2 = (ro * o2c - t2_out) * sbar + u2_in - u2_out
+        cn1n = cn1c + (cn1c * dPhi + 12.0 * (dY1 - o1n * Zr)) / rn
+        cn2n = cn2c + (cn2c * dPhi + 12.0 * (dY2 - o2n * Zr)) / rn
+        Q1f, Q2f, C12f = Q1[..., ff], Q2[..., ff], C12[..., ff]
+        q1n = q1c + (q1c * dPhi - (p_(Q1f) - q_(Q1f))) / rn
+        q2n = q2c + (q2c * dPhi - (p_(Q2f) - q_(Q2f))) / rn
+        c12n = c12c + (c12c * dPhi - (p_(C12f) - q_(C12f))) / rn
+        g_ = fvn * (1.0 - fvn)
+        bm, bcn = 6.0 * g_, 36.0 * g_
+        qlo, qhi = -15.0 * g_ * (1.0 + fvn), 15.0 * g_ * (2.0 - fvn)
+        qnn, q1n, q2n = (np.clip(a, qlo, qhi) for a in (qnn, q1n, q2n))
+        cn1n, cn2n, c12n = (np.clip(a, -bcn, bcn) for a in (cn1n, cn2n, c12n))
+        bnd = bm
     onn, o1n, o2n = (np.clip(a, -bnd, bnd) for a in (onn, o1n, o2n))
     # back to full variables, physical frame
     inner = lambda a: a[..., 1:n + 1]
-    out = [None] * 9
+    out = [None] * (15 if ten else 9)
     r0c = rho0c[..., G:G + n]
     p0cc = p0c[..., G:G + n]
     out[0] = r0c + inner(rdn)
@@ -334,4 +394,7 @@ def sweep(p, q, axis, dt):
     out[6 + axis] = onn
     out[6 + t1] = o1n
     out[6 + t2] = o2n
+    if ten:
+        out[9 + axis], out[9 + t1], out[9 + t2] = qnn, q1n, q2n
+        out[12 + axis], out[12 + t2], out[12 + t1] = c12n, cn1n, cn2n
     return [np.ascontiguousarray(np.moveaxis(a, -1, npax)) for a in out]

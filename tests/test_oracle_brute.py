@@ -1,6 +1,6 @@
 """Brute-force cross-check of the oracle's pencil machinery.
 
-`brute_pass.sweep` restates one four-value PPM+PPB pass (Sec. 1: interface
+`brute_pass.sweep` restates one PPM+PPB pass, four-value and ten-value (Sec. 1: interface
 values, smoothness weights, flattening, constrained parabolas, tracing with
 half-step buoyancy, two-shock Riemann solve, fluxes and gravity sources in
 deviation form, PPB profiles, swept-slab transfers, FCT, moment update) as
@@ -16,6 +16,8 @@ Inputs are made to reach every branch: random volume fractions with cells
 pinned at exactly 0 and 1 (FCT and theta limiting active), a Sod tube
 (flattening and constraints active), plane gravity with reflecting walls.
 """
+import copy
+
 import numpy as np
 import pytest
 
@@ -99,6 +101,52 @@ def test_whole_grid_pass_matches_pencil_oracle(name, p, make, npass, active):
             o.sweep(qo, ax, dt)
             qb = brute_pass.sweep(p, qb, ax, dt)
             for v in range(9):
+                assert np.isfinite(qo[v]).all(), (name, axis, ax, v)
+                assert np.array_equal(qb[v], qo[v]), (name, axis, ax, v,
+                                                      np.abs(qb[v] - qo[v]).max())
+    c = oracle.Oracle.counters()
+    for key in active:
+        assert c[key] > 0, (key, c)
+
+
+def _ten_moments(q, seed):
+    """Second and mixed moments (seeded) inside their realisable ranges:
+    -15 g (1 + FV) <= q_d <= 15 g (2 - FV), |c_de| <= 36 g, g = FV (1 - FV)."""
+    rng = np.random.default_rng(seed)
+    fv = q[5]
+    g = fv * (1.0 - fv)
+    qs = [7.5 * g * rng.uniform(-1.0, 1.0, fv.shape) for _ in range(3)]
+    cs = [20.0 * g * rng.uniform(-1.0, 1.0, fv.shape) for _ in range(3)]
+    return list(q[:9]) + qs + cs
+
+
+def _ten_cases():
+    out = []
+    for name, p, make, npass, active in _cases():
+        if name in ("box", "strat", "box_rough"):
+            p10 = copy.copy(p)
+            p10.nmom = 9
+            out.append((name + "_ten", p10, make, npass, tuple(k for k in active if k != "flattened")))
+    return out
+
+
+@pytest.mark.parametrize("name,p,make,npass,active", _ten_cases(), ids=[c[0] for c in _ten_cases()])
+def test_whole_grid_ten_value_pass_matches_pencil_oracle(name, p, make, npass, active):
+    """The same cross-check for the ten-value form (FV, 3 first, 3 second and
+    3 mixed moments): the swept-slab second moments, the transverse
+    xi-moments and the second-moment and mixed-moment updates."""
+    q0 = _ten_moments(_rough_fv(make(), seed=len(name)), seed=len(name) + 1)
+    o = oracle.Oracle(p)
+    oracle.Oracle.reset_counters()
+    for axis in range(3):
+        qo = [a.copy() for a in q0]
+        qb = [a.copy() for a in q0]
+        for k in range(npass):
+            ax = (axis + k) % 3
+            dt = o.cfl_dt(qo, p.cfl)
+            o.sweep(qo, ax, dt)
+            qb = brute_pass.sweep(p, qb, ax, dt)
+            for v in range(15):
                 assert np.isfinite(qo[v]).all(), (name, axis, ax, v)
                 assert np.array_equal(qb[v], qo[v]), (name, axis, ax, v,
                                                       np.abs(qb[v] - qo[v]).max())
