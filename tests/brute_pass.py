@@ -38,6 +38,25 @@ def _face_pos(n, periodic):
     return np.where(P < 0, -P, np.where(P > n, 2 * n - P, P))
 
 
+def divergence(p, q):
+    """Cell velocity divergence (central differences of u_d = m_d / rho,
+    summed x, y, z), ghosts by the boundary conditions: periodic wrap, or at
+    a wall the mirror cell with its normal velocity reversed."""
+    diffs = []
+    for d in range(3):
+        npd = 2 - d
+        assert p.bc[2 * d] == p.bc[2 * d + 1]
+        u = np.moveaxis(q[1 + d] / q[0], npd, -1)
+        if p.bc[2 * d] == 0:
+            up = np.concatenate([u[..., 1:], u[..., :1]], axis=-1)
+            dn = np.concatenate([u[..., -1:], u[..., :-1]], axis=-1)
+        else:
+            up = np.concatenate([u[..., 1:], -u[..., -1:]], axis=-1)
+            dn = np.concatenate([-u[..., :1], u[..., :-1]], axis=-1)
+        diffs.append(np.moveaxis(up - dn, -1, npd))
+    return ((diffs[0] + diffs[1]) + diffs[2]) * (0.5 / p.dx)
+
+
 def sweep(p, q, axis, dt):
     """One pass along `axis` of the 9 full-variable arrays q (z, y, x)."""
     t = p.tables
@@ -60,6 +79,9 @@ def sweep(p, q, axis, dt):
     on = take(q[6 + axis]) * sg
     o1 = take(q[6 + t1])
     o2 = take(q[6 + t2])
+    kshock = float(getattr(p, "shock_k", 0.0) or 0.0)
+    if kshock > 0.0:
+        dv = take(divergence(p, q))          # even under a mirror
     ten = len(q) == 15
     if ten:
         # second moments along (n, t1, t2); mixed moments: c12 of the two
@@ -230,6 +252,17 @@ def sweep(p, q, axis, dt):
     Fn = Fr * ust + pst
     Ft1, Ft2 = Fr * vst, Fr * wst
     FE = ust * (gg1 * pst + gg1 * p0) + 0.5 * (ust * ust + (vst * vst + wst * wst)) * Fr
+    if kshock > 0.0:
+        # dissipation across faces where the face divergence marks a shock
+        dface = 0.5 * (at(dv, 0, fl_, fh_) + at(dv, 1, fl_, fh_))
+        cface = 0.5 * (CL / rL + CR / rR)
+        nu = kshock * np.maximum(0.0, -(dface * p.dx) - 0.05 * cface)
+        on_ = nu > 0.0
+        jump = lambda a: at(a, 1, fl_, fh_) - at(a, 0, fl_, fh_)
+        Fn = np.where(on_, Fn - nu * jump(mn), Fn)
+        Ft1 = np.where(on_, Ft1 - nu * jump(m1), Ft1)
+        Ft2 = np.where(on_, Ft2 - nu * jump(m2), Ft2)
+        FE = np.where(on_, FE - nu * jump(ed), FE)
     # cells i in [-1, n+1): faces i - 1/2 (index i-1) and i + 1/2 (index i)
     cl_, ch_ = -1, n + 1
     f_m = lambda F: F[..., (cl_ - 1) - fl_:(ch_ - 1) - fl_]

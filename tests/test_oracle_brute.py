@@ -1,6 +1,7 @@
 """Brute-force cross-check of the oracle's pencil machinery.
 
-`brute_pass.sweep` restates one PPM+PPB pass, four-value and ten-value (Sec. 1: interface
+`brute_pass.sweep` restates one PPM+PPB pass, four-value and ten-value, with
+the optional 3-D shock dissipation (Sec. 1: interface
 values, smoothness weights, flattening, constrained parabolas, tracing with
 half-step buoyancy, two-shock Riemann solve, fluxes and gravity sources in
 deviation form, PPB profiles, swept-slab transfers, FCT, moment update) as
@@ -69,11 +70,29 @@ def _evolved(p, q, steps):
     return q
 
 
+def _shock_box(n=16):
+    """Periodic box whose sinusoidal velocity field steepens into shocks,
+    evolved 8 double steps with the 3-D dissipation on."""
+    p = workloads.periodic_box(shape=(n, n, n), mach=0.0)
+    p.shock_k = 0.1
+    q = workloads.build(p)
+    x = (np.arange(n) + 0.5) / n
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    q[1] += 0.9 * np.sin(2 * np.pi * X) * np.cos(2 * np.pi * Y)
+    q[2] += 0.9 * np.sin(2 * np.pi * Y) * np.cos(2 * np.pi * Z)
+    q[3] += 0.9 * np.sin(2 * np.pi * Z)
+    q[4] += 0.5 * (q[1] ** 2 + q[2] ** 2 + q[3] ** 2) / q[0]
+    o = oracle.Oracle(p)
+    for _ in range(8):
+        o.double_step(q, o.cfl_dt(q, 0.5))
+    return p, q
+
+
 def _cases():
     box = workloads.periodic_box(shape=(8, 6, 10), mach=0.3)
     strat = workloads.strat_box(shape=(8, 6, 12))
     sod = workloads.tube("sod", n=16, axis=0, ntrans=6)
-    return [
+    out = [
         # (name, problem, state builder, passes in sequence, counters that must be > 0)
         ("box", box, lambda: workloads.build(box), 2, ("theta_limited", "moment_clamped")),
         ("strat", strat, lambda: workloads.build(strat), 2, ("theta_limited", "nonsmooth")),
@@ -84,6 +103,16 @@ def _cases():
         ("strat_rough", strat, lambda: _rough_flow(strat, workloads.build(strat), 2, 0.7, 0.1), 1,
          ("flattened", "nonsmooth")),
     ]
+    shock_p, shock_q = _shock_box()
+    sod_k = copy.copy(sod)
+    sod_k.shock_k = 0.1
+    out += [
+        # 3-D shock dissipation: a periodic box after its shocks formed, and
+        # an evolved Sod tube between walls
+        ("shock_box", shock_p, lambda: [a.copy() for a in shock_q], 2, ("dissipative_faces", "flattened")),
+        ("sod_shock", sod_k, lambda: _evolved(sod_k, workloads.build(sod_k), 4), 2, ("dissipative_faces",)),
+    ]
+    return out
 
 
 @pytest.mark.parametrize("name,p,make,npass,active", _cases(), ids=[c[0] for c in _cases()])
