@@ -173,8 +173,11 @@ int ppm_sweep(ppm_ctx *ctx, int axis, double dt, int sources);
  * work, no wait); EINVAL if not finite. */
 int ppm_set_rotation(ppm_ctx *ctx, double domega);
 
-/* FP64 reductions of the current state:
- * totals[7] = (M, Px, Py, Pz, E, sum rho*FV, sum FV), each times dx^3;
+/* Reductions of the current state to FP64 accuracy:
+ * totals[7] = (M, Px, Py, Pz, E, sum rho*FV, sum FV), each times dx^3 (FP32
+ * form: each thread sums its cells as float pairs with exact error terms,
+ * added into FP64 every 32 cells, plus the FP64 sums of the base state; the
+ * first call builds the cached base state, 12 bytes per cell);
  * profiles (may be NULL when nbins == 0): nbins x 5 volume averages of
  * (rho, p, FV, |u|, u_r^2) over shells of width rmax/nbins about the
  * coordinate origin (Sec. 1: averages on spherical surfaces), 0 <= nbins <= 1024;
