@@ -220,6 +220,8 @@ class Context:
         return out
 
     def get_state_into(self, out: Sequence[np.ndarray]):
+        assert len(out) == self.nvar and all(
+            a.dtype == np.float64 and a.size == self.ncell and a.flags.c_contiguous for a in out)
         self._check(self.lib.ppm_get_state(self.h, _ptrs(out)))
 
     @staticmethod
@@ -232,11 +234,15 @@ class Context:
     def set_region(self, lo, hi, q, device: bool = False):
         """q: 6 + nmom host float64 arrays, or CUDA float64 tensors when device=True."""
         assert len(q) == self.nvar
+        nb = (hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2])
         if device:
+            import torch
+            assert all(t.dtype == torch.float64 and t.numel() == nb and t.is_contiguous() for t in q)
             self._sync_torch()
             ptrs = (_DP * len(q))(*[C.cast(C.c_void_p(int(t.data_ptr())), _DP) for t in q])
         else:
             q = [_f64(a) for a in q]
+            assert all(a.size == nb for a in q)
             ptrs = _ptrs(q)
         self._check(self.lib.ppm_set_region(self.h, (C.c_int * 3)(*lo), (C.c_int * 3)(*hi), ptrs,
                                             MEM_DEVICE if device else MEM_HOST))
@@ -246,10 +252,14 @@ class Context:
         if out is None:
             out = [np.empty((b[2], b[1], b[0])) for _ in range(self.nvar)]
         assert len(out) == self.nvar
+        nb = b[0] * b[1] * b[2]
         if device:
+            import torch
+            assert all(t.dtype == torch.float64 and t.numel() == nb and t.is_contiguous() for t in out)
             self._sync_torch()
             ptrs = (_DP * len(out))(*[C.cast(C.c_void_p(int(t.data_ptr())), _DP) for t in out])
         else:
+            assert all(a.dtype == np.float64 and a.size == nb and a.flags.c_contiguous for a in out)
             ptrs = _ptrs(out)
         self._check(self.lib.ppm_get_region(self.h, (C.c_int * 3)(*lo), (C.c_int * 3)(*hi), ptrs,
                                             MEM_DEVICE if device else MEM_HOST))
@@ -354,14 +364,21 @@ class Ensemble:
 
     def set_state(self, box: int, q):
         arrs = [_f64(a) for a in q]
+        nx, ny, nz = self.shapes[box]
+        assert len(arrs) == 9 and all(a.size == nx * ny * nz for a in arrs)
         self._check(self.lib.ppm_ensemble_set_state(self.h, int(box), _ptrs(arrs)))
 
     def set_region(self, box: int, lo, hi, q, device: bool = False):
+        assert len(q) == 9
+        nb = (hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2])
         if device:
+            import torch
+            assert all(t.dtype == torch.float64 and t.numel() == nb and t.is_contiguous() for t in q)
             Context._sync_torch()
             ptrs = (_DP * len(q))(*[C.cast(C.c_void_p(int(t.data_ptr())), _DP) for t in q])
         else:
             q = [_f64(a) for a in q]
+            assert all(a.size == nb for a in q)
             ptrs = _ptrs(q)
         self._check(self.lib.ppm_ensemble_set_region(self.h, int(box), (C.c_int * 3)(*lo), (C.c_int * 3)(*hi),
                                                      ptrs, MEM_DEVICE if device else MEM_HOST))
