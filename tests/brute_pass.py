@@ -115,6 +115,33 @@ def sweep(p, q, axis, dt):
         p0f = np.broadcast_to(_lerp(t.p0, t.s0, t.ds, zf), shape)
     rd = rho_full - rho0c
     ed = E - p0c / gm1
+    g = dict(rd=rd, mn=mn, m1=m1, m2=m2, ed=ed, fv=fv, on=on, o1=o1, o2=o2, rho0c=rho0c, p0c=p0c, gc=gc,
+             rho0f=rho0f, p0f=p0f)
+    if kshock > 0.0:
+        g["dv"] = dv
+    if ten:
+        g.update(qn=qn, q1=q1, q2=q2, c12=c12, cn1=cn1, cn2=cn2)
+    out = _core(p, axis, dt, n, not periodic, g)
+    return [np.ascontiguousarray(np.moveaxis(a, -1, npax)) for a in out]
+
+
+def _core(p, axis, dt, n, walls, g):
+    """Steps a1 (primitives) to a9 on pencil-batched arrays (pass axis
+    last, n cells plus G ghosts on each side), walls at both ends or not.
+    Returns the new full variables of the n cells, in the pass frame's
+    storage order (index = stored variable)."""
+    t = p.tables
+    gam, gm1 = p.gamma, p.gamma - 1.0
+    t1, t2 = (axis + 1) % 3, (axis + 2) % 3
+    kshock = float(getattr(p, "shock_k", 0.0) or 0.0)
+    ten = "qn" in g
+    rd, mn, m1, m2, ed = g["rd"], g["mn"], g["m1"], g["m2"], g["ed"]
+    fv, on, o1, o2 = g["fv"], g["on"], g["o1"], g["o2"]
+    rho0c, p0c, gc, rho0f, p0f = g["rho0c"], g["p0c"], g["gc"], g["rho0f"], g["p0f"]
+    if kshock > 0.0:
+        dv = g["dv"]
+    if ten:
+        qn, q1, q2, c12, cn1, cn2 = g["qn"], g["q1"], g["q2"], g["c12"], g["cn1"], g["cn2"]
     # primitives
     rho = rho0c + rd
     u, v, w = mn / rho, m1 / rho, m2 / rho
@@ -238,7 +265,7 @@ def sweep(p, q, axis, dt):
     pst = pdL + WLi * (WRi * (uL - uR) + (pdR - pdL)) / den
     ust = uL + (WRi * (uR - uL) + (pdL - pdR)) / den
     pst = np.where(p0 + pst < pfl, pfl - p0, pst)
-    if not periodic:
+    if walls:
         jj = np.arange(fl_, fh_)
         ust = np.where((jj == -1) | (jj == n - 1), 0.0, ust)
     left = ust >= 0
@@ -430,4 +457,87 @@ def sweep(p, q, axis, dt):
     if ten:
         out[9 + axis], out[9 + t1], out[9 + t2] = qnn, q1n, q2n
         out[12 + axis], out[12 + t2], out[12 + t1] = c12n, cn1n, cn2n
+    return out
+
+
+def _fold(i, n):
+    """Source cell and mirror flag of pencil index i for a run of n cells
+    with walls at both ends: the run and its mirror images repeat with
+    period 2n."""
+    k = np.mod(i, 2 * n)
+    inside = (i >= 0) & (i < n)
+    src = np.where(inside, i, np.where(k < n, k, 2 * n - 1 - k))
+    flip = ~inside & (k >= n)
+    return src, flip
+
+
+def _fold_face(j, n):
+    """Position (cells from the run's low end) of face j + 1/2, walls at
+    both ends, same images as _fold."""
+    P = j + 1
+    k = np.mod(P, 2 * n)
+    return np.where((P >= 0) & (P <= n), P, np.where(k <= n, k, 2 * n - k))
+
+
+def _central_base(p, x, y, z):
+    """rho0, p0 and g/r at points (x, y, z): tables in r about the origin."""
+    t = p.tables
+    r = np.sqrt((x * x + y * y) + z * z)
+    rho0 = _lerp(t.rho0, t.s0, t.ds, r)
+    p0 = _lerp(t.p0, t.s0, t.ds, r)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        gor = np.where(r > 0.0, _lerp(t.g, t.s0, t.ds, r) / r, 0.0)
+    return rho0, p0, gor
+
+
+def sweep_confined(p, q, axis, dt):
+    """One pass along `axis` with a confining sphere (central gravity, four
+    values): every pencil's run of fluid cells is updated as a pencil with
+    walls at both ends; pencils are batched by their run (start, length)."""
+    assert p.grav == 2 and p.confine_r > 0.0 and len(q) == 9
+    gm1 = p.gamma - 1.0
+    t1, t2 = (axis + 1) % 3, (axis + 2) % 3
+    npax = 2 - axis
+    mv = lambda a: np.moveaxis(a, npax, -1)
+    coord = [p.origin[d] + (np.arange(p.shape[d]) + 0.5) * p.dx for d in range(3)]
+    Z, Y, X = np.meshgrid(coord[2], coord[1], coord[0], indexing="ij")
+    fluid = mv((X * X + Y * Y) + Z * Z < p.confine_r * p.confine_r)
+    XYZ = [mv(X), mv(Y), mv(Z)]
+    qm = [mv(a) for a in q]
+    out = [a.copy() for a in qm]
+    groups = {}
+    for lead in np.ndindex(fluid.shape[:-1]):
+        f = fluid[lead]
+        idx = np.nonzero(f)[0]
+        if idx.size == 0:
+            continue
+        i0, n = int(idx[0]), int(idx.size)
+        assert idx[-1] - idx[0] + 1 == n
+        groups.setdefault((i0, n), []).append(lead)
+    for (i0, n), leads in groups.items():
+        l1 = np.array([a for a, _ in leads])
+        l2 = np.array([b for _, b in leads])
+        i = np.arange(-G, n + G)
+        src, flip = _fold(i, n)
+        cells = i0 + src
+        sg = np.where(flip, -1.0, 1.0)
+        take = lambda a: a[l1, l2][:, cells]
+        pos = [take(c) for c in XYZ]
+        rho0c, p0c, gor = _central_base(p, pos[0], pos[1], pos[2])
+        gc = (gor * pos[axis]) * sg
+        # faces: along-axis position from the folded face index, transverse
+        # coordinates those of the pencil
+        fpos = [np.broadcast_to(c[l1, l2][:, :1], (len(leads), n + 2 * G)) for c in XYZ]
+        fpos[axis] = p.origin[axis] + (i0 + _fold_face(i, n)) * p.dx
+        fpos[axis] = np.broadcast_to(fpos[axis], (len(leads), n + 2 * G))
+        rho0f, p0f, _ = _central_base(p, fpos[0], fpos[1], fpos[2])
+        g = dict(rd=take(qm[0]) - rho0c, mn=take(qm[1 + axis]) * sg, m1=take(qm[1 + t1]),
+                 m2=take(qm[1 + t2]), ed=take(qm[4]) - p0c / gm1, fv=take(qm[5]),
+                 on=take(qm[6 + axis]) * sg, o1=take(qm[6 + t1]), o2=take(qm[6 + t2]),
+                 rho0c=rho0c, p0c=p0c, gc=gc, rho0f=rho0f, p0f=p0f)
+        res = _core(p, axis, dt, n, True, g)
+        run = np.arange(i0, i0 + n)
+        for v in range(9):
+            o = out[v]
+            o[l1[:, None], l2[:, None], run[None, :]] = res[v]
     return [np.ascontiguousarray(np.moveaxis(a, -1, npax)) for a in out]

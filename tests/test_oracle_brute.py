@@ -1,7 +1,8 @@
 """Brute-force cross-check of the oracle's pencil machinery.
 
 `brute_pass.sweep` restates one PPM+PPB pass, four-value and ten-value, with
-the optional 3-D shock dissipation (Sec. 1: interface
+the optional 3-D shock dissipation, and `brute_pass.sweep_confined` the pass
+inside the confining sphere (Sec. 1: interface
 values, smoothness weights, flattening, constrained parabolas, tracing with
 half-step buoyancy, two-shock Riemann solve, fluxes and gravity sources in
 deviation form, PPB profiles, swept-slab transfers, FCT, moment update) as
@@ -182,3 +183,29 @@ def test_whole_grid_ten_value_pass_matches_pencil_oracle(name, p, make, npass, a
     c = oracle.Oracle.counters()
     for key in active:
         assert c[key] > 0, (key, c)
+
+
+@pytest.mark.parametrize("shape,min_run", [((24, 24, 24), 4), ((22, 19, 26), 2), ((21, 23, 25), 3)])
+def test_whole_grid_confined_pass_matches_pencil_oracle(shape, min_run):
+    """The confining sphere (Sec. 3) with central gravity tapered inside it:
+    pencils batched by their fluid run, each run a pencil with walls at both
+    ends and period-2n folded ghosts (runs of 2 and 3 cells at the rim included),
+    base state at mirrored cells and folded faces from the radial tables."""
+    p = workloads.sphere(shape=shape, confine=True)
+    q0 = _rough_fv(workloads.build(p), seed=sum(shape))
+    o = oracle.Oracle(p)
+    xs = [p.origin[d] + (np.arange(p.shape[d]) + 0.5) * p.dx for d in range(3)]
+    Z, Y, X = np.meshgrid(xs[2], xs[1], xs[0], indexing="ij")
+    fluid = (X * X + Y * Y) + Z * Z < p.confine_r ** 2
+    shortest = min(int(fluid.sum(axis=a)[fluid.sum(axis=a) > 0].min()) for a in range(3))
+    assert shortest == min_run                      # runs shorter than the stencil at the rim
+    for axis in range(3):
+        qo = [a.copy() for a in q0]
+        qb = [a.copy() for a in q0]
+        for k in range(2):
+            ax = (axis + k) % 3
+            dt = o.cfl_dt(qo, p.cfl)
+            o.sweep(qo, ax, dt)
+            qb = brute_pass.sweep_confined(p, qb, ax, dt)
+            for v in range(9):
+                assert np.array_equal(qb[v], qo[v]), (shape, axis, ax, v, np.abs(qb[v] - qo[v]).max())
