@@ -57,8 +57,9 @@ def divergence(p, q):
     return ((diffs[0] + diffs[1]) + diffs[2]) * (0.5 / p.dx)
 
 
-def sweep(p, q, axis, dt):
-    """One pass along `axis` of the 9 full-variable arrays q (z, y, x)."""
+def sweep(p, q, axis, dt, sources=0, domega=0.0):
+    """One pass along `axis` of the full-variable arrays q (z, y, x);
+    sources: bit 0 heating / damping, bit 1 the rotation increment domega."""
     t = p.tables
     gam, gm1 = p.gamma, p.gamma - 1.0
     n = p.shape[axis]
@@ -98,6 +99,17 @@ def sweep(p, q, axis, dt):
         gc = np.zeros(shape)
         rho0f = np.full(shape, t.rho0[0])
         p0f = np.full(shape, t.p0[0])
+    elif p.grav == 2:
+        # central gravity: tables in r at the mirrored cells' own positions
+        # and at the folded faces (transverse coordinates of the pencil)
+        Z3, Y3, X3 = np.meshgrid(coord[2], coord[1], coord[0], indexing="ij")
+        XYZ = [mv(X3), mv(Y3), mv(Z3)]
+        pos = [np.take(c, src, axis=-1) for c in XYZ]
+        rho0c, p0c, gor = _central_base(p, pos[0], pos[1], pos[2])
+        gc = (gor * pos[axis]) * sg
+        fpos = [np.broadcast_to(c[..., :1], shape) for c in XYZ]
+        fpos[axis] = np.broadcast_to(p.origin[axis] + _face_pos(n, periodic) * p.dx, shape)
+        rho0f, p0f, _ = _central_base(p, fpos[0], fpos[1], fpos[2])
     else:
         assert p.grav == 1
         if axis == 2:
@@ -121,11 +133,41 @@ def sweep(p, q, axis, dt):
         g["dv"] = dv
     if ten:
         g.update(qn=qn, q1=q1, q2=q2, c12=c12, cn1=cn1, cn2=cn2)
-    out = _core(p, axis, dt, n, not periodic, g)
+    src_info = None
+    if sources:
+        Z3, Y3, X3 = np.meshgrid(coord[2], coord[1], coord[0], indexing="ij")
+        src_info = dict(flags=sources, domega=domega, pos=[mv(X3), mv(Y3), mv(Z3)])
+    out = _core(p, axis, dt, n, not periodic, g, src_info)
     return [np.ascontiguousarray(np.moveaxis(a, -1, npax)) for a in out]
 
 
-def _core(p, axis, dt, n, walls, g):
+def _sources(p, axis, dt, rho, mn, m1, m2, ed, info):
+    """Heating / damping (bit 0) then the rotation increment (bit 1) on the
+    new values of the updated cells, in the pass frame."""
+    t = p.tables
+    t1, t2 = (axis + 1) % 3, (axis + 2) % 3
+    x, y, z = info["pos"]
+    if (info["flags"] & 1) and (t.heat is not None or t.damp is not None):
+        sv = z if p.grav == 1 else np.sqrt((x * x + y * y) + z * z)
+        if t.heat is not None:
+            ed = ed + dt * _lerp(t.heat, t.s0, t.ds, sv)
+        if t.damp is not None:
+            kd = _lerp(t.damp, t.s0, t.ds, sv)
+            f = np.maximum(0.0, 1.0 - dt * kd)
+            ke = 0.5 * (mn * mn + (m1 * m1 + m2 * m2)) / rho
+            mn, m1, m2 = mn * f, m1 * f, m2 * f
+            ed = ed - (1.0 - f * f) * ke
+    if (info["flags"] & 2) and info["domega"] != 0.0:
+        w = info["domega"]
+        du = [-(w * y), w * x, np.zeros_like(x)]
+        dn, d1, d2 = du[axis], du[t1], du[t2]
+        dE = (mn * dn + (m1 * d1 + m2 * d2)) + 0.5 * rho * (dn * dn + (d1 * d1 + d2 * d2))
+        mn, m1, m2 = mn + rho * dn, m1 + rho * d1, m2 + rho * d2
+        ed = ed + dE
+    return mn, m1, m2, ed
+
+
+def _core(p, axis, dt, n, walls, g, src_info=None):
     """Steps a1 (primitives) to a9 on pencil-batched arrays (pass axis
     last, n cells plus G ghosts on each side), walls at both ends or not.
     Returns the new full variables of the n cells, in the pass frame's
@@ -445,11 +487,14 @@ def _core(p, axis, dt, n, walls, g):
     out = [None] * (15 if ten else 9)
     r0c = rho0c[..., G:G + n]
     p0cc = p0c[..., G:G + n]
+    mni, m1i, m2i, edi = inner(mnn), inner(m1n), inner(m2n), inner(edn)
+    if src_info is not None:
+        mni, m1i, m2i, edi = _sources(p, axis, dt, r0c + inner(rdn), mni, m1i, m2i, edi, src_info)
     out[0] = r0c + inner(rdn)
-    out[1 + axis] = inner(mnn)
-    out[1 + t1] = inner(m1n)
-    out[1 + t2] = inner(m2n)
-    out[4] = p0cc / gm1 + inner(edn)
+    out[1 + axis] = mni
+    out[1 + t1] = m1i
+    out[1 + t2] = m2i
+    out[4] = p0cc / gm1 + edi
     out[5] = fvn
     out[6 + axis] = onn
     out[6 + t1] = o1n
@@ -490,7 +535,7 @@ def _central_base(p, x, y, z):
     return rho0, p0, gor
 
 
-def sweep_confined(p, q, axis, dt):
+def sweep_confined(p, q, axis, dt, sources=0, domega=0.0):
     """One pass along `axis` with a confining sphere (central gravity, four
     values): every pencil's run of fluid cells is updated as a pencil with
     walls at both ends; pencils are batched by their run (start, length)."""
@@ -535,8 +580,11 @@ def sweep_confined(p, q, axis, dt):
                  m2=take(qm[1 + t2]), ed=take(qm[4]) - p0c / gm1, fv=take(qm[5]),
                  on=take(qm[6 + axis]) * sg, o1=take(qm[6 + t1]), o2=take(qm[6 + t2]),
                  rho0c=rho0c, p0c=p0c, gc=gc, rho0f=rho0f, p0f=p0f)
-        res = _core(p, axis, dt, n, True, g)
         run = np.arange(i0, i0 + n)
+        info = None
+        if sources:
+            info = dict(flags=sources, domega=domega, pos=[c[l1, l2][:, run] for c in XYZ])
+        res = _core(p, axis, dt, n, True, g, info)
         for v in range(9):
             o = out[v]
             o[l1[:, None], l2[:, None], run[None, :]] = res[v]

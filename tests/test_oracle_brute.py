@@ -209,3 +209,23 @@ def test_whole_grid_confined_pass_matches_pencil_oracle(shape, min_run):
             qb = brute_pass.sweep_confined(p, qb, ax, dt)
             for v in range(9):
                 assert np.array_equal(qb[v], qo[v]), (shape, axis, ax, v, np.abs(qb[v] - qo[v]).max())
+
+
+@pytest.mark.parametrize("sources,domega", [(0, 0.0), (1, 0.0), (3, 0.01)])
+@pytest.mark.parametrize("confine", [False, True])
+def test_whole_grid_sphere_pass_with_sources_matches_pencil_oracle(sources, domega, confine):
+    """The benchmark's workload: the sphere in the cube with central gravity
+    and reflecting walls (or confined), with the heating and damping (bit 0)
+    and the rotation increment (bit 1) applied after the pass."""
+    p = workloads.sphere(shape=(20, 18, 22), confine=confine)
+    q0 = _rough_fv(workloads.build(p), seed=7)
+    o = oracle.Oracle(p)
+    o.set_rotation(domega)
+    step = brute_pass.sweep_confined if confine else brute_pass.sweep
+    for axis in range(3):
+        qo = [a.copy() for a in q0]
+        dt = o.cfl_dt(qo, p.cfl)
+        o.sweep(qo, axis, dt, sources=sources)
+        qb = step(p, [a.copy() for a in q0], axis, dt, sources=sources, domega=domega)
+        for v in range(9):
+            assert np.array_equal(qb[v], qo[v]), (axis, v, np.abs(qb[v] - qo[v]).max())
