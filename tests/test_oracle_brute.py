@@ -229,3 +229,21 @@ def test_whole_grid_sphere_pass_with_sources_matches_pencil_oracle(sources, dome
         qb = step(p, [a.copy() for a in q0], axis, dt, sources=sources, domega=domega)
         for v in range(9):
             assert np.array_equal(qb[v], qo[v]), (axis, v, np.abs(qb[v] - qo[v]).max())
+
+
+def test_whole_grid_double_step_matches_pencil_oracle():
+    """Strang double step (Sec. 1 / Sec. 4 directional splitting): X Y Z,
+    heating and damping after that Z pass, then Z Y X with heating, damping
+    and the rotation increment after the last X pass, one dt."""
+    p = workloads.sphere(shape=(20, 18, 22))
+    q = _rough_fv(workloads.build(p), seed=11)
+    o = oracle.Oracle(p)
+    o.set_rotation(0.02)
+    qo = [a.copy() for a in q]
+    dt = o.cfl_dt(qo, p.cfl)
+    o.double_step(qo, dt)
+    qb = [a.copy() for a in q]
+    for axis, src in ((0, 0), (1, 0), (2, 1), (2, 0), (1, 0), (0, 3)):
+        qb = brute_pass.sweep(p, qb, axis, dt, sources=src, domega=0.02)
+    for v in range(9):
+        assert np.array_equal(qb[v], qo[v]), (v, np.abs(qb[v] - qo[v]).max())
