@@ -380,12 +380,11 @@ def _core(p, axis, dt, n, walls, g, src_info=None):
     PHI, KM = phi, phi * M1
     if ten:
         M4 = 0.0625 - 0.25 * s + 0.5 * s * s - 0.5 * s * s * s + 0.2 * s * s * s * s
-        M2r = 0.25 - 0.5 * s + s * s * (1.0 / 3.0)
-        chibar = Fd * M2r + med * M3 + aed * (M4 - M2r * (1.0 / 12.0))
-        K2L, K2H, KM2 = phi * Fd * M2r, phi * chibar, phi * M2r
+        chibar = Fd * M2 + med * M3 + aed * (M4 - M2 * (1.0 / 12.0))
+        K2L, K2H, KM2 = phi * Fd * M2, phi * chibar, phi * M2
         cn1d, cn2d = donor(at(cn1, 0, il, ih)), donor(at(cn2, 0, il, ih))
         T1, T2 = phi * (o1d + cn1d * M1), phi * (o2d + cn2d * M1)
-        U1, U2 = phi * (o1d * M1 + cn1d * M2r), phi * (o2d * M1 + cn2d * M2r)
+        U1, U2 = phi * (o1d * M1 + cn1d * M2), phi * (o2d * M1 + cn2d * M2)
         Q1, Q2 = phi * donor(at(q1, 0, il, ih)), phi * donor(at(q2, 0, il, ih))
         C12 = phi * donor(at(c12, 0, il, ih))
     else:
@@ -444,21 +443,20 @@ def _core(p, axis, dt, n, walls, g, src_info=None):
     bnd = 6.0 * fvn * (1.0 - fvn)
     if ten:
         sel = lambda cond, a: np.where(cond, a, 0.0)
-        K2ff, KM2f = K2f, KM2[..., ff]
+        KM2f = KM2[..., ff]
         U1f, U2f = U1[..., ff], U2[..., ff]
-        hp_, hm_ = shp, shm
-        z2_out = sel(outp, p_(K2ff)) - sel(~inm, q_(K2ff))
+        z2_out = sel(outp, p_(K2f)) - sel(~inm, q_(K2f))
         zr2_out = sel(outp, p_(KM2f)) - sel(~inm, q_(KM2f))
         t1_out = sel(outp, p_(T1f)) - sel(~inm, q_(T1f))
         t2_out = sel(outp, p_(T2f)) - sel(~inm, q_(T2f))
         u1_out = sel(outp, p_(U1f)) - sel(~inm, q_(U1f))
         u2_out = sel(outp, p_(U2f)) - sel(~inm, q_(U2f))
-        z2_in = (-sel(~outp, p_(K2ff) + 2.0 * hp_ * p_(Kf) + hp_ * hp_ * p_(Gf))
-                 + sel(inm, q_(K2ff) + 2.0 * hm_ * q_(Kf) + hm_ * hm_ * q_(Gf)))
-        zr2_in = (-sel(~outp, p_(KM2f) + 2.0 * hp_ * p_(KMf) + hp_ * hp_ * p_(PHIf))
-                  + sel(inm, q_(KM2f) + 2.0 * hm_ * q_(KMf) + hm_ * hm_ * q_(PHIf)))
-        u1_in = -sel(~outp, p_(U1f) + p_(T1f) * hp_) + sel(inm, q_(U1f) + q_(T1f) * hm_)
-        u2_in = -sel(~outp, p_(U2f) + p_(T2f) * hp_) + sel(inm, q_(U2f) + q_(T2f) * hm_)
+        z2_in = (-sel(~outp, p_(K2f) + 2.0 * shp * p_(Kf) + shp * shp * p_(Gf))
+                 + sel(inm, q_(K2f) + 2.0 * shm * q_(Kf) + shm * shm * q_(Gf)))
+        zr2_in = (-sel(~outp, p_(KM2f) + 2.0 * shp * p_(KMf) + shp * shp * p_(PHIf))
+                  + sel(inm, q_(KM2f) + 2.0 * shm * q_(KMf) + shm * shm * q_(PHIf)))
+        u1_in = -sel(~outp, p_(U1f) + p_(T1f) * shp) + sel(inm, q_(U1f) + q_(T1f) * shm)
+        u2_in = -sel(~outp, p_(U2f) + p_(T2f) * shp) + sel(inm, q_(U2f) + q_(T2f) * shm)
         S0 = cold - c_out
         S1 = ro * onc * (1.0 / 12.0) - z_out
         dZc2 = 2.0 * sbar * S1 + sbar * sbar * S0 + z2_in - z2_out
