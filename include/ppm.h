@@ -258,7 +258,7 @@ int ppm_ensemble_cfl_dt(ppm_ens *e, double cfl, double *dt_out);
 /* One Strang double step of every box as one graph launch; dt > 0: that dt
  * for all boxes; dt <= 0: each box's device dt (ESTATE before any cfl). */
 int ppm_ensemble_step(ppm_ens *e, double dt);
-/* FP64 totals and max Mach of one box (as ppm_diagnostics). */
+/* Totals (to FP64 accuracy) and max Mach of one box (as ppm_diagnostics). */
 int ppm_ensemble_diagnostics(ppm_ens *e, int box, double totals[7], double *max_mach);
 /* Wait for the ensemble's work; ENONPHYS if any box flagged a bad cell. */
 int ppm_ensemble_sync(ppm_ens *e);
