@@ -52,8 +52,12 @@ def _peaks():
 
 
 def _src_hash() -> str:
+    """Hash of the FP32 pass as compiled: its source and its nvcc flags."""
+    import importlib
+    _b = importlib.import_module("paper_1810_13416_gb300.build")
     with open(SWEEP_SRC, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+        src = f.read()
+    return hashlib.sha256(src + repr(_b.UNIT_FLAGS.get("sweep_f32")).encode()).hexdigest()[:16]
 
 
 def _traffic_per_cell(prec: str):
