@@ -22,3 +22,21 @@ def test_reference_arm_prints_one_contract_line():
     assert d["impl"] == "reference" and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+
+
+def test_traffic_figure_is_tied_to_the_pass_source_and_flags(monkeypatch):
+    """`roofline.traffic` comes from the committed ncu figures only while the
+    pass source and its nvcc flags are those they were taken on."""
+    sys.path.insert(0, ROOT)
+    import importlib
+    import bench
+    b = importlib.import_module("paper_1810_13416_gb300.build")
+    with open(bench.TRAFFIC_JSON) as f:
+        committed = json.load(f)["f32"]["sweep_src_sha256_16"]
+    assert bench._src_hash() == committed
+    assert bench._traffic_per_cell("f32") is not None
+    flags = dict(b.UNIT_FLAGS)
+    flags["sweep_f32"] = [f for f in flags["sweep_f32"] if f != "-ftz=true"]
+    monkeypatch.setattr(b, "UNIT_FLAGS", flags)
+    assert bench._src_hash() != committed
+    assert bench._traffic_per_cell("f32") is None
