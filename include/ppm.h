@@ -214,12 +214,20 @@ long long ppm_launch_count(const ppm_ctx *ctx);
  * Limits: nz <= PPM_NOALLOC_MAX_PLANES (else EINVAL with a message from
  * ppm_last_error(NULL)).  Scratch: a fixed static device array of
  * PPM_NOALLOC_MAX_PLANES x 8 doubles (512 KiB), held by every GPU that loads
- * the library until the process exits; each call overwrites the rows it uses
- * (nothing carries over from one call to the next, so nothing needs
- * clearing), and calls that overlap on the GPU race on it.  The first call on
- * each device looks up the array's device address (a one-time set-up); make
- * that first call before any stream capture.  Errors: EINVAL (NULL pointers,
- * extents, nz too large), ECUDA (lookup or launch failed). */
+ * the library until the process exits.  All calls on a device share that one
+ * array and it keeps the last call's contents; each call overwrites the rows
+ * it uses before reading them (nothing needs clearing), and calls that
+ * overlap on the GPU (for example on two streams) race on it.  Each call
+ * looks up the array's device address in the current context
+ * (cudaGetSymbolAddress, which allocates nothing once the library's device
+ * code is loaded), so a device reset between calls leaves no stale address.
+ * The first call on each device is its set-up: CUDA loads device code lazily
+ * by default, so that call may load this library's module and map the array,
+ * which can allocate device memory.  Make the first call once, outside any
+ * budgeted step loop and before any stream capture.  Errors: EINVAL (NULL
+ * pointers, extents, nz too large), ECUDA (an earlier CUDA error still
+ * pending -- reported, not cleared -- or the lookup or a launch failed; the
+ * message names which). */
 int ppm_totals_noalloc(const double *const q_dev[9], int nx, int ny, int nz, double dx,
                        double *totals_dev, void *stream);
 

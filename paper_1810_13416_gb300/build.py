@@ -39,21 +39,37 @@ def _sources():
     return srcs
 
 
-def stale() -> bool:
-    if not os.path.exists(LIB):
+def _stamp(extra=()) -> str:
+    """Hash of every source's contents and of the full nvcc command lines, so
+    that a change of a flag (not only of a source) triggers a rebuild."""
+    import hashlib
+    h = hashlib.sha256()
+    for src in sorted(_sources()):
+        h.update(os.path.basename(src).encode())
+        with open(src, "rb") as f:
+            h.update(f.read())
+    h.update(repr((ARCH, FLAGS, sorted(UNIT_FLAGS.items()), UNITS, list(extra))).encode())
+    return h.hexdigest()
+
+
+STAMP = os.path.join(BUILD, "stamp")
+
+
+def stale(extra=()) -> bool:
+    if not os.path.exists(LIB) or not os.path.exists(STAMP):
         return True
-    t = os.path.getmtime(LIB)
-    return any(os.path.getmtime(s) > t for s in _sources())
+    with open(STAMP) as f:
+        return f.read().strip() != _stamp(extra)
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
-    """Build libppm.so if missing or older than its sources; returns its path."""
+    """Build libppm.so if missing or if its sources or flags changed; returns its path."""
     with _lock:
-        if not force and not stale():
+        extra = list(extra_flags or [])
+        if not force and not stale(extra):
             return LIB
         os.makedirs(BUILD, exist_ok=True)
         nvcc = _nvcc()
-        extra = list(extra_flags or [])
         procs = []
         for u in UNITS:
             obj = os.path.join(BUILD, u + ".o")
@@ -76,6 +92,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
         os.replace(tmp, LIB)
         with open(os.path.join(BUILD, "ptxas.log"), "w") as f:
             f.write("\n".join(logs))
+        with open(STAMP, "w") as f:
+            f.write(_stamp(extra))
     return LIB
 
 

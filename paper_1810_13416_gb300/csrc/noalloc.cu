@@ -12,7 +12,6 @@
 #include <cuda_runtime.h>
 
 #include <cstdio>
-#include <mutex>
 
 #include "../../include/ppm.h"
 
@@ -24,14 +23,10 @@ namespace {
 
 constexpr int NOALLOC_MAX_PLANES = PPM_NOALLOC_MAX_PLANES;
 constexpr int NOALLOC_THREADS = 256;
-constexpr int MAX_DEVICES = 64;
 
 // One row of 8 doubles per z-plane: the plane's 7 partial totals (+1 pad).
 // Shared by every call on a device; the last call's contents stay behind.
 static __device__ __align__(256) double g_plane_sums[NOALLOC_MAX_PLANES * 8];
-
-std::mutex g_mu;
-double *g_scratch[MAX_DEVICES] = {nullptr};
 
 // The nine state pointers, passed by value as a kernel argument.
 struct StatePtrs {
@@ -79,35 +74,30 @@ __global__ void total_kernel(const double *sums, int nz, double dV, double *out)
     }
 }
 
-// Device address of the static array for the current device, looked up once
-// per device (the first call on each device does this set-up).
+// Device address of the static array in the current device's context.  It
+// is looked up on every call (the lookup allocates nothing and queues no
+// work), so a device reset or a new context on the same ordinal never leaves
+// a stale address behind.
 int scratch_for_current_device(double **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_plane_sums);
     if (e != cudaSuccess) {
         char msg[256];
-        snprintf(msg, sizeof(msg), "ppm_totals_noalloc: cudaGetDevice: %s", cudaGetErrorString(e));
+        snprintf(msg, sizeof(msg), "ppm_totals_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
         ppm::set_global_error(msg);
         return PPM_ECUDA;
     }
-    if (dev < 0 || dev >= MAX_DEVICES) {
-        ppm::set_global_error("ppm_totals_noalloc: device ordinal beyond 63");
-        return PPM_EINVAL;
-    }
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_plane_sums);
-        if (e != cudaSuccess) {
-            char msg[256];
-            snprintf(msg, sizeof(msg), "ppm_totals_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-            ppm::set_global_error(msg);
-            return PPM_ECUDA;
-        }
-        g_scratch[dev] = static_cast<double *>(p);
-    }
-    *out = g_scratch[dev];
+    *out = static_cast<double *>(p);
     return PPM_OK;
+}
+
+int launch_failed(const char *which) {
+    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) return PPM_OK;
+    char msg[256];
+    snprintf(msg, sizeof(msg), "ppm_totals_noalloc: launch of %s: %s", which, cudaGetErrorString(e));
+    ppm::set_global_error(msg);
+    return PPM_ECUDA;
 }
 
 }  // namespace
@@ -134,6 +124,18 @@ extern "C" int ppm_totals_noalloc(const double *const *q_dev, int nx, int ny, in
         ppm::set_global_error(msg);
         return PPM_EINVAL;
     }
+    {
+        // an error left behind by earlier, unrelated work is reported as such
+        // and not cleared, so that its owner can still see it
+        const cudaError_t pe = cudaPeekAtLastError();
+        if (pe != cudaSuccess) {
+            char msg[256];
+            snprintf(msg, sizeof(msg), "ppm_totals_noalloc: an earlier CUDA error is pending: %s",
+                     cudaGetErrorString(pe));
+            ppm::set_global_error(msg);
+            return PPM_ECUDA;
+        }
+    }
     double *scratch = nullptr;
     int rc = scratch_for_current_device(&scratch);
     if (rc != PPM_OK) return rc;
@@ -142,13 +144,8 @@ extern "C" int ppm_totals_noalloc(const double *const *q_dev, int nx, int ny, in
     cudaStream_t st = (cudaStream_t)stream;
     const long long plane = (long long)nx * ny;
     plane_sums_kernel<<<nz, NOALLOC_THREADS, 0, st>>>(S, plane, scratch);
+    if ((rc = launch_failed("plane_sums_kernel")) != PPM_OK) return rc;
     total_kernel<<<1, 32, 0, st>>>(scratch, nz, dx * dx * dx, totals_dev);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) {
-        char msg[256];
-        snprintf(msg, sizeof(msg), "ppm_totals_noalloc: launch: %s", cudaGetErrorString(e));
-        ppm::set_global_error(msg);
-        return PPM_ECUDA;
-    }
+    if ((rc = launch_failed("total_kernel")) != PPM_OK) return rc;
     return PPM_OK;
 }

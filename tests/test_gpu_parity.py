@@ -18,6 +18,7 @@ import torch
 import oracle
 import paper_1810_13416_gb300 as ppm
 import workloads
+from parity_f32 import assert_f32
 
 pytestmark = pytest.mark.gpu
 
@@ -59,13 +60,9 @@ def _assert_f64(qg, qo):
         assert _relinf(qg[v], qo[v]) <= TOL_F64, (v, _relinf(qg[v], qo[v]))
 
 
-def _assert_f32(qg, qo):
-    for v in (0, 4):
-        l1 = np.abs(qg[v] - qo[v]).sum() / np.abs(qo[v]).sum()
-        assert l1 <= TOL_F32_L1, (v, l1)
-    fv = np.abs(qg[5] - qo[5]).mean()
-    assert fv <= TOL_F32_FV, fv
-    assert qg[5].min() >= 0.0 and qg[5].max() <= 1.0
+def _assert_f32(qg, qo, tag=""):
+    # rho, E, the momenta, FV (mean and L-inf) and the first moments
+    assert_f32(qg, qo, tag)
 
 
 def test_periodic_box_fp64_20_steps():

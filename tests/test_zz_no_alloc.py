@@ -69,3 +69,25 @@ def test_noalloc_rejects_too_many_planes(lib):
     rc = lib.ppm_totals_noalloc(ptrs, 1, 1, 8193, 1.0, _dptr(out), None)
     assert rc == -1
     assert "8192" in lib.ppm_last_error(None).decode()
+
+
+def test_noalloc_last_scratch_row_and_sub_warp_planes(lib):
+    """nz equal to the scratch limit (its last row is used) and planes of 6
+    cells, smaller than a warp, so most lanes add zeros in the shuffle
+    reduction; checked against numpy sums of the same arrays times dx^3."""
+    nx, ny, nz, dx = 3, 2, 8192, 0.125
+    g = np.random.default_rng(7)
+    q = [g.uniform(0.5, 2.0, nx * ny * nz) for _ in range(9)]
+    q[5] = g.uniform(0.0, 1.0, nx * ny * nz)
+    dev = [torch.tensor(a, device="cuda") for a in q]
+    out = torch.zeros(7, dtype=torch.float64, device="cuda")
+    ptrs = (_DP * 9)(*[_dptr(t) for t in dev])
+    for _ in range(2):
+        out.fill_(-1.0)
+        rc = lib.ppm_totals_noalloc(ptrs, nx, ny, nz, dx, _dptr(out), None)
+        assert rc == 0, lib.ppm_last_error(None).decode()
+        torch.cuda.synchronize()
+        r = out.cpu().numpy()
+        ref = np.array([q[0].sum(), q[1].sum(), q[2].sum(), q[3].sum(), q[4].sum(),
+                        (q[0] * q[5]).sum(), q[5].sum()]) * dx ** 3
+        np.testing.assert_allclose(r, ref, rtol=1e-12, atol=0.0)
