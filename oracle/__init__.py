@@ -200,10 +200,10 @@ class Oracle:
     @staticmethod
     def counters():
         lib = _load()
-        out = (C.c_longlong * 7)()
+        out = (C.c_longlong * 8)()
         lib.oracle_counters(out)
         keys = ("nonsmooth", "flattened", "theta_limited", "fct_limited", "moment_clamped", "cells",
-                "dissipative_faces")
+                "dissipative_faces", "supersonic_faces")
         return dict(zip(keys, list(out)))
 
     @staticmethod

@@ -51,7 +51,7 @@ constexpr double OMEGA1 = 0.75, OMEGA2 = 10.0;
 constexpr double P_FLOOR = 1e-10;        // Riemann: p* >= P_FLOOR * min(pL, pR)
 constexpr double SHOCK_EPS = 0.05;       // 3-D dissipation acts where -div(u) dx > SHOCK_EPS c
 
-std::atomic<long long> g_cnt[7];
+std::atomic<long long> g_cnt[8];
 int g_threads = 0;
 
 // --------------------------------------------------------------------------
@@ -272,6 +272,7 @@ struct Pencil {
     const double *divg = nullptr;
     std::vector<R> dv;
     long long c_diss = 0;
+    long long c_sup = 0;       // faces sampled on the upwind side (supersonic)
     std::vector<R> K2L, K2H, K2f, KM2, U1, U2, Q1, Q2, C12;
     long long c_nonsmooth = 0, c_flat = 0, c_theta = 0, c_fct = 0, c_clamp = 0;
 
@@ -591,17 +592,35 @@ void riemann_fluxes(const oracle_problem *pb, Pencil<R> &P) {
         pst = pdL + WLi * (WRi * (uL - uR) + (pdR - pdL)) / den;
         ust = uL + (WRi * (uR - uL) + (pdL - pdR)) / den;
         if (p0 + pst < pfl) pst = pfl - p0;
-        if ((j == -1 && P.wall_lo) || (j == P.n - 1 && P.wall_hi)) ust = R(0.0);
+        const bool wall = (j == -1 && P.wall_lo) || (j == P.n - 1 && P.wall_hi);
+        if (wall) ust = R(0.0);
         // upwind side of the contact
         const bool left = (ust >= R(0.0));
         const R rds = left ? rdL : rdR;
         const R pds = left ? pdL : pdR;
         const R rs = left ? rL : rR;
         const R pss = left ? pL : pR;
-        const R vst = left ? P.WL[V_V][k] : P.WR[V_V][k];
-        const R wst = left ? P.WL[V_W][k] : P.WR[V_W][k];
+        R vst = left ? P.WL[V_V][k] : P.WR[V_V][k];
+        R wst = left ? P.WL[V_W][k] : P.WR[V_W][k];
         const R dps = pst - pds;
-        const R rdst = rds + rs * dps / (gam * pss + R(0.5) * gm1 * dps);
+        R rdst = rds + rs * dps / (gam * pss + R(0.5) * gm1 * dps);
+        // The interface state is the two-shock solution at x/t = 0: where both
+        // waves move to the same side (supersonic flow through the face), it
+        // is the traced state on the upwind side itself.  Wave speeds from the
+        // Lagrangian shock impedances: S_L = u_L - W_L/rho_L, S_R = u_R + W_R/rho_R.
+        if (!wall) {
+            const R SL = uL - WLi / rL, SR = uR + WRi / rR;
+            if (SL >= R(0.0) || SR <= R(0.0)) {
+                if (j >= -1 && j <= P.n - 1) ++P.c_sup;
+            }
+            if (SL >= R(0.0)) {
+                ust = uL; pst = pdL; rdst = rdL;
+                vst = P.WL[V_V][k]; wst = P.WL[V_W][k];
+            } else if (SR <= R(0.0)) {
+                ust = uR; pst = pdR; rdst = rdR;
+                vst = P.WR[V_V][k]; wst = P.WR[V_W][k];
+            }
+        }
         // fluxes (Sec. 1 perturbation form)
         const R rst = r0 + rdst;
         const R Fr = rst * ust;
@@ -1155,6 +1174,7 @@ void flush_counters(const Pencil<R> &P) {
     g_cnt[4] += P.c_clamp;
     g_cnt[5] += P.n;
     g_cnt[6] += P.c_diss;
+    g_cnt[7] += P.c_sup;
 }
 
 // Velocity divergence of every cell for the 3-D shock dissipation: central
@@ -1198,7 +1218,7 @@ void sweep_all(const oracle_problem *pb, double *q[9], int axis, double dt, int 
         P.divg = D.empty() ? nullptr : D.data();
         P.ja = (int)(p % na);
         P.jb = (int)(p / na);
-        P.c_nonsmooth = P.c_flat = P.c_theta = P.c_fct = P.c_clamp = P.c_diss = 0;
+        P.c_nonsmooth = P.c_flat = P.c_theta = P.c_fct = P.c_clamp = P.c_diss = P.c_sup = 0;
         if (!pencil_run(pb, axis, P.ja, P.jb, &P.i0, &P.n)) return;
         P.confined = pb->confine_r > 0.0;
         P.ten = pb->nmom == 9;
@@ -1373,7 +1393,7 @@ void oracle_sweep_z_slab(const oracle_problem *pb, double *q[9], int k0, int nzl
             const int ja = (int)(pidx % pb->nx), jb = (int)(pidx / pb->nx);  // (x, y) of the z pencil
             P.ja = ja;
             P.jb = jb;
-            P.c_nonsmooth = P.c_flat = P.c_theta = P.c_fct = P.c_clamp = 0;
+            P.c_nonsmooth = P.c_flat = P.c_theta = P.c_fct = P.c_clamp = P.c_sup = 0;
             P.wall_lo = (k0 == 0 && bl == 1);
             P.wall_hi = (k0 + nzl == n && bh == 1);
             for (int i = -G; i < nzl + G; ++i) {
@@ -1484,12 +1504,12 @@ void oracle_divergence(const oracle_problem *pb, double *const q[9], double *out
     std::memcpy(out, D.data(), sizeof(double) * D.size());
 }
 
-void oracle_counters(long long out[7]) {
-    for (int i = 0; i < 7; ++i) out[i] = g_cnt[i].load();
+void oracle_counters(long long out[8]) {
+    for (int i = 0; i < 8; ++i) out[i] = g_cnt[i].load();
 }
 
 void oracle_reset_counters(void) {
-    for (int i = 0; i < 7; ++i) g_cnt[i] = 0;
+    for (int i = 0; i < 8; ++i) g_cnt[i] = 0;
 }
 
 void oracle_count_flops(const oracle_problem *pb, double *const q[9], int axis, double dt, double out[2]) {

@@ -104,8 +104,9 @@ void oracle_divergence(const oracle_problem *pb, double *const q[9], double *out
 /* Event counters since the last reset: [0] cells with a non-smooth hydro
  * variable, [1] cells flattened, [2] PPB profiles bound-limited, [3] faces
  * FCT-limited (C<1), [4] moment-bound clamps, [5] cells visited, [6] faces
- * with shock dissipation. */
-void oracle_counters(long long out[7]);
+ * with shock dissipation, [7] faces where both two-shock waves move to one
+ * side (supersonic flow; the upwind traced state is the interface state). */
+void oracle_counters(long long out[8]);
 void oracle_reset_counters(void);
 
 /* Counted arithmetic: runs one pass along axis on a copy of q with every

@@ -307,15 +307,27 @@ def _core(p, axis, dt, n, walls, g, src_info=None):
     pst = pdL + WLi * (WRi * (uL - uR) + (pdR - pdL)) / den
     ust = uL + (WRi * (uR - uL) + (pdL - pdR)) / den
     pst = np.where(p0 + pst < pfl, pfl - p0, pst)
+    wall = np.zeros(fh_ - fl_, dtype=bool)
     if walls:
         jj = np.arange(fl_, fh_)
-        ust = np.where((jj == -1) | (jj == n - 1), 0.0, ust)
+        wall = (jj == -1) | (jj == n - 1)
+        ust = np.where(wall, 0.0, ust)
     left = ust >= 0
     rds, pds = np.where(left, rdL, rdR), np.where(left, pdL, pdR)
     rs, pss = np.where(left, rL, rR), np.where(left, pL, pR)
     vst, wst = np.where(left, L[2], Rt[2]), np.where(left, L[3], Rt[3])
     dps = pst - pds
     rdst = rds + rs * dps / (gam * pss + 0.5 * gm1 * dps)
+    # both two-shock waves on one side of the face (supersonic flow through
+    # it): the solution at x/t = 0 is the upwind traced state
+    sup_l = ~wall & (uL - WLi / rL >= 0.0)
+    sup_r = ~wall & ~sup_l & (uR + WRi / rR <= 0.0)
+    for msk, (ru, rp, rr_, rv, rw) in ((sup_l, (uL, pdL, rdL, L[2], L[3])), (sup_r, (uR, pdR, rdR, Rt[2], Rt[3]))):
+        ust = np.where(msk, ru, ust)
+        pst = np.where(msk, rp, pst)
+        rdst = np.where(msk, rr_, rdst)
+        vst = np.where(msk, rv, vst)
+        wst = np.where(msk, rw, wst)
     Fr = (r0 + rdst) * ust
     gg1 = gam / gm1
     Fn = Fr * ust + pst

@@ -16,7 +16,13 @@ at the wrong position, a stencil shifted by one, an axis permutation) shows.
 
 Inputs are made to reach every branch: random volume fractions with cells
 pinned at exactly 0 and 1 (FCT and theta limiting active), a Sod tube
-(flattening and constraints active), plane gravity with reflecting walls.
+(flattening and constraints active), plane gravity with reflecting walls,
+random flows at Mach ~3 (faces whose two-shock waves both move one way, so
+the upwind traced state is the interface state).  The FCT limiter is not
+required to fire: with the interface state sampled at x/t = 0 it fired in
+none of the finite states tried (random flows at Mach 0.1-3, density
+contrasts up to 100, contacts advected at uniform velocity); it is pinned by
+the bounds pin and by the GPU parity of the same expressions.
 """
 import copy
 
@@ -46,15 +52,15 @@ def _rough_fv(q, seed):
     return q
 
 
-def _rough_flow(p, q, seed, amp, pres):
-    """Cell-to-cell random density (x 0.7..1.4), velocity (|u_d| <= amp) and
+def _rough_flow(p, q, seed, amp, pres, rho_range=(0.7, 1.4)):
+    """Cell-to-cell random density (x rho_range), velocity (|u_d| <= amp) and
     pressure (pres x 0.5..2): discontinuous everywhere, so that every cell
     takes the constrained branches and strong compressions reach the FCT
     limiter.  Only single passes are taken from it (a second pass may meet a
     negative traced pressure, which PPM does not exclude)."""
     rng = np.random.default_rng(seed)
     q = [a.copy() for a in q]
-    rho = q[0] * rng.uniform(0.7, 1.4, q[0].shape)
+    rho = q[0] * rng.uniform(rho_range[0], rho_range[1], q[0].shape)
     u = [amp * rng.uniform(-1.0, 1.0, rho.shape) for _ in range(3)]
     pr = pres * rng.uniform(0.5, 2.0, rho.shape)
     q[0] = rho
@@ -100,7 +106,7 @@ def _cases():
         ("sod_evolved", sod, lambda: _evolved(sod, workloads.build(sod), 4), 2,
          ("flattened", "nonsmooth", "theta_limited")),
         ("box_rough", box, lambda: _rough_flow(box, workloads.build(box), 1, 1.0, 0.05), 1,
-         ("fct_limited", "flattened", "nonsmooth")),
+         ("flattened", "nonsmooth", "supersonic_faces")),
         ("strat_rough", strat, lambda: _rough_flow(strat, workloads.build(strat), 2, 0.7, 0.1), 1,
          ("flattened", "nonsmooth")),
     ]
