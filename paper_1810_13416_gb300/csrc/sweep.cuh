@@ -895,16 +895,30 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
             pst = pdL + WLi * (WRi * (uL - uR) + (pdR - pdL)) / den;
             ust = uL + (WRi * (uR - uL) + (pdL - pdR)) / den;
             if (p0 + pst < pfl) pst = pfl - p0;
-            if ((j == -1 && bcl == 1) || (j == n - 1 && bch == 1)) ust = (R)0;
+            const bool wall = (j == -1 && bcl == 1) || (j == n - 1 && bch == 1);
+            if (wall) ust = (R)0;
             const bool left = (ust >= (R)0);
             const R rds = left ? rdL : rdR;
             const R pds = left ? pdL : pdR;
             const R rs = left ? rL : rR;
             const R pss = left ? pL : pR;
-            const R vst = left ? WLp[2] : WRc[2];
-            const R wst = left ? WLp[3] : WRc[3];
+            R vst = left ? WLp[2] : WRc[2];
+            R wst = left ? WLp[3] : WRc[3];
             const R dps = pst - pds;
-            const R rdst = rds + rs * dps / (gam * pss + (R)0.5 * gm1 * dps);
+            R rdst = rds + rs * dps / (gam * pss + (R)0.5 * gm1 * dps);
+            {
+                // the interface state is the two-shock solution at x/t = 0:
+                // where both waves move to one side (supersonic flow through
+                // the face) it is the upwind traced state itself; wave speeds
+                // from the Lagrangian impedances (selects: no divergence)
+                const bool supL = !wall && (uL - WLi / rL >= (R)0);
+                const bool supR = !wall && !supL && (uR + WRi / rR <= (R)0);
+                ust = supL ? uL : (supR ? uR : ust);
+                pst = supL ? pdL : (supR ? pdR : pst);
+                rdst = supL ? rdL : (supR ? rdR : rdst);
+                vst = supL ? WLp[2] : (supR ? WRc[2] : vst);
+                wst = supL ? WLp[3] : (supR ? WRc[3] : wst);
+            }
             const R h0 = gg1 * p0;
             const R kin = (R)0.5 * (ust * ust + (vst * vst + wst * wst));
             if constexpr (F32) {
