@@ -284,6 +284,8 @@ def run_ours(args):
 
     # ---------------- FP32 deviation form: the headline -----------------
     ctx = ppm.Context.from_problem(p, precision=ppm.FP32_DEVIATION, stream=stream, device=local)
+    if args.design == "tile":
+        ctx.set_pass_design(ppm.PASS_TILE)
     _upload(ctx, p, torch)
     ctx.cfl_dt(p.cfl, fetch=False)
     # evolve the state first, so that the timed steps see a realistic mix of
@@ -534,6 +536,8 @@ def main():
     ap.add_argument("--no-shock", action="store_true")
     ap.add_argument("--shock-steps", type=int, default=3)
     ap.add_argument("--ens-boxes", type=int, default=24)
+    ap.add_argument("--design", default="march", choices=["march", "tile"],
+                    help="form of the FP32 pass kernel for the headline")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")

@@ -44,7 +44,7 @@ typedef enum {
     PPM_ECUDA = -3,      /* CUDA runtime error: the context must be destroyed */
     PPM_ENONPHYS = -4,   /* a pass produced rho<=0, p<=0 or a non-finite value */
     PPM_ECFL = -5,       /* requested time step exceeds the CFL limit (cfl > 1) */
-    PPM_ETIMEOUT = -6,   /* a bounded device wait gave up */
+    PPM_ETIMEOUT = -6,   /* a bounded device wait gave up (tile pass: a TMA copy never completed) */
     PPM_ESTATE = -7      /* call out of order (e.g. step with device dt before any cfl_dt) */
 } ppm_status;
 
@@ -172,6 +172,23 @@ int ppm_sweep(ppm_ctx *ctx, int axis, double dt, int sources);
  * ppm_sweep applies it with sources bit 1.  Host state only (no device
  * work, no wait); EINVAL if not finite. */
 int ppm_set_rotation(ppm_ctx *ctx, double domega);
+
+/* Form of the FP32 pass kernel (the arithmetic of a pass, Sec. 1 and Sec. 4,
+ * is the same in both; results agree with the FP64 oracle at the FP32
+ * tolerances, not bit for bit with each other):
+ *   PPM_PASS_MARCH: one thread per pencil marching along it with a five-cell
+ *     register window (every context; the FP64 form always uses it);
+ *   PPM_PASS_TILE: 256 threads per 8 pencils, each taking one cell of a
+ *     32-cell chunk through every stage, stages joined by shared-memory
+ *     rings, chunks moved by TMA in both directions.  Needs the FP32
+ *     four-value form without a confining sphere or shock dissipation, and
+ *     nx % 4 == 0 (else EINVAL).
+ * The choice holds for later steps and passes of the context (the step
+ * graph is captured again). */
+enum { PPM_PASS_MARCH = 0, PPM_PASS_TILE = 1 };
+int ppm_set_pass_design(ppm_ctx *ctx, int design);
+/* The current design and whether PPM_PASS_TILE applies (either may be NULL). */
+int ppm_get_pass_design(const ppm_ctx *ctx, int *design, int *tile_available);
 
 /* Reductions of the current state to FP64 accuracy:
  * totals[7] = (M, Px, Py, Pz, E, sum rho*FV, sum FV), each times dx^3 (FP32

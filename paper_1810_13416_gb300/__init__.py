@@ -31,6 +31,8 @@ __all__ = ["Context", "Ensemble", "PpmError", "build", "library_path", "FP64_PLA
 
 FP64_PLAIN = 0
 FP32_DEVIATION = 1
+PASS_MARCH = 0      # one thread per pencil, register window
+PASS_TILE = 1       # cell-parallel tiles of 8 pencils x 32 cells, TMA staging
 BC_PERIODIC = 0
 BC_REFLECT = 1
 GRAV_NONE = 0
@@ -98,6 +100,8 @@ def _load():
     lib.ppm_step.argtypes = [P, C.c_double]
     lib.ppm_sweep.argtypes = [P, C.c_int, C.c_double, C.c_int]
     lib.ppm_set_rotation.argtypes = [P, C.c_double]
+    lib.ppm_set_pass_design.argtypes = [P, C.c_int]
+    lib.ppm_get_pass_design.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     lib.ppm_diagnostics.argtypes = [P, _DP, C.c_int, C.c_double, _DP, _DP]
     lib.ppm_sync.argtypes = [P]
     lib.ppm_launch_count.argtypes = [P]
@@ -283,6 +287,22 @@ class Context:
     def set_rotation(self, domega: float):
         """Rotation increment added by each following double step (0 ends the ramp)."""
         self._check(self.lib.ppm_set_rotation(self.h, float(domega)))
+
+    def set_pass_design(self, design: int):
+        """PASS_MARCH or PASS_TILE (FP32 four-value form, nx % 4 == 0)."""
+        self._check(self.lib.ppm_set_pass_design(self.h, int(design)))
+
+    @property
+    def pass_design(self) -> int:
+        d, a = C.c_int(), C.c_int()
+        self._check(self.lib.ppm_get_pass_design(self.h, C.byref(d), C.byref(a)))
+        return d.value
+
+    @property
+    def tile_available(self) -> bool:
+        d, a = C.c_int(), C.c_int()
+        self._check(self.lib.ppm_get_pass_design(self.h, C.byref(d), C.byref(a)))
+        return bool(a.value)
 
     def diagnostics(self, nbins: int = 0, rmax: float = 1.0):
         tot = np.zeros(7)

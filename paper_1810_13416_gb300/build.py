@@ -15,14 +15,15 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libppm.so")
 BUILD = os.path.join(HERE, "_build")
-UNITS = ["sweep_f32", "sweep_f64", "sweep_ens", "ppm_api", "noalloc"]
+UNITS = ["sweep_f32", "sweep_f64", "sweep_ens", "tile_f32", "ppm_api", "noalloc"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 # per-unit flags: the FP32 passes use approximate division and square root
 # and flush denormals to zero (values below 1.2e-38 carry no information in
 # these deviations and fractions; measured 3% faster passes)
 UNIT_FLAGS = {"sweep_f32": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
-              "sweep_ens": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]}
+              "sweep_ens": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
+              "tile_f32": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]}
 _lock = threading.Lock()
 
 

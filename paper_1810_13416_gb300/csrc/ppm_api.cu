@@ -1,5 +1,6 @@
 // ppm_api.cu -- the C ABI of libppm.so (include/ppm.h): context, state
 // conversion, CFL and diagnostic reductions, and the CUDA-graph double step.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -22,6 +23,9 @@ cudaError_t prepare_sweep_ensemble();
 int ensemble_blocks_per_sm(int f32, int vec, int nb);
 void launch_sweep_ensemble(int f32, int vec, int nb, const void *args, const WorkItem *work, int nwork,
                            int *counter, int persistent, int grid, cudaStream_t st);
+cudaError_t prepare_tile_f32();
+int tile_encode_map(CUtensorMap *m, void *state, int nx, int ny, int nz, int axis);
+void launch_tile_f32(const SweepArgs<float> &a, const CUtensorMap *m, cudaStream_t st);
 }  // namespace ppm
 
 using namespace ppm;
@@ -94,6 +98,9 @@ struct ppm_ctx {
     cudaGraphNode_t dt_node;   // first node of the step graph (dt_kernel)
     bool have_speed;           // a valid device max speed exists for dt <= 0
     long long launches;
+    int design;                // PPM_PASS_MARCH or PPM_PASS_TILE
+    bool tile_ok;              // the tile form applies to this context
+    CUtensorMap tmap[3];       // its TMA maps of the state, one box shape per pass axis
     std::string err;
 };
 
@@ -186,7 +193,10 @@ int launch_sweep(ppm_ctx *c, int axis, int sources, int cfl) {
         a.sources = sources;
         a.cfl = cfl;
         dim3 grid((a.nlane + SWEEP_BLOCK - 1) / SWEEP_BLOCK, a.nblk);
-        launch_sweep_f32(a, grid, block, c->stream);
+        if (c->design == PPM_PASS_TILE && c->tile_ok)
+            launch_tile_f32(a, &c->tmap[axis], c->stream);
+        else
+            launch_sweep_f32(a, grid, block, c->stream);
     } else {
         SweepArgs<double> a = make_args<double>(c, axis);
         a.sources = sources;
@@ -702,6 +712,10 @@ int check_flags(ppm_ctx *c) {
     int fl = 0;
     CK(c, cudaMemcpyAsync(&fl, &c->ds_dev->flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
+    if (fl & FLAG_TIMEOUT) {
+        CK(c, cudaMemsetAsync(&c->ds_dev->flags, 0, sizeof(int), c->stream));
+        return fail(c, PPM_ETIMEOUT, "a bounded device wait gave up (a TMA copy did not complete)");
+    }
     if (fl & FLAG_NONPHYS) {
         CK(c, cudaMemsetAsync(&c->ds_dev->flags, 0, sizeof(int), c->stream));
         return fail(c, PPM_ENONPHYS, "a pass produced rho<=0, p<=0 or a non-finite value");
@@ -1044,7 +1058,42 @@ int ppm_create(ppm_ctx **out, int nx, int ny, int nz, double gamma, const int bc
         fail(c, PPM_ECUDA, "initialising device buffers failed");
         return bail(PPM_ECUDA);
     }
+    // the tile form of the pass: FP32 four-value state, no confining sphere
+    // or shock dissipation, and rows of whole 16-byte groups for TMA
+    c->design = PPM_PASS_MARCH;
+    c->tile_ok = false;
+    if (c->prec == PPM_FP32_DEVIATION && c->nmom == 3 && !(c->confine_r > 0.0) && !(c->shock_k > 0.0) &&
+        nx % 4 == 0) {
+        bool ok = prepare_tile_f32() == cudaSuccess;
+        for (int a = 0; a < 3 && ok; ++a) ok = tile_encode_map(&c->tmap[a], c->state, nx, ny, nz, a) == 0;
+        if (!ok) cudaGetLastError();
+        c->tile_ok = ok;
+    }
     *out = c;
+    return PPM_OK;
+}
+
+int ppm_set_pass_design(ppm_ctx *c, int design) {
+    if (!c) return PPM_EINVAL;
+    if (design != PPM_PASS_MARCH && design != PPM_PASS_TILE) return fail(c, PPM_EINVAL, "unknown pass design %d", design);
+    if (design == PPM_PASS_TILE && !c->tile_ok)
+        return fail(c, PPM_EINVAL, "the tile pass needs the FP32 four-value form, no confining sphere or shock "
+                                   "dissipation, and nx %% 4 == 0");
+    if (design != c->design) {
+        // the step graph holds the pass kernels: capture it again
+        if (c->gexec) cudaGraphExecDestroy(c->gexec);
+        if (c->graph) cudaGraphDestroy(c->graph);
+        c->gexec = nullptr;
+        c->graph = nullptr;
+        c->design = design;
+    }
+    return PPM_OK;
+}
+
+int ppm_get_pass_design(const ppm_ctx *c, int *design, int *tile_available) {
+    if (!c) return PPM_EINVAL;
+    if (design) *design = c->design;
+    if (tile_available) *tile_available = c->tile_ok ? 1 : 0;
     return PPM_OK;
 }
 

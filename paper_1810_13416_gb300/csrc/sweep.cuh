@@ -45,6 +45,7 @@ constexpr int G = 4;  // ghost width (Sec. 4: the difference stencil reaches 4 c
 
 // status flags (device int, OR-ed)
 constexpr int FLAG_NONPHYS = 1;
+constexpr int FLAG_TIMEOUT = 2;   // a bounded device wait gave up
 
 template <typename R>
 struct SweepArgs {

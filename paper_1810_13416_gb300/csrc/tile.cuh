@@ -51,7 +51,6 @@ constexpr int CHUNK_FLOATS = 9 * S * P;          // one chunk of the 9 values
 constexpr unsigned CHUNK_BYTES = CHUNK_FLOATS * 4u;
 constexpr int NX1 = 8, NX2 = 12, NX3 = 16, NX4 = 3;
 constexpr long long WAIT_LIMIT = 1ll << 26;      // bounded mbarrier wait (iterations)
-constexpr int FLAG_TIMEOUT = 2;
 
 // Shared memory of one block (offsets from a 1024-byte aligned base).
 struct Smem {
@@ -190,7 +189,10 @@ __global__ void __launch_bounds__(NT, 2) tile_pass_kernel(const SweepArgs<float>
 
     // raw (stored) value v of cell c of this thread's pencil
     auto in_idx = [&](int c) {
-        const int k = (c - 4 + S) / S - 1;          // chunk of cell c (c >= -8)
+        // cells below the first ghost only feed values that no stored cell
+        // uses (the start of the pipeline); they read ghost -4 instead
+        c = max(c, -4);
+        const int k = (c - 4 + S) / S - 1;          // chunk of cell c (c >= -4)
         const int b = (k + 1) % NIN;
         return b * CHUNK_FLOATS + chunk_pos<XP>(p, c - 4 - k * S);
     };
@@ -251,5 +253,546 @@ __global__ void __launch_bounds__(NT, 2) tile_pass_kernel(const SweepArgs<float>
 
     float smax_local = 0.0f;
     bool bad = false;
+    int kstop = klast + 1;                          // step at which a wait gave up
+
+    for (int k = -1; k <= klast; ++k) {
+        const int cA = k * S + 4 + l;               // stage A cell of this thread
+        // ---- producer: the next chunk into the buffer of chunk k-2 --------
+        if (tid == 0 && k + 1 <= klast) {
+            const int b = (k + 2) % NIN;
+            fence_async_smem();   // reads of this buffer (chunk k-2) by the block came first
+            int k0, k1, k2;
+            coords((k + 1) * S + 4, k0, k1, k2);
+            mbar_expect_tx(&sm.bar[b], CHUNK_BYTES);
+            tma_load4(&sm.in[b][0], &tmap, k0, k1, k2, 0, &sm.bar[b]);
+        }
+        // ---- wait for chunk k (its buffer's use (k+1)/3, parity & 1) -------
+        {
+            const int b = (k + 1) % NIN;
+            if (!mbar_wait(&sm.bar[b], (unsigned)(((k + 1) / NIN) & 1))) sm.abort = 1;
+        }
+        __syncthreads();
+        if (sm.abort) {
+            kstop = k;
+            break;
+        }
+        // ---- ghost cells of this chunk (rows [k S + 4, k S + S + 4)) -------
+        {
+            const int c0 = k * S + 4;
+            // low side (chunk -1 only): periodic from the cells read at the
+            // start; walls mirror cells 0..3 with the normal components flipped
+            if (k == -1 && tid < 4 * P) {
+                const int gp = tid % P, gc = tid / P;
+                const int c = -4 + gc;
+                const int ri = (c - c0);
+                float *dst = &sm.in[0][0];
+                if (bcl == 0) {
+                    for (int v = 0; v < 9; ++v) dst[v * (S * P) + chunk_pos<XP>(gp, ri)] = gpre[v];
+                } else {
+                    const int src = chunk_pos<XP>(gp, (-1 - c) - c0);
+                    for (int v = 0; v < 9; ++v) {
+                        const float x = dst[v * (S * P) + src];
+                        dst[v * (S * P) + chunk_pos<XP>(gp, ri)] = (v == pn || v == on_) ? -x : x;
+                    }
+                }
+            }
+            // high side: cells n..n+3 if they fall in this chunk
+            if (tid < 4 * P) {
+                const int gp = tid % P, gc = tid / P;
+                const int c = n + gc;
+                if (c >= c0 && c < c0 + S) {
+                    float *dst = &sm.in[0][0] + ((k + 1) % NIN) * CHUNK_FLOATS;
+                    const int di = chunk_pos<XP>(gp, c - c0);
+                    if (bch == 0) {
+                        for (int v = 0; v < 9; ++v) dst[v * (S * P) + di] = sm.stash[v][gc * P + gp];
+                    } else {
+                        const int cs = 2 * n - 1 - c;   // mirror cell (n-1 .. n-4)
+                        const int kc = (cs - 4 + S) / S - 1;
+                        const float *src = &sm.in[0][0] + ((kc + 1) % NIN) * CHUNK_FLOATS;
+                        const int si = chunk_pos<XP>(gp, cs - 4 - kc * S);
+                        for (int v = 0; v < 9; ++v) {
+                            const float x = src[v * (S * P) + si];
+                            dst[v * (S * P) + di] = (v == pn || v == on_) ? -x : x;
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (k == -1 && bch == 0 && tid < 4 * P) {
+            // cells 0..3 of periodic pencils, before they are overwritten
+            const int gp = tid % P, gc = tid / P;
+            for (int v = 0; v < 9; ++v) sm.stash[v][gc * P + gp] = raw(v, gc);
+        }
+
+        // ================= A: primitives of cell cA ==========================
+        {
+            const int c = cA;
+            bool flip = false;
+            const int m = (c >= -4 && c < n + 4) ? map_cell(c, n, bcl, bch, flip) : 0;
+            const float4 bb = base_at_x(xcell32(m));
+            const float sg = flip ? -1.0f : 1.0f;
+            const float rd = raw(0, c);
+            const float mn = raw(pn, c), m1 = raw(p1, c), m2 = raw(p2, c);
+            const float ed = raw(4, c);
+            const float rho = bb.x + rd;
+            const float rinv = 1.0f / rho;
+            const float u = mn * rinv, v = m1 * rinv, w = m2 * rinv;
+            const float ke = 0.5f * (mn * u + (m1 * v + m2 * w));
+            const float pd = gm1 * (ed - ke);
+            const int sl = slot_of(c);
+            X(sm.x1, 0, sl) = rd;
+            X(sm.x1, 1, sl) = u;
+            X(sm.x1, 2, sl) = v;
+            X(sm.x1, 3, sl) = w;
+            X(sm.x1, 4, sl) = pd;
+            X(sm.x1, 5, sl) = bb.x;
+            X(sm.x1, 6, sl) = bb.y;
+            X(sm.x1, 7, sl) = sg * bb.z;
+        }
+        __syncthreads();
+
+        // ================= B: cell cA-2 ======================================
+        {
+            const int c = cA - 2;
+            const int s0 = slot_of(c);
+            float wrd[5], wu[5], wv[5], ww[5], wpd[5];
+#pragma unroll
+            for (int d = 0; d < 5; ++d) {
+                const int sl = slot_add(s0, d - 2);
+                wrd[d] = X(sm.x1, 0, sl);
+                wu[d] = X(sm.x1, 1, sl);
+                wv[d] = X(sm.x1, 2, sl);
+                ww[d] = X(sm.x1, 3, sl);
+                wpd[d] = X(sm.x1, 4, sl);
+            }
+            const int sm1 = slot_add(s0, -1), sp1 = slot_add(s0, 1);
+            const float r0c = X(sm.x1, 5, s0), p0c = X(sm.x1, 6, s0), gc = X(sm.x1, 7, s0);
+            const float p0m = X(sm.x1, 6, sm1), p0p = X(sm.x1, 6, sp1);
+            // interface values of faces c-1/2 and c+1/2 (a2)
+            float afp[5], afn[5];
+            afp[0] = iface(wrd[0], wrd[1], wrd[2], wrd[3]);
+            afp[1] = iface(wu[0], wu[1], wu[2], wu[3]);
+            afp[2] = iface(wv[0], wv[1], wv[2], wv[3]);
+            afp[3] = iface(ww[0], ww[1], ww[2], ww[3]);
+            afp[4] = iface(wpd[0], wpd[1], wpd[2], wpd[3]);
+            afn[0] = iface(wrd[1], wrd[2], wrd[3], wrd[4]);
+            afn[1] = iface(wu[1], wu[2], wu[3], wu[4]);
+            afn[2] = iface(wv[1], wv[2], wv[3], wv[4]);
+            afn[3] = iface(ww[1], ww[2], ww[3], ww[4]);
+            afn[4] = iface(wpd[1], wpd[2], wpd[3], wpd[4]);
+            float WLn[5], WRc[5];
+            const float rho2 = r0c + wrd[2];
+            const float p2 = p0c + wpd[2];
+            const float c2 = gam * p2 / rho2;
+            const float cs = rsq(c2);
+            // flattening coefficient (a3)
+            float f = 0.0f;
+            {
+                const float dp1 = wpd[3] - wpd[1];
+                const float dp2 = wpd[4] - wpd[0];
+                const float pmin = rmin(p0p + wpd[3], p0m + wpd[1]);
+                if (rabs(dp1) > 0.33f * pmin && wu[1] - wu[3] > 0.0f) {
+                    const float r = (dp2 != 0.0f) ? dp1 / dp2 : 1.0f;
+                    f = rclamp(10.0f * (r - 0.75f), 0.0f, 1.0f);
+                }
+            }
+            // parabolas of the five variables (a3, a4)
+            float aL[5], aR[5], a6[5];
+            {
+                const float q0 = smooth5(wrd[0], wrd[1], wrd[2], wrd[3], wrd[4], rho2);
+                parabola(wrd[1], wrd[2], wrd[3], afp[0], afn[0], f, q0, aL[0], aR[0], a6[0]);
+                const float q1 = smooth5(wu[0], wu[1], wu[2], wu[3], wu[4], cs);
+                parabola(wu[1], wu[2], wu[3], afp[1], afn[1], f, q1, aL[1], aR[1], a6[1]);
+                const float q2 = smooth5(wv[0], wv[1], wv[2], wv[3], wv[4], cs);
+                parabola(wv[1], wv[2], wv[3], afp[2], afn[2], f, q2, aL[2], aR[2], a6[2]);
+                const float q3 = smooth5(ww[0], ww[1], ww[2], ww[3], ww[4], cs);
+                parabola(ww[1], ww[2], ww[3], afp[3], afn[3], f, q3, aL[3], aR[3], a6[3]);
+                const float q4 = smooth5(wpd[0], wpd[1], wpd[2], wpd[3], wpd[4], p2);
+                parabola(wpd[1], wpd[2], wpd[3], afp[4], afn[4], f, q4, aL[4], aR[4], a6[4]);
+            }
+            // characteristic tracing (waves u-c, u, u+c) + buoyancy (a5)
+            const float uc = wu[2];
+            const float C = rho2 * cs;
+            const float lm = uc - cs, l0 = uc, lp = uc + cs;
+            const float hg = hdt * ((wrd[2] / rho2) * gc);
+            {   // right edge -> left state of face c+1/2
+                const float sp = rmax(lp, 0.0f) * dtdx;
+                float st[5];
+#pragma unroll
+                for (int q = 0; q < 5; ++q) st[q] = fR(aL[q], aR[q], a6[q], sp);
+                const float rr = st[0], ru = st[1], rv = st[2], rw = st[3], rp = st[4];
+                if (l0 > 0.0f) {
+                    const float sq = l0 * dtdx;
+                    const float dr = rr - fR(aL[0], aR[0], a6[0], sq);
+                    const float dp = rp - fR(aL[4], aR[4], a6[4], sq);
+                    st[0] = st[0] - (dr - dp / c2);
+                    st[2] = st[2] - (rv - fR(aL[2], aR[2], a6[2], sq));
+                    st[3] = st[3] - (rw - fR(aL[3], aR[3], a6[3], sq));
+                }
+                if (lm > 0.0f) {
+                    const float sq = lm * dtdx;
+                    const float du = ru - fR(aL[1], aR[1], a6[1], sq);
+                    const float dp = rp - fR(aL[4], aR[4], a6[4], sq);
+                    const float Aa = 0.5f * (dp - C * du);
+                    st[0] = st[0] - Aa / c2;
+                    st[1] = st[1] + Aa / C;
+                    st[4] = st[4] - Aa;
+                }
+                st[1] = st[1] + hg;
+#pragma unroll
+                for (int q = 0; q < 5; ++q) WLn[q] = st[q];
+            }
+            {   // left edge -> right state of face c-1/2
+                const float sq0 = rmax(-lm, 0.0f) * dtdx;
+                float st[5];
+#pragma unroll
+                for (int q = 0; q < 5; ++q) st[q] = fL(aL[q], aR[q], a6[q], sq0);
+                const float rr = st[0], ru = st[1], rv = st[2], rw = st[3], rp = st[4];
+                if (l0 < 0.0f) {
+                    const float sq = -l0 * dtdx;
+                    const float dr = rr - fL(aL[0], aR[0], a6[0], sq);
+                    const float dp = rp - fL(aL[4], aR[4], a6[4], sq);
+                    st[0] = st[0] - (dr - dp / c2);
+                    st[2] = st[2] - (rv - fL(aL[2], aR[2], a6[2], sq));
+                    st[3] = st[3] - (rw - fL(aL[3], aR[3], a6[3], sq));
+                }
+                if (lp < 0.0f) {
+                    const float sq = -lp * dtdx;
+                    const float du = ru - fL(aL[1], aR[1], a6[1], sq);
+                    const float dp = rp - fL(aL[4], aR[4], a6[4], sq);
+                    const float Aa = 0.5f * (dp + C * du);
+                    st[0] = st[0] - Aa / c2;
+                    st[1] = st[1] - Aa / C;
+                    st[4] = st[4] - Aa;
+                }
+                st[1] = st[1] + hg;
+#pragma unroll
+                for (int q = 0; q < 5; ++q) WRc[q] = st[q];
+            }
+            // PPB profile of cell c: f = FV + m xi + a2 (xi^2 - 1/12), bound-limited (a9)
+            float me2, ae2;
+            {
+                const float fs = raw(5, c);
+                const float F = fv_unfold(fs), mm = raw(on_, c);
+                const float a2 = 0.25f * (raw(on_, c + 1) - raw(on_, c - 1));
+                const float ep = 0.5f * mm + a2 * (1.0f / 6.0f);
+                const float em = a2 * (1.0f / 6.0f) - 0.5f * mm;
+                float gmax = rmax(ep, em), gmin = rmin(ep, em);
+                const bool nz = (a2 != 0.0f);
+                const float xv = -mm / (2.0f * (nz ? a2 : 1.0f));
+                const float gv = mm * xv + a2 * (xv * xv - (1.0f / 12.0f));
+                const bool in = nz && (rabs(xv) < 0.5f);
+                gmax = in ? rmax(gmax, gv) : gmax;
+                gmin = in ? rmin(gmin, gv) : gmin;
+                float th = 1.0f;
+                const float omf = fv_complement(fs);
+                const bool hi = gmax > omf, lo = -gmin > F;
+                const float t1 = omf / (hi ? gmax : 1.0f), t2 = F / (lo ? -gmin : 1.0f);
+                th = hi ? rmin(th, t1) : th;
+                th = lo ? rmin(th, t2) : th;
+                me2 = th * mm;
+                ae2 = th * a2;
+            }
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                X(sm.x2, q, s0) = WLn[q];
+                X(sm.x2, 5 + q, s0) = WRc[q];
+            }
+            X(sm.x2, 10, s0) = me2;
+            X(sm.x2, 11, s0) = ae2;
+        }
+        __syncthreads();
+
+        // ================= C: face (cA-3)+1/2 ================================
+        {
+            const int j = cA - 3;                    // face j+1/2 between cells j and j+1
+            const int sj = slot_of(j), sr = slot_add(sj, 1);
+            float WLp[5], WRc[5];
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                WLp[q] = X(sm.x2, q, sj);            // left state: right edge of cell j
+                WRc[q] = X(sm.x2, 5 + q, sr);        // right state: left edge of cell j+1
+            }
+            const float4 bf = base_at_x(xface32(j));
+            const float r0 = bf.x, p0 = bf.y;
+            const float rdL = WLp[0], uL = WLp[1], pdL = WLp[4];
+            const float rdR = WRc[0], uR = WRc[1], pdR = WRc[4];
+            const float rL = r0 + rdL, pL = p0 + pdL;
+            const float rR = r0 + rdR, pR = p0 + pdR;
+            const float CL = rsq(gam * pL * rL), CR = rsq(gam * pR * rR);
+            const float pfl = 1e-10f * rmin(pL, pR);
+            float den = CL + CR;
+            float pst = pdL + CL * (CR * (uL - uR) + (pdR - pdL)) / den;
+            float ust = uL + (CR * (uR - uL) + (pdL - pdR)) / den;
+            if (p0 + pst < pfl) pst = pfl - p0;
+            const float WLi = CL * rsq(1.0f + kk * (pst - pdL) / pL);
+            const float WRi = CR * rsq(1.0f + kk * (pst - pdR) / pR);
+            den = WLi + WRi;
+            pst = pdL + WLi * (WRi * (uL - uR) + (pdR - pdL)) / den;
+            ust = uL + (WRi * (uR - uL) + (pdL - pdR)) / den;
+            if (p0 + pst < pfl) pst = pfl - p0;
+            const bool wall = (j == -1 && bcl == 1) || (j == n - 1 && bch == 1);
+            if (wall) ust = 0.0f;
+            const bool left = (ust >= 0.0f);
+            const float rds = left ? rdL : rdR;
+            const float pds = left ? pdL : pdR;
+            const float rs = left ? rL : rR;
+            const float pss = left ? pL : pR;
+            float vst = left ? WLp[2] : WRc[2];
+            float wst = left ? WLp[3] : WRc[3];
+            const float dps = pst - pds;
+            float rdst = rds + rs * dps / (gam * pss + 0.5f * gm1 * dps);
+            {
+                // the two-shock solution at x/t = 0: upwind traced state where
+                // both waves move to one side
+                const bool supL = !wall && (uL - WLi / rL >= 0.0f);
+                const bool supR = !wall && !supL && (uR + WRi / rR <= 0.0f);
+                ust = supL ? uL : (supR ? uR : ust);
+                pst = supL ? pdL : (supR ? pdR : pst);
+                rdst = supL ? rdL : (supR ? rdR : rdst);
+                vst = supL ? WLp[2] : (supR ? WRc[2] : vst);
+                wst = supL ? WLp[3] : (supR ? WRc[3] : wst);
+            }
+            const float h0 = gg1 * p0;
+            const float kin = 0.5f * (ust * ust + (vst * vst + wst * wst));
+            // mass and energy fluxes carry their base-state parts (rho0 u*,
+            // h0 u*) as exact hi + lo pairs (a7)
+            float Frc, Frlc, FEc, FElc;
+            {
+                float hi, e;
+                two_prod(r0, ust, hi, e);
+                Frc = hi;
+                Frlc = e + rdst * ust;
+            }
+            const float Fr = Frc + Frlc;
+            {
+                float hE, eE;
+                two_prod(ust, h0, hE, eE);
+                FEc = hE;
+                FElc = eE + (ust * (gg1 * pst) + kin * Fr);
+            }
+            const float Fnc = Fr * ust + pst;
+            const float Ft1c = Fr * vst;
+            const float Ft2c = Fr * wst;
+            // PPB transfers across the face: donor j (from the left) or j+1
+            float GLc, Ac, KLc, KHc, T1c, T2c;
+            {
+                const float sig = ust * dtdx;
+                const float phi = dtdx * Fr;
+                const bool fromleft = (sig >= 0.0f);
+                const float sabs = fromleft ? sig : -sig;
+                float M1 = 0.5f - 0.5f * sabs;
+                const float M2 = 0.25f - 0.5f * sabs + sabs * sabs * (1.0f / 3.0f);
+                float M3 = 0.125f - 0.375f * sabs + 0.5f * sabs * sabs - 0.25f * sabs * sabs * sabs;
+                if (!fromleft) {
+                    M1 = -M1;
+                    M3 = -M3;
+                }
+                const int dc = fromleft ? j : j + 1;
+                const int sd = fromleft ? sj : sr;
+                const float F = fv_unfold(raw(5, dc));
+                const float me = X(sm.x2, 10, sd);
+                const float ae = X(sm.x2, 11, sd);
+                const float ot1 = raw(o1_, dc), ot2 = raw(o2_, dc);
+                const float phibar = F + me * M1 + ae * (M2 - (1.0f / 12.0f));
+                const float psibar = F * M1 + me * M2 + ae * (M3 - M1 * (1.0f / 12.0f));
+                GLc = phi * F;
+                Ac = phi * phibar - GLc;
+                KLc = phi * F * M1;
+                KHc = phi * psibar;
+                T1c = phi * ot1;
+                T2c = phi * ot2;
+                X(sm.x3, 13, sj) = phi;
+                X(sm.x3, 14, sj) = phi * M1;
+                X(sm.x3, 15, sj) = sig;
+            }
+            X(sm.x3, 0, sj) = Frc;
+            X(sm.x3, 1, sj) = Frlc;
+            X(sm.x3, 2, sj) = Fnc;
+            X(sm.x3, 3, sj) = Ft1c;
+            X(sm.x3, 4, sj) = Ft2c;
+            X(sm.x3, 5, sj) = FEc;
+            X(sm.x3, 6, sj) = FElc;
+            X(sm.x3, 7, sj) = GLc;
+            X(sm.x3, 8, sj) = Ac;
+            X(sm.x3, 9, sj) = KLc;
+            X(sm.x3, 10, sj) = KHc;
+            X(sm.x3, 11, sj) = T1c;
+            X(sm.x3, 12, sj) = T2c;
+        }
+        if (tid == 0) bulk_wait_read_all();   // the last store has read its buffer
+        __syncthreads();
+
+        // ================= D: cell cA-3 ======================================
+        {
+            const int c = cA - 3;
+            const int sc = slot_of(c), sl = slot_add(sc, -1);
+            const float g = X(sm.x1, 7, sc), r0c = X(sm.x1, 5, sc), p0c = X(sm.x1, 6, sc);
+            const float rd3 = raw(0, c), mn3 = raw(pn, c), m13 = raw(p1, c), m23 = raw(p2, c), ed3 = raw(4, c);
+            const float Frc = X(sm.x3, 0, sc), Frlc = X(sm.x3, 1, sc), Frp = X(sm.x3, 0, sl), Frlp = X(sm.x3, 1, sl);
+            const float FEc = X(sm.x3, 5, sc), FElc = X(sm.x3, 6, sc), FEp = X(sm.x3, 5, sl), FElp = X(sm.x3, 6, sl);
+            float sE, eE;
+            two_sum(Frc, -Frp, sE, eE);
+            const float dFr = sE + (eE + (Frlc - Frlp));
+            const float rdn = rd3 - dtdx * dFr;
+            two_sum(FEc, -FEp, sE, eE);
+            const float dFE = sE + (eE + (FElc - FElp));
+            float edo = ed3 - dtdx * dFE + dt * g * (0.5f * ((Frp + Frlp) + (Frc + Frlc)));
+            float mno = mn3 - dtdx * (X(sm.x3, 2, sc) - X(sm.x3, 2, sl)) + dt * g * (0.5f * (rd3 + rdn));
+            float m1o = m13 - dtdx * (X(sm.x3, 3, sc) - X(sm.x3, 3, sl));
+            float m2o = m23 - dtdx * (X(sm.x3, 4, sc) - X(sm.x3, 4, sl));
+            const float rnew = r0c + rdn;
+            // FCT factors of cell c, bounds [0, 1]
+            float Rp, Rm;
+            {
+                const float rold = r0c + rd3;
+                const float GLc = X(sm.x3, 7, sc), GLp = X(sm.x3, 7, sl);
+                const float Ac = X(sm.x3, 8, sc), Ap = X(sm.x3, 8, sl);
+                const float cL = rold * fv_unfold(raw(5, c)) - (GLc - GLp);
+                const float FVL = cL / rnew;
+                const float Pp = rmax(0.0f, Ap) - rmin(0.0f, Ac);
+                const float Pm = rmax(0.0f, Ac) - rmin(0.0f, Ap);
+                const float Qp = (1.0f - FVL) * rnew;
+                const float Qm = FVL * rnew;
+                Rp = (Pp > 0.0f) ? rclamp(Qp / Pp, 0.0f, 1.0f) : 0.0f;
+                Rm = (Pm > 0.0f) ? rclamp(Qm / Pm, 0.0f, 1.0f) : 0.0f;
+            }
+            X(sm.x4, 0, sc) = Rp;
+            X(sm.x4, 1, sc) = Rm;
+            X(sm.x4, 2, sc) = rnew;
+            // heating and damping after the pass (fused), checks and CFL
+            if (A.sources) {
+                const float xa = xcell32(c);
+                const float sv = (A.grav == 1) ? (ax == 2 ? xa : zt) : fmaf(xa, xa, rt2);
+                const float4 hs = tab4(A.t4_src, A.ntab4, A.s4_0, A.inv_ds4, sv);
+                if (A.t_heat) edo = edo + dt * hs.x;
+                if (A.t_damp) {
+                    const float fd = rmax(0.0f, 1.0f - dt * hs.y);
+                    const float kin = 0.5f * (mno * mno + (m1o * m1o + m2o * m2o)) / rnew;
+                    mno = mno * fd;
+                    m1o = m1o * fd;
+                    m2o = m2o * fd;
+                    edo = edo - (1.0f - fd * fd) * kin;
+                }
+            }
+            if (c >= 0 && c < n && pen_ok) {
+                const float ri = 1.0f / rnew;
+                const float uu = mno * ri, vv = m1o * ri, wv_ = m2o * ri;
+                const float kin = 0.5f * (mno * uu + (m1o * vv + m2o * wv_));
+                const float pr = p0c + gm1 * (edo - kin);
+                if (!(rnew > 0.0f) || !(pr > 0.0f)) bad = true;
+                if (A.cfl) {
+                    const float spd = rmax(rmax(rabs(uu), rabs(vv)), rabs(wv_)) + rsq(gam * pr * ri);
+                    smax_local = rmax(smax_local, spd);
+                }
+            }
+            if (c >= -S) {
+                out_ref(0, c) = rdn;
+                out_ref(pn, c) = mno;
+                out_ref(p1, c) = m1o;
+                out_ref(p2, c) = m2o;
+                out_ref(4, c) = edo;
+            }
+        }
+        __syncthreads();
+
+        // ================= E: cell cA-4 ======================================
+        {
+            const int c = cA - 4;
+            const int sc = slot_of(c), sl = slot_add(sc, -1), sr = slot_add(sc, 1);
+            const float Rpl = X(sm.x4, 0, sl), Rml = X(sm.x4, 1, sl);
+            const float Rpc = X(sm.x4, 0, sc), Rmc = X(sm.x4, 1, sc);
+            const float Rpr = X(sm.x4, 0, sr), Rmr = X(sm.x4, 1, sr);
+            // limited transfers of the right face (c+1/2) and the left face (c-1/2)
+            const float Ar = X(sm.x3, 8, sc), Al = X(sm.x3, 8, sl);
+            const float Cfr = (Ar >= 0.0f) ? rmin(Rpr, Rmc) : rmin(Rpc, Rmr);
+            const float Cfl = (Al >= 0.0f) ? rmin(Rpc, Rml) : rmin(Rpl, Rmc);
+            const float KLr = X(sm.x3, 9, sc), KLl = X(sm.x3, 9, sl);
+            const float Gc4 = X(sm.x3, 7, sc) + Cfr * Ar;
+            const float Kc4 = KLr + Cfr * (X(sm.x3, 10, sc) - KLr);
+            const float Gq = X(sm.x3, 7, sl) + Cfl * Al;
+            const float Kq = KLl + Cfl * (X(sm.x3, 10, sl) - KLl);
+            const float PHIp = X(sm.x3, 13, sc), PHIq = X(sm.x3, 13, sl);
+            const float KMp = X(sm.x3, 14, sc), KMq = X(sm.x3, 14, sl);
+            const float sp = X(sm.x3, 15, sc), smm = X(sm.x3, 15, sl);
+            const float T1p = X(sm.x3, 11, sc), T1q = X(sm.x3, 11, sl);
+            const float T2p = X(sm.x3, 12, sc), T2q = X(sm.x3, 12, sl);
+            const float rold = X(sm.x1, 5, sc) + raw(0, c);
+            const float rnew = X(sm.x4, 2, sc);
+            const float fs0 = raw(5, c);
+            const float fv0 = fv_unfold(fs0);
+            const float on0 = raw(on_, c), o10 = raw(o1_, c), o20 = raw(o2_, c);
+            const float cold = rold * fv0;
+            float c_out = 0, z_out = 0, z_in = 0, m_out = 0, zr_out = 0, zr_in = 0;
+            if (sp >= 0.0f) {
+                c_out = c_out + Gc4;
+                z_out = z_out + Kc4;
+                m_out = m_out + PHIp;
+                zr_out = zr_out + KMp;
+            } else {
+                const float sh = sp + 1.0f;
+                z_in = z_in + (-Kc4 - Gc4 * sh);
+                zr_in = zr_in + (-KMp - PHIp * sh);
+            }
+            if (smm >= 0.0f) {
+                const float sh = smm - 1.0f;
+                z_in = z_in + (Kq + Gq * sh);
+                zr_in = zr_in + (KMq + PHIq * sh);
+            } else {
+                c_out = c_out - Gq;
+                z_out = z_out - Kq;
+                m_out = m_out - PHIq;
+                zr_out = zr_out - KMq;
+            }
+            const float sbar = 0.5f * (smm + sp);
+            const float dZc = (cold - c_out) * sbar + z_in - z_out;
+            const float Zr = (rold - m_out) * sbar + zr_in - zr_out;
+            const float dPhi = PHIp - PHIq;
+            const float dG = Gc4 - Gq;
+            const float rinvn = 1.0f / rnew;
+            const float fvs = fv_add(fs0, (fv0 * dPhi - dG) * rinvn);
+            const float fvn = fv_unfold(fvs);
+            const float bnd = fv_moment_bound(fvs);
+            float onn = on0 + (on0 * dPhi + 12.0f * (dZc - fvn * Zr)) * rinvn;
+            float o1 = o10 + (o10 * dPhi - (T1p - T1q)) * rinvn;
+            float o2 = o20 + (o20 * dPhi - (T2p - T2q)) * rinvn;
+            onn = rclamp(onn, -bnd, bnd);
+            o1 = rclamp(o1, -bnd, bnd);
+            o2 = rclamp(o2, -bnd, bnd);
+            if (c >= -S) {
+                out_ref(5, c) = fvs;
+                out_ref(on_, c) = onn;
+                out_ref(o1_, c) = o1;
+                out_ref(o2_, c) = o2;
+            }
+        }
+        fence_async_smem();        // this thread's output writes, seen by the TMA store
+        __syncthreads();
+        if (tid == 0 && k >= 0) {
+            int k0, k1, k2;
+            coords(k * S, k0, k1, k2);
+            tma_store4(&tmap, k0, k1, k2, 0, &sm.out[k % NOUT][0]);
+        }
+    }
+
+    if (tid == 0) {
+        if (kstop <= klast) {
+            // the loads still in flight (chunks kstop and kstop + 1) land
+            // before the block leaves; each wait is bounded
+            for (int kk2 = kstop; kk2 <= kstop + 1 && kk2 <= klast; ++kk2)
+                (void)mbar_wait(&sm.bar[(kk2 + 1) % NIN], (unsigned)(((kk2 + 1) / NIN) & 1));
+            atomicOr(A.flags, FLAG_TIMEOUT);
+        }
+        bulk_wait_all();
+    }
+    if (bad && pen_ok) atomicOr(A.flags, FLAG_NONPHYS);
+    if (A.cfl) {
+        double smx = (double)smax_local;
+        for (int o = 16; o > 0; o >>= 1) smx = fmax(smx, __shfl_xor_sync(0xffffffffu, smx, o));
+        if ((threadIdx.x & 31) == 0) atomicMax(A.smax, dbits(smx));
+    }
+}
+
 }  // namespace tile
 }  // namespace ppm
