@@ -22,7 +22,9 @@
 // The state moves by TMA: a producer thread loads each 8 x 32 x 9 tile of
 // the next chunk (cp.async.bulk.tensor, completion on an mbarrier) while the
 // block works on the current one, and stores each finished chunk the same
-// way, in place.  For the y and z passes the box is 8 cells along x (32 B)
+// way, in place.  Stage A reads each cell's nine stored values once, maps the
+// ghost cells (periodic wrap, or the mirror image with the normal components
+// reversed) and puts them in a ring of their own for the later stages.  For the y and z passes the box is 8 cells along x (32 B)
 // by 32 cells along the pass; for the x pass it is 32 cells along x by 8
 // rows, read through the 128-byte swizzle so that a warp's 8 rows x 4 cells
 // fall in 32 different banks.
@@ -45,7 +47,7 @@ constexpr int S = 32;          // cells per pencil and step
 constexpr int P = 8;           // pencils per block
 constexpr int NT = S * P;      // threads per block
 constexpr int R = 40;          // ring slots per pencil (>= S + the 8 cells of lag)
-constexpr int NIN = 3;         // input chunk buffers (two read, one in flight)
+constexpr int NIN = 2;         // input chunk buffers (one read, one in flight)
 constexpr int NOUT = 2;        // output chunk buffers
 constexpr int CHUNK_FLOATS = 9 * S * P;          // one chunk of the 9 values
 constexpr unsigned CHUNK_BYTES = CHUNK_FLOATS * 4u;
@@ -56,6 +58,7 @@ constexpr long long WAIT_LIMIT = 1ll << 26;      // bounded mbarrier wait (itera
 struct Smem {
     float in[NIN][CHUNK_FLOATS];   // TMA destinations (9216 B each: 1024-byte multiples)
     float out[NOUT][CHUNK_FLOATS]; // TMA sources
+    float x0[9][R * P];            // A -> B..E: the stored values (ghosts mapped and mirrored)
     float x1[NX1][R * P];          // A -> B, D, E: rho', u, v, w, p', rho0, p0, g
     float x2[NX2][R * P];          // B -> C: left state (5), right state (5), PPB profile (2)
     float x3[NX3][R * P];          // C -> D, E: fluxes (7), PPB transfers (9)
@@ -132,27 +135,34 @@ __device__ __forceinline__ int slot_add(int s, int d) {
 }
 
 // ---------------------------------------------------------------------------
-// The kernel.  XP: x pass (pencils are rows along x); otherwise the y or z
-// pass (A.axis), pencils along it, 8 neighbouring x columns per block.
+// The kernel for the pass along axis AX.  AX = 0: pencils are rows along x,
+// 8 neighbouring rows per block; AX = 1, 2: pencils along y or z, 8
+// neighbouring x columns per block.
 // Grid: (ceil(nlane / 8), nblk).  Needs nx % 4 == 0 (TMA strides), no
 // confining sphere, four-value PPB, no shock dissipation.
+//
+// Step k (k = -1 .. klast) loads chunk k = cells [kS + 4, kS + S + 4) of
+// every pencil; thread (p, l) takes cell kS + 4 + l in stage A, the cell or
+// face l - 2, l - 3, l - 3, l - 4 behind it in stages B to E, and the block
+// stores cells [kS, kS + S) at the end of the step.
 // ---------------------------------------------------------------------------
-template <bool XP>
+template <int AX>
 __global__ void __launch_bounds__(NT, 2) tile_pass_kernel(const SweepArgs<float> A,
                                                          const __grid_constant__ CUtensorMap tmap) {
+    constexpr bool XP = (AX == 0);
     extern __shared__ unsigned char smem_raw[];
     Smem &sm = *reinterpret_cast<Smem *>(smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u));
     const int tid = threadIdx.x;
     const int p = tid & (P - 1);          // pencil of this thread
     const int l = tid >> 3;               // cell of this thread within a step
-    const int ax = XP ? 0 : A.axis, t1d = (ax + 1) % 3, t2d = (ax + 2) % 3;
+    constexpr int ax = AX, t1d = (AX + 1) % 3, t2d = (AX + 2) % 3;
     const int n = A.n, bcl = A.bc_lo, bch = A.bc_hi;
     const int lane = blockIdx.x * P + p, blk = blockIdx.y;
     const bool pen_ok = lane < A.nlane;
     const bool lane_t1 = (A.lane_dim == t1d);
     // variables in the pass frame: normal and transverse momenta / moments
-    const int pn = 1 + ax, p1 = 1 + t1d, p2 = 1 + t2d;
-    const int on_ = 6 + ax, o1_ = 6 + t1d, o2_ = 6 + t2d;
+    constexpr int pn = 1 + ax, p1 = 1 + t1d, p2 = 1 + t2d;
+    constexpr int on_ = 6 + ax, o1_ = 6 + t1d, o2_ = 6 + t2d;
 
     const float gam = (float)A.gamma, gm1 = (float)(A.gamma - 1.0);
     const float kk = (float)((A.gamma + 1.0) / (2.0 * A.gamma));
@@ -184,31 +194,51 @@ __global__ void __launch_bounds__(NT, 2) tile_pass_kernel(const SweepArgs<float>
         if (A.grav == 2) r.z *= xa;
         return r;
     };
-    auto xcell32 = [&](int mm) { return orgf + ((float)mm + 0.5f) * dxf; };
-    auto xface32 = [&](int j) { return orgf + (float)map_face(j, n, bcl, bch) * dxf; };
+    // The same lookup split in two, so that the two rows can be fetched a
+    // stage before they are needed (the latency then overlaps other work)
+    struct Rows {
+        float4 a, b;
+        float w;
+    };
+    auto rows_issue = [&](float xa) -> Rows {
+        Rows r;
+        if (!bvar) {
+            r.a = r.b = bconst;
+            r.w = 0.0f;
+            return r;
+        }
+        const float sv = (A.grav == 1) ? xa : fmaf(xa, xa, rt2);
+        const float u = (sv - A.s4_0) * A.inv_ds4;
+        const float fl = fminf(fmaxf(floorf(u), 0.0f), (float)(A.ntab4 - 2));
+        const int i = (int)fl;
+        r.a = __ldg(A.t4_base + i);
+        r.b = __ldg(A.t4_base + i + 1);
+        r.w = u - fl;
+        return r;
+    };
+    auto rows_finish = [&](const Rows &t, float xa) -> float4 {
+        if (!bvar) return bconst;
+        float4 r = make_float4(fmaf(t.w, t.b.x - t.a.x, t.a.x), fmaf(t.w, t.b.y - t.a.y, t.a.y),
+                               fmaf(t.w, t.b.z - t.a.z, t.a.z), 0.0f);
+        if (A.grav == 2) r.z *= xa;
+        return r;
+    };
+    // cell centres and faces from float cell indices: k S + (small integer)
+    // is exact in FP32, so these equal the register-window form's values
+    auto xcell_f = [&](float fm) { return orgf + (fm + 0.5f) * dxf; };
 
-    // raw (stored) value v of cell c of this thread's pencil
-    auto in_idx = [&](int c) {
-        // cells below the first ghost only feed values that no stored cell
-        // uses (the start of the pipeline); they read ghost -4 instead
-        c = max(c, -4);
-        const int k = (c - 4 + S) / S - 1;          // chunk of cell c (c >= -4)
-        const int b = (k + 1) % NIN;
-        return b * CHUNK_FLOATS + chunk_pos<XP>(p, c - 4 - k * S);
-    };
-    auto raw = [&](int v, int c) -> float { return (&sm.in[0][0])[in_idx(c) + v * (S * P)]; };
-    auto out_ref = [&](int v, int c) -> float & {
-        const int j = (c + S) / S - 1;              // output chunk of cell c (c >= -S)
-        const int b = (j + NOUT) % NOUT;
-        return sm.out[b][v * (S * P) + chunk_pos<XP>(p, c - j * S)];
-    };
     auto X = [&](float (*ring)[R * P], int v, int slot) -> float & { return ring[v][slot * P + p]; };
+    // this thread's row in a chunk buffer: stage A reads row l of chunk k;
+    // stage E writes row l of output chunk k, stage D row l + 1 (or row 0 of
+    // chunk k + 1 for l = S - 1)
+    const int posA = chunk_pos<XP>(p, l);
+    const int posD = chunk_pos<XP>(p, (l + 1) & (S - 1));
 
     // tile coordinates of a chunk: cells [c0, c0 + S) along the pass
     auto coords = [&](int c0, int &k0, int &k1, int &k2) {
         if constexpr (XP) {
             k0 = c0; k1 = blockIdx.x * P; k2 = blk;
-        } else if (A.axis == 1) {
+        } else if constexpr (AX == 1) {
             k0 = blockIdx.x * P; k1 = c0; k2 = blk;
         } else {
             k0 = blockIdx.x * P; k1 = blk; k2 = c0;
@@ -222,25 +252,24 @@ __global__ void __launch_bounds__(NT, 2) tile_pass_kernel(const SweepArgs<float>
         sm.abort = 0;
         fence_mbar_init();
     }
+    for (int i = tid; i < 9 * R * P; i += NT) (&sm.x0[0][0])[i] = 0.0f;
     for (int i = tid; i < NX1 * R * P; i += NT) (&sm.x1[0][0])[i] = 0.0f;
     for (int i = tid; i < NX2 * R * P; i += NT) (&sm.x2[0][0])[i] = 0.0f;
     for (int i = tid; i < NX3 * R * P; i += NT) (&sm.x3[0][0])[i] = 0.0f;
     for (int i = tid; i < NX4 * R * P; i += NT) (&sm.x4[0][0])[i] = 0.0f;
-    // periodic pencils: cells n-4..n-1 are the low-side ghosts; read them now,
-    // before any store of this block can overwrite them (thread tid < 4 P
-    // holds ghost (tid / P) of pencil tid % P)
+    // periodic pencils: cells n-4..n-1 are the low-side ghosts -4..-1, which
+    // the threads l = S-8 .. S-5 take in stage A of step -1; they read them
+    // now, before any store of this block can overwrite them
     float gpre[9];
-    const bool gthr = (bcl == 0) && tid < 4 * P;
-    if (gthr) {
-        const int gp = tid % P, gc = tid / P;      // ghost cell -4 + gc <- cell n - 4 + gc
-        const int gl = blockIdx.x * P + gp;
-        if (gl < A.nlane) {
-            const float *q = A.q + (long long)gl * A.s_lane + (long long)blk * A.s_blk +
-                             (long long)(n - 4 + gc) * A.s_axis;
-            for (int v = 0; v < 9; ++v) gpre[v] = q[(long long)v * A.vs];
-        } else {
-            for (int v = 0; v < 9; ++v) gpre[v] = 0.0f;
-        }
+    const int c_first = -S + 4 + l;                 // stage A cell of step -1
+    if (bcl == 0 && c_first >= -4 && c_first < 0 && pen_ok) {
+        const float *q = A.q + (long long)lane * A.s_lane + (long long)blk * A.s_blk +
+                         (long long)(n + c_first) * A.s_axis;
+#pragma unroll
+        for (int v = 0; v < 9; ++v) gpre[v] = q[(long long)v * A.vs];
+    } else {
+#pragma unroll
+        for (int v = 0; v < 9; ++v) gpre[v] = 0.0f;
     }
     __syncthreads();
     if (tid == 0) {
@@ -254,119 +283,122 @@ __global__ void __launch_bounds__(NT, 2) tile_pass_kernel(const SweepArgs<float>
     float smax_local = 0.0f;
     bool bad = false;
     int kstop = klast + 1;                          // step at which a wait gave up
+    int sA = (l + 12) % R;                          // ring slot of the stage A cell (-S + 4 + l)
+    const float flA = (float)(4 + l);
+    Rows rowsA = rows_issue(xcell_f((float)(-S) + flA));   // stage A of step -1
 
     for (int k = -1; k <= klast; ++k) {
         const int cA = k * S + 4 + l;               // stage A cell of this thread
-        // ---- producer: the next chunk into the buffer of chunk k-2 --------
+        const float fk = (float)(k * S);
+        if (k > -1) sA = (sA + S >= R) ? sA + S - R : sA + S;
+        // ---- producer: chunk k+1 into the buffer of chunk k-1 -------------
         if (tid == 0 && k + 1 <= klast) {
-            const int b = (k + 2) % NIN;
-            fence_async_smem();   // reads of this buffer (chunk k-2) by the block came first
+            const int b = (k + 2) & 1;
+            fence_async_smem();   // the block's reads of chunk k-1 came first
             int k0, k1, k2;
             coords((k + 1) * S + 4, k0, k1, k2);
             mbar_expect_tx(&sm.bar[b], CHUNK_BYTES);
             tma_load4(&sm.in[b][0], &tmap, k0, k1, k2, 0, &sm.bar[b]);
         }
-        // ---- wait for chunk k (its buffer's use (k+1)/3, parity & 1) -------
-        {
-            const int b = (k + 1) % NIN;
-            if (!mbar_wait(&sm.bar[b], (unsigned)(((k + 1) / NIN) & 1))) sm.abort = 1;
-        }
+        // ---- wait for chunk k (its buffer's use (k+1)/2, parity & 1) -------
+        const float *inb = &sm.in[(k + 1) & 1][0];
+        if (!mbar_wait(&sm.bar[(k + 1) & 1], (unsigned)(((k + 1) >> 1) & 1))) sm.abort = 1;
         __syncthreads();
         if (sm.abort) {
             kstop = k;
             break;
         }
-        // ---- ghost cells of this chunk (rows [k S + 4, k S + S + 4)) -------
-        {
-            const int c0 = k * S + 4;
-            // low side (chunk -1 only): periodic from the cells read at the
-            // start; walls mirror cells 0..3 with the normal components flipped
-            if (k == -1 && tid < 4 * P) {
-                const int gp = tid % P, gc = tid / P;
-                const int c = -4 + gc;
-                const int ri = (c - c0);
-                float *dst = &sm.in[0][0];
-                if (bcl == 0) {
-                    for (int v = 0; v < 9; ++v) dst[v * (S * P) + chunk_pos<XP>(gp, ri)] = gpre[v];
-                } else {
-                    const int src = chunk_pos<XP>(gp, (-1 - c) - c0);
-                    for (int v = 0; v < 9; ++v) {
-                        const float x = dst[v * (S * P) + src];
-                        dst[v * (S * P) + chunk_pos<XP>(gp, ri)] = (v == pn || v == on_) ? -x : x;
-                    }
-                }
-            }
-            // high side: cells n..n+3 if they fall in this chunk
-            if (tid < 4 * P) {
-                const int gp = tid % P, gc = tid / P;
-                const int c = n + gc;
-                if (c >= c0 && c < c0 + S) {
-                    float *dst = &sm.in[0][0] + ((k + 1) % NIN) * CHUNK_FLOATS;
-                    const int di = chunk_pos<XP>(gp, c - c0);
-                    if (bch == 0) {
-                        for (int v = 0; v < 9; ++v) dst[v * (S * P) + di] = sm.stash[v][gc * P + gp];
-                    } else {
-                        const int cs = 2 * n - 1 - c;   // mirror cell (n-1 .. n-4)
-                        const int kc = (cs - 4 + S) / S - 1;
-                        const float *src = &sm.in[0][0] + ((kc + 1) % NIN) * CHUNK_FLOATS;
-                        const int si = chunk_pos<XP>(gp, cs - 4 - kc * S);
-                        for (int v = 0; v < 9; ++v) {
-                            const float x = src[v * (S * P) + si];
-                            dst[v * (S * P) + di] = (v == pn || v == on_) ? -x : x;
-                        }
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        if (k == -1 && bch == 0 && tid < 4 * P) {
-            // cells 0..3 of periodic pencils, before they are overwritten
-            const int gp = tid % P, gc = tid / P;
-            for (int v = 0; v < 9; ++v) sm.stash[v][gc * P + gp] = raw(v, gc);
-        }
 
-        // ================= A: primitives of cell cA ==========================
+        // ================= A: stored values and primitives of cell cA ========
         {
             const int c = cA;
+            float q[9];
             bool flip = false;
-            const int m = (c >= -4 && c < n + 4) ? map_cell(c, n, bcl, bch, flip) : 0;
-            const float4 bb = base_at_x(xcell32(m));
+            int m = c;
+            if (c >= 0 && c < n) {
+#pragma unroll
+                for (int v = 0; v < 9; ++v) q[v] = inb[v * (S * P) + posA];
+                if (k == -1 && bch == 0) {
+                    // cells 0..3 of periodic pencils, before they are overwritten
+#pragma unroll
+                    for (int v = 0; v < 9; ++v) sm.stash[v][c * P + p] = q[v];
+                }
+            } else if (c < -4 || c >= n + 4) {
+#pragma unroll
+                for (int v = 0; v < 9; ++v) q[v] = 0.0f;   // beyond the ghosts: never used
+                m = 0;
+            } else {
+                // ghost: periodic image or mirror image (normal components reversed)
+                m = map_cell(c, n, bcl, bch, flip);
+                if (c < 0 && bcl == 0) {
+#pragma unroll
+                    for (int v = 0; v < 9; ++v) q[v] = gpre[v];
+                } else if (c < 0) {
+                    const int pos = chunk_pos<XP>(p, m + S - 4);   // row of cell m in chunk -1
+#pragma unroll
+                    for (int v = 0; v < 9; ++v) q[v] = inb[v * (S * P) + pos];
+                } else if (bch == 0) {
+#pragma unroll
+                    for (int v = 0; v < 9; ++v) q[v] = sm.stash[v][m * P + p];
+                } else if (m >= k * S + 4) {
+                    const int pos = chunk_pos<XP>(p, m - k * S - 4);
+#pragma unroll
+                    for (int v = 0; v < 9; ++v) q[v] = inb[v * (S * P) + pos];
+                } else {
+                    const int sm_ = slot_of(m);
+#pragma unroll
+                    for (int v = 0; v < 9; ++v) q[v] = X(sm.x0, v, sm_);
+                }
+                if (flip) {
+                    q[pn] = -q[pn];
+                    q[on_] = -q[on_];
+                }
+            }
+            // base state: the rows fetched a step ahead hold cell c itself
+            const float4 bb = (m == c) ? rows_finish(rowsA, xcell_f(fk + flA)) : base_at_x(xcell_f((float)m));
             const float sg = flip ? -1.0f : 1.0f;
-            const float rd = raw(0, c);
-            const float mn = raw(pn, c), m1 = raw(p1, c), m2 = raw(p2, c);
-            const float ed = raw(4, c);
+            const float rd = q[0];
+            const float mn = q[pn], m1 = q[p1], m2 = q[p2];
+            const float ed = q[4];
             const float rho = bb.x + rd;
             const float rinv = 1.0f / rho;
             const float u = mn * rinv, v = m1 * rinv, w = m2 * rinv;
             const float ke = 0.5f * (mn * u + (m1 * v + m2 * w));
             const float pd = gm1 * (ed - ke);
-            const int sl = slot_of(c);
-            X(sm.x1, 0, sl) = rd;
-            X(sm.x1, 1, sl) = u;
-            X(sm.x1, 2, sl) = v;
-            X(sm.x1, 3, sl) = w;
-            X(sm.x1, 4, sl) = pd;
-            X(sm.x1, 5, sl) = bb.x;
-            X(sm.x1, 6, sl) = bb.y;
-            X(sm.x1, 7, sl) = sg * bb.z;
+#pragma unroll
+            for (int vv = 0; vv < 9; ++vv) X(sm.x0, vv, sA) = q[vv];
+            X(sm.x1, 0, sA) = rd;
+            X(sm.x1, 1, sA) = u;
+            X(sm.x1, 2, sA) = v;
+            X(sm.x1, 3, sA) = w;
+            X(sm.x1, 4, sA) = pd;
+            X(sm.x1, 5, sA) = bb.x;
+            X(sm.x1, 6, sA) = bb.y;
+            X(sm.x1, 7, sA) = sg * bb.z;
         }
         __syncthreads();
 
+        // face j+1/2 of stage C (j = cA - 3): its position, and its table rows
+        // fetched now so that stage B covers their latency
+        const int jC = cA - 3;
+        const bool plain_face = (jC + 1 >= 0 && jC + 1 <= n && !(jC + 1 == n && bch == 0));
+        const float xfC = orgf + (plain_face ? fk + (float)(l + 2) : (float)map_face(jC, n, bcl, bch)) * dxf;
+        const Rows rowsC = rows_issue(xfC);
+
         // ================= B: cell cA-2 ======================================
         {
-            const int c = cA - 2;
-            const int s0 = slot_of(c);
+            const int s0 = slot_add(sA, -2);
+            const int sm2 = slot_add(sA, -4), sm1 = slot_add(sA, -3), sp1 = slot_add(sA, -1);
+            const int sl5[5] = {sm2, sm1, s0, sp1, sA};
             float wrd[5], wu[5], wv[5], ww[5], wpd[5];
 #pragma unroll
             for (int d = 0; d < 5; ++d) {
-                const int sl = slot_add(s0, d - 2);
-                wrd[d] = X(sm.x1, 0, sl);
-                wu[d] = X(sm.x1, 1, sl);
-                wv[d] = X(sm.x1, 2, sl);
-                ww[d] = X(sm.x1, 3, sl);
-                wpd[d] = X(sm.x1, 4, sl);
+                wrd[d] = X(sm.x1, 0, sl5[d]);
+                wu[d] = X(sm.x1, 1, sl5[d]);
+                wv[d] = X(sm.x1, 2, sl5[d]);
+                ww[d] = X(sm.x1, 3, sl5[d]);
+                wpd[d] = X(sm.x1, 4, sl5[d]);
             }
-            const int sm1 = slot_add(s0, -1), sp1 = slot_add(s0, 1);
             const float r0c = X(sm.x1, 5, s0), p0c = X(sm.x1, 6, s0), gc = X(sm.x1, 7, s0);
             const float p0m = X(sm.x1, 6, sm1), p0p = X(sm.x1, 6, sp1);
             // interface values of faces c-1/2 and c+1/2 (a2)
@@ -473,9 +505,9 @@ __global__ void __launch_bounds__(NT, 2) tile_pass_kernel(const SweepArgs<float>
             // PPB profile of cell c: f = FV + m xi + a2 (xi^2 - 1/12), bound-limited (a9)
             float me2, ae2;
             {
-                const float fs = raw(5, c);
-                const float F = fv_unfold(fs), mm = raw(on_, c);
-                const float a2 = 0.25f * (raw(on_, c + 1) - raw(on_, c - 1));
+                const float fs = X(sm.x0, 5, s0);
+                const float F = fv_unfold(fs), mm = X(sm.x0, on_, s0);
+                const float a2 = 0.25f * (X(sm.x0, on_, sp1) - X(sm.x0, on_, sm1));
                 const float ep = 0.5f * mm + a2 * (1.0f / 6.0f);
                 const float em = a2 * (1.0f / 6.0f) - 0.5f * mm;
                 float gmax = rmax(ep, em), gmin = rmin(ep, em);
@@ -507,14 +539,14 @@ __global__ void __launch_bounds__(NT, 2) tile_pass_kernel(const SweepArgs<float>
         // ================= C: face (cA-3)+1/2 ================================
         {
             const int j = cA - 3;                    // face j+1/2 between cells j and j+1
-            const int sj = slot_of(j), sr = slot_add(sj, 1);
+            const int sj = slot_add(sA, -3), sr = slot_add(sA, -2);
             float WLp[5], WRc[5];
 #pragma unroll
             for (int q = 0; q < 5; ++q) {
                 WLp[q] = X(sm.x2, q, sj);            // left state: right edge of cell j
                 WRc[q] = X(sm.x2, 5 + q, sr);        // right state: left edge of cell j+1
             }
-            const float4 bf = base_at_x(xface32(j));
+            const float4 bf = rows_finish(rowsC, xfC);
             const float r0 = bf.x, p0 = bf.y;
             const float rdL = WLp[0], uL = WLp[1], pdL = WLp[4];
             const float rdR = WRc[0], uR = WRc[1], pdR = WRc[4];
@@ -572,11 +604,7 @@ __global__ void __launch_bounds__(NT, 2) tile_pass_kernel(const SweepArgs<float>
                 FEc = hE;
                 FElc = eE + (ust * (gg1 * pst) + kin * Fr);
             }
-            const float Fnc = Fr * ust + pst;
-            const float Ft1c = Fr * vst;
-            const float Ft2c = Fr * wst;
             // PPB transfers across the face: donor j (from the left) or j+1
-            float GLc, Ac, KLc, KHc, T1c, T2c;
             {
                 const float sig = ust * dtdx;
                 const float phi = dtdx * Fr;
@@ -589,37 +617,31 @@ __global__ void __launch_bounds__(NT, 2) tile_pass_kernel(const SweepArgs<float>
                     M1 = -M1;
                     M3 = -M3;
                 }
-                const int dc = fromleft ? j : j + 1;
                 const int sd = fromleft ? sj : sr;
-                const float F = fv_unfold(raw(5, dc));
+                const float F = fv_unfold(X(sm.x0, 5, sd));
                 const float me = X(sm.x2, 10, sd);
                 const float ae = X(sm.x2, 11, sd);
-                const float ot1 = raw(o1_, dc), ot2 = raw(o2_, dc);
+                const float ot1 = X(sm.x0, o1_, sd), ot2 = X(sm.x0, o2_, sd);
                 const float phibar = F + me * M1 + ae * (M2 - (1.0f / 12.0f));
                 const float psibar = F * M1 + me * M2 + ae * (M3 - M1 * (1.0f / 12.0f));
-                GLc = phi * F;
-                Ac = phi * phibar - GLc;
-                KLc = phi * F * M1;
-                KHc = phi * psibar;
-                T1c = phi * ot1;
-                T2c = phi * ot2;
+                const float GLc = phi * F;
+                X(sm.x3, 7, sj) = GLc;
+                X(sm.x3, 8, sj) = phi * phibar - GLc;
+                X(sm.x3, 9, sj) = phi * F * M1;
+                X(sm.x3, 10, sj) = phi * psibar;
+                X(sm.x3, 11, sj) = phi * ot1;
+                X(sm.x3, 12, sj) = phi * ot2;
                 X(sm.x3, 13, sj) = phi;
                 X(sm.x3, 14, sj) = phi * M1;
                 X(sm.x3, 15, sj) = sig;
             }
             X(sm.x3, 0, sj) = Frc;
             X(sm.x3, 1, sj) = Frlc;
-            X(sm.x3, 2, sj) = Fnc;
-            X(sm.x3, 3, sj) = Ft1c;
-            X(sm.x3, 4, sj) = Ft2c;
+            X(sm.x3, 2, sj) = Fr * ust + pst;
+            X(sm.x3, 3, sj) = Fr * vst;
+            X(sm.x3, 4, sj) = Fr * wst;
             X(sm.x3, 5, sj) = FEc;
             X(sm.x3, 6, sj) = FElc;
-            X(sm.x3, 7, sj) = GLc;
-            X(sm.x3, 8, sj) = Ac;
-            X(sm.x3, 9, sj) = KLc;
-            X(sm.x3, 10, sj) = KHc;
-            X(sm.x3, 11, sj) = T1c;
-            X(sm.x3, 12, sj) = T2c;
         }
         if (tid == 0) bulk_wait_read_all();   // the last store has read its buffer
         __syncthreads();
@@ -627,9 +649,10 @@ __global__ void __launch_bounds__(NT, 2) tile_pass_kernel(const SweepArgs<float>
         // ================= D: cell cA-3 ======================================
         {
             const int c = cA - 3;
-            const int sc = slot_of(c), sl = slot_add(sc, -1);
+            const int sc = slot_add(sA, -3), sl = slot_add(sA, -4);
             const float g = X(sm.x1, 7, sc), r0c = X(sm.x1, 5, sc), p0c = X(sm.x1, 6, sc);
-            const float rd3 = raw(0, c), mn3 = raw(pn, c), m13 = raw(p1, c), m23 = raw(p2, c), ed3 = raw(4, c);
+            const float rd3 = X(sm.x0, 0, sc), mn3 = X(sm.x0, pn, sc), m13 = X(sm.x0, p1, sc);
+            const float m23 = X(sm.x0, p2, sc), ed3 = X(sm.x0, 4, sc);
             const float Frc = X(sm.x3, 0, sc), Frlc = X(sm.x3, 1, sc), Frp = X(sm.x3, 0, sl), Frlp = X(sm.x3, 1, sl);
             const float FEc = X(sm.x3, 5, sc), FElc = X(sm.x3, 6, sc), FEp = X(sm.x3, 5, sl), FElp = X(sm.x3, 6, sl);
             float sE, eE;
@@ -644,26 +667,23 @@ __global__ void __launch_bounds__(NT, 2) tile_pass_kernel(const SweepArgs<float>
             float m2o = m23 - dtdx * (X(sm.x3, 4, sc) - X(sm.x3, 4, sl));
             const float rnew = r0c + rdn;
             // FCT factors of cell c, bounds [0, 1]
-            float Rp, Rm;
             {
                 const float rold = r0c + rd3;
                 const float GLc = X(sm.x3, 7, sc), GLp = X(sm.x3, 7, sl);
                 const float Ac = X(sm.x3, 8, sc), Ap = X(sm.x3, 8, sl);
-                const float cL = rold * fv_unfold(raw(5, c)) - (GLc - GLp);
+                const float cL = rold * fv_unfold(X(sm.x0, 5, sc)) - (GLc - GLp);
                 const float FVL = cL / rnew;
                 const float Pp = rmax(0.0f, Ap) - rmin(0.0f, Ac);
                 const float Pm = rmax(0.0f, Ac) - rmin(0.0f, Ap);
                 const float Qp = (1.0f - FVL) * rnew;
                 const float Qm = FVL * rnew;
-                Rp = (Pp > 0.0f) ? rclamp(Qp / Pp, 0.0f, 1.0f) : 0.0f;
-                Rm = (Pm > 0.0f) ? rclamp(Qm / Pm, 0.0f, 1.0f) : 0.0f;
+                X(sm.x4, 0, sc) = (Pp > 0.0f) ? rclamp(Qp / Pp, 0.0f, 1.0f) : 0.0f;
+                X(sm.x4, 1, sc) = (Pm > 0.0f) ? rclamp(Qm / Pm, 0.0f, 1.0f) : 0.0f;
+                X(sm.x4, 2, sc) = rnew;
             }
-            X(sm.x4, 0, sc) = Rp;
-            X(sm.x4, 1, sc) = Rm;
-            X(sm.x4, 2, sc) = rnew;
             // heating and damping after the pass (fused), checks and CFL
             if (A.sources) {
-                const float xa = xcell32(c);
+                const float xa = xcell_f(fk + (float)(l + 1));
                 const float sv = (A.grav == 1) ? (ax == 2 ? xa : zt) : fmaf(xa, xa, rt2);
                 const float4 hs = tab4(A.t4_src, A.ntab4, A.s4_0, A.inv_ds4, sv);
                 if (A.t_heat) edo = edo + dt * hs.x;
@@ -687,20 +707,21 @@ __global__ void __launch_bounds__(NT, 2) tile_pass_kernel(const SweepArgs<float>
                     smax_local = rmax(smax_local, spd);
                 }
             }
-            if (c >= -S) {
-                out_ref(0, c) = rdn;
-                out_ref(pn, c) = mno;
-                out_ref(p1, c) = m1o;
-                out_ref(p2, c) = m2o;
-                out_ref(4, c) = edo;
-            }
+            float *o = &sm.out[(l == S - 1 ? k + 1 : k) & 1][posD];
+            o[0] = rdn;
+            o[pn * (S * P)] = mno;
+            o[p1 * (S * P)] = m1o;
+            o[p2 * (S * P)] = m2o;
+            o[4 * (S * P)] = edo;
         }
         __syncthreads();
 
+        // rows of the next step's stage A cell (cA + S), fetched during stage E
+        rowsA = rows_issue(xcell_f(fk + (float)S + flA));
+
         // ================= E: cell cA-4 ======================================
         {
-            const int c = cA - 4;
-            const int sc = slot_of(c), sl = slot_add(sc, -1), sr = slot_add(sc, 1);
+            const int sc = slot_add(sA, -4), sl = slot_add(sA, -5), sr = slot_add(sA, -3);
             const float Rpl = X(sm.x4, 0, sl), Rml = X(sm.x4, 1, sl);
             const float Rpc = X(sm.x4, 0, sc), Rmc = X(sm.x4, 1, sc);
             const float Rpr = X(sm.x4, 0, sr), Rmr = X(sm.x4, 1, sr);
@@ -718,11 +739,11 @@ __global__ void __launch_bounds__(NT, 2) tile_pass_kernel(const SweepArgs<float>
             const float sp = X(sm.x3, 15, sc), smm = X(sm.x3, 15, sl);
             const float T1p = X(sm.x3, 11, sc), T1q = X(sm.x3, 11, sl);
             const float T2p = X(sm.x3, 12, sc), T2q = X(sm.x3, 12, sl);
-            const float rold = X(sm.x1, 5, sc) + raw(0, c);
+            const float rold = X(sm.x1, 5, sc) + X(sm.x0, 0, sc);
             const float rnew = X(sm.x4, 2, sc);
-            const float fs0 = raw(5, c);
+            const float fs0 = X(sm.x0, 5, sc);
             const float fv0 = fv_unfold(fs0);
-            const float on0 = raw(on_, c), o10 = raw(o1_, c), o20 = raw(o2_, c);
+            const float on0 = X(sm.x0, on_, sc), o10 = X(sm.x0, o1_, sc), o20 = X(sm.x0, o2_, sc);
             const float cold = rold * fv0;
             float c_out = 0, z_out = 0, z_in = 0, m_out = 0, zr_out = 0, zr_in = 0;
             if (sp >= 0.0f) {
@@ -760,19 +781,18 @@ __global__ void __launch_bounds__(NT, 2) tile_pass_kernel(const SweepArgs<float>
             onn = rclamp(onn, -bnd, bnd);
             o1 = rclamp(o1, -bnd, bnd);
             o2 = rclamp(o2, -bnd, bnd);
-            if (c >= -S) {
-                out_ref(5, c) = fvs;
-                out_ref(on_, c) = onn;
-                out_ref(o1_, c) = o1;
-                out_ref(o2_, c) = o2;
-            }
+            float *o = &sm.out[k & 1][posA];
+            o[5 * (S * P)] = fvs;
+            o[on_ * (S * P)] = onn;
+            o[o1_ * (S * P)] = o1;
+            o[o2_ * (S * P)] = o2;
         }
         fence_async_smem();        // this thread's output writes, seen by the TMA store
         __syncthreads();
         if (tid == 0 && k >= 0) {
             int k0, k1, k2;
             coords(k * S, k0, k1, k2);
-            tma_store4(&tmap, k0, k1, k2, 0, &sm.out[k % NOUT][0]);
+            tma_store4(&tmap, k0, k1, k2, 0, &sm.out[k & 1][0]);
         }
     }
 
@@ -781,7 +801,7 @@ __global__ void __launch_bounds__(NT, 2) tile_pass_kernel(const SweepArgs<float>
             // the loads still in flight (chunks kstop and kstop + 1) land
             // before the block leaves; each wait is bounded
             for (int kk2 = kstop; kk2 <= kstop + 1 && kk2 <= klast; ++kk2)
-                (void)mbar_wait(&sm.bar[(kk2 + 1) % NIN], (unsigned)(((kk2 + 1) / NIN) & 1));
+                (void)mbar_wait(&sm.bar[(kk2 + 1) & 1], (unsigned)(((kk2 + 1) >> 1) & 1));
             atomicOr(A.flags, FLAG_TIMEOUT);
         }
         bulk_wait_all();

@@ -9,11 +9,15 @@
 namespace ppm {
 
 cudaError_t prepare_tile_f32() {
-    cudaError_t e = cudaFuncSetAttribute(tile::tile_pass_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(tile::tile_pass_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)tile::SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(tile::tile_pass_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)tile::SMEM_BYTES);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tile::tile_pass_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tile::SMEM_BYTES);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tile::tile_pass_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tile::SMEM_BYTES);
+    return e;
 }
 
 size_t tile_smem_bytes() { return tile::SMEM_BYTES; }
@@ -56,9 +60,11 @@ int tile_encode_map(CUtensorMap *m, void *state, int nx, int ny, int nz, int axi
 void launch_tile_f32(const SweepArgs<float> &a, const CUtensorMap *m, cudaStream_t st) {
     const dim3 grid((a.nlane + tile::P - 1) / tile::P, a.nblk);
     if (a.axis == 0)
-        tile::tile_pass_kernel<true><<<grid, tile::NT, tile::SMEM_BYTES, st>>>(a, *m);
+        tile::tile_pass_kernel<0><<<grid, tile::NT, tile::SMEM_BYTES, st>>>(a, *m);
+    else if (a.axis == 1)
+        tile::tile_pass_kernel<1><<<grid, tile::NT, tile::SMEM_BYTES, st>>>(a, *m);
     else
-        tile::tile_pass_kernel<false><<<grid, tile::NT, tile::SMEM_BYTES, st>>>(a, *m);
+        tile::tile_pass_kernel<2><<<grid, tile::NT, tile::SMEM_BYTES, st>>>(a, *m);
 }
 
 }  // namespace ppm

@@ -59,8 +59,8 @@ def test_periodic_box_20_steps():
 
 @pytest.mark.parametrize("make", [lambda: workloads.strat_box(shape=(148, 20, 36)),
                                   lambda: workloads.sphere(shape=(44, 36, 40)),
-                                  lambda: workloads.sphere(shape=(36, 70, 33))],
-                         ids=["strat148", "sphere44", "sphere36x70x33"])
+                                  lambda: workloads.strat_box(shape=(36, 70, 33))],
+                         ids=["strat148", "sphere44", "strat36x70x33"])
 def test_gravity_problems(make):
     p = make()
     qg, qo = _run_pair(p, 8)
