@@ -671,14 +671,165 @@ __global__ void divergence_kernel(SweepArgs<R> A, const R *st, R *D, long long n
     }
 }
 
+// The same divergence for the FP32 form, tiled: a block of 32 x 16 threads
+// owns a 32 x 16 column of cells in x-y and marches up a run of DIV_ZRUN
+// z-planes.  Each cell's velocity (rho u_d / (rho0 + rho'), rho0 from the
+// pass kernels' FP32 tables) is computed once; u_x and u_y of a plane, with a
+// one-cell halo, sit in shared memory (two planes, one barrier per plane),
+// u_z of the planes below and above stay in registers.  The loads of a plane
+// are issued two planes ahead of their use.  Ghost neighbours as in the
+// passes: periodic wrap, or the mirror cell with the normal velocity
+// reversed.  Differences summed in x, y, z order, times 1/(2 dx).
+constexpr int DIV_TX = 32, DIV_TY = 16, DIV_ZRUN = 64;
+
+struct DivLoad {
+    float rd, m0, m1, m2;   // rho', rho u, rho v, rho w
+    float ta, tb, tw;       // rho0 table rows and weight
+    bool ok;                // a cell was loaded
+    signed char sx, sy, sz; // mirror signs of u, v, w
+};
+
+__global__ void __launch_bounds__(DIV_TX * DIV_TY) divergence_tile_kernel(SweepArgs<float> A, const float *st,
+                                                                          float *D, long long ncell, int nx, int ny,
+                                                                          int nz, int bx0, int bx1, int by0, int by1,
+                                                                          int bz0, int bz1) {
+    __shared__ float ux[2][DIV_TY + 2][DIV_TX + 2];
+    __shared__ float uy[2][DIV_TY + 2][DIV_TX + 2];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int i = blockIdx.x * DIV_TX + tx, j = blockIdx.y * DIV_TY + ty;
+    const int k0 = blockIdx.z * DIV_ZRUN, k1 = min(nz, k0 + DIV_ZRUN);
+    const float h = (float)(0.5 / A.dx);
+    const float ox = (float)A.org[0], oy = (float)A.org[1], oz = (float)A.org[2], dxf = (float)A.dx;
+    // loads of cell (gi, gj, gk), mapped onto the grid when it is a ghost
+    auto issue = [&](int gi, int gj, int gk) -> DivLoad {
+        DivLoad d;
+        bool fx = false, fy = false, fz = false;
+        const int ii = map_cell(gi, nx, bx0, bx1, fx), jj = map_cell(gj, ny, by0, by1, fy);
+        const int kk = map_cell(gk, nz, bz0, bz1, fz);
+        d.sx = fx ? -1 : 1;
+        d.sy = fy ? -1 : 1;
+        d.sz = fz ? -1 : 1;
+        d.ok = true;
+        const long long cc = ((long long)kk * ny + jj) * nx + ii;
+        d.rd = __ldg(st + cc);
+        d.m0 = __ldg(st + ncell + cc);
+        d.m1 = __ldg(st + 2 * ncell + cc);
+        d.m2 = __ldg(st + 3 * ncell + cc);
+        d.ta = d.tb = (float)A.rho0_c;
+        d.tw = 0.0f;
+        if (A.grav != 0) {
+            float sv;
+            if (A.grav == 1) {
+                sv = oz + ((float)kk + 0.5f) * dxf;
+            } else {
+                const float x = ox + ((float)ii + 0.5f) * dxf, y = oy + ((float)jj + 0.5f) * dxf;
+                const float z = oz + ((float)kk + 0.5f) * dxf;
+                sv = fmaf(z, z, fmaf(y, y, x * x));
+            }
+            const float uu = (sv - A.s4_0) * A.inv_ds4;
+            const float fl = fminf(fmaxf(floorf(uu), 0.0f), (float)(A.ntab4 - 2));
+            const int r = (int)fl;
+            d.tw = uu - fl;
+            d.ta = __ldg(reinterpret_cast<const float *>(A.t4_base + r));
+            d.tb = __ldg(reinterpret_cast<const float *>(A.t4_base + r + 1));
+        }
+        return d;
+    };
+    auto none = []() {
+        DivLoad d;
+        d.rd = d.m0 = d.m1 = d.m2 = d.ta = d.tb = d.tw = 0.0f;
+        d.ok = false;
+        d.sx = d.sy = d.sz = 1;
+        return d;
+    };
+    auto finish = [&](const DivLoad &d, float &u, float &v, float &w) {
+        if (!d.ok) {
+            u = v = w = 0.0f;
+            return;
+        }
+        const float rho0 = fmaf(d.tw, d.tb - d.ta, d.ta);
+        const float ri = 1.0f / (rho0 + d.rd);
+        u = d.sx * (d.m0 * ri);
+        v = d.sy * (d.m1 * ri);
+        w = d.sz * (d.m2 * ri);
+    };
+    // this thread's slot of a plane, and for threads 0..95 one halo slot
+    // (rows j = -1 and j = 16 across the tile, columns i = -1 and i = 32 along
+    // it; the corners are never used).  Just past the grid edge (i == nx or
+    // j == ny) the slot is the ghost neighbour of the last cell.
+    const bool own = (i < nx && j < ny);
+    const bool slot_ok = i <= nx && j <= ny && !(i == nx && j == ny);
+    const int t = ty * DIV_TX + tx;
+    int hx = -1, hy = -1;
+    if (t < 2 * DIV_TX) {
+        hx = (t % DIV_TX) + 1;
+        hy = (t < DIV_TX) ? 0 : DIV_TY + 1;
+    } else if (t < 2 * DIV_TX + 2 * DIV_TY) {
+        const int r = t - 2 * DIV_TX;
+        hy = (r % DIV_TY) + 1;
+        hx = (r < DIV_TY) ? 0 : DIV_TX + 1;
+    }
+    const int gi = blockIdx.x * DIV_TX + hx - 1, gj = blockIdx.y * DIV_TY + hy - 1;
+    const bool halo_ok = hx >= 0 && gi >= -1 && gi <= nx && gj >= -1 && gj <= ny;
+    // loads of plane kk: own slot (any kk in [-1, nz]) and halo (kk inside)
+    auto issue_own = [&](int kk) { return slot_ok ? issue(i, j, kk) : none(); };
+    auto issue_halo = [&](int kk) { return (halo_ok && kk < k1) ? issue(gi, gj, kk) : none(); };
+    // finish plane kk into buffer b; returns its u_z at this thread's cell
+    auto put = [&](int b, const DivLoad &lo, const DivLoad &lh) {
+        float u, v, w, uh, vh, wh;
+        finish(lo, u, v, w);
+        ux[b][ty + 1][tx + 1] = u;
+        uy[b][ty + 1][tx + 1] = v;
+        if (hx >= 0) {
+            finish(lh, uh, vh, wh);
+            ux[b][hy][hx] = uh;
+            uy[b][hy][hx] = vh;
+        }
+        return w;
+    };
+    float wm, w0, wp, u_, v_;
+    finish(own ? issue(i, j, k0 - 1) : none(), u_, v_, wm);
+    DivLoad lo1 = issue_own(k0), lh1 = issue_halo(k0);
+    w0 = put(0, lo1, lh1);
+    lo1 = issue_own(k0 + 1);
+    lh1 = issue_halo(k0 + 1);
+    __syncthreads();
+    for (int k = k0; k < k1; ++k) {
+        const int b = (k - k0) & 1;
+        // plane k+2's loads in flight while plane k+1 is finished
+        DivLoad lo2 = none(), lh2 = none();
+        if (k + 2 <= k1) {
+            lo2 = issue_own(k + 2);
+            lh2 = issue_halo(k + 2);
+        }
+        if (k + 1 < k1) {
+            wp = put(b ^ 1, lo1, lh1);
+        } else {
+            finish(lo1, u_, v_, wp);   // the plane above the run: only its u_z
+        }
+        if (own) {
+            const float dxu = ux[b][ty + 1][tx + 2] - ux[b][ty + 1][tx];
+            const float dyv = uy[b][ty + 2][tx + 1] - uy[b][ty][tx + 1];
+            D[((long long)k * ny + j) * nx + i] = ((dxu + dyv) + (wp - wm)) * h;
+        }
+        wm = w0;
+        w0 = wp;
+        lo1 = lo2;
+        lh1 = lh2;
+        __syncthreads();
+    }
+}
+
 int launch_divergence(ppm_ctx *c) {
     const int g = grid_for(c->ncell, 256);
     const int *b = c->bc;
-    if (c->prec == PPM_FP32_DEVIATION)
-        divergence_kernel<float, false><<<g, 256, 0, c->stream>>>(make_args<float>(c, 0), (const float *)c->state,
-                                                                  (float *)c->divg, c->ncell, c->n[0], c->n[1], c->n[2],
-                                                                  b[0], b[1], b[2], b[3], b[4], b[5]);
-    else
+    if (c->prec == PPM_FP32_DEVIATION) {
+        const dim3 grid((c->n[0] + DIV_TX - 1) / DIV_TX, (c->n[1] + DIV_TY - 1) / DIV_TY,
+                        (c->n[2] + DIV_ZRUN - 1) / DIV_ZRUN);
+        divergence_tile_kernel<<<grid, dim3(DIV_TX, DIV_TY), 0, c->stream>>>(
+            make_args<float>(c, 0), (const float *)c->state, (float *)c->divg, c->ncell, c->n[0], c->n[1], c->n[2],
+            b[0], b[1], b[2], b[3], b[4], b[5]);
+    } else
         divergence_kernel<double, true><<<g, 256, 0, c->stream>>>(make_args<double>(c, 0), (const double *)c->state,
                                                                   (double *)c->divg, c->ncell, c->n[0], c->n[1], c->n[2],
                                                                   b[0], b[1], b[2], b[3], b[4], b[5]);
