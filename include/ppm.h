@@ -190,6 +190,12 @@ int ppm_set_pass_design(ppm_ctx *ctx, int design);
 /* The current design and whether PPM_PASS_TILE applies (either may be NULL). */
 int ppm_get_pass_design(const ppm_ctx *ctx, int *design, int *tile_available);
 
+/* Device durations (ms) of the six passes X Y Z Z Y X of the most recent
+ * ppm_step, from CUDA events recorded inside the step graph between its pass
+ * launches (with the 3-D shock dissipation a pass includes its divergence
+ * kernel).  Waits for that step to finish.  ESTATE before the first step. */
+int ppm_pass_times(ppm_ctx *ctx, double ms[6]);
+
 /* Reductions of the current state to FP64 accuracy:
  * totals[7] = (M, Px, Py, Pz, E, sum rho*FV, sum FV), each times dx^3 (FP32
  * form: each thread sums its cells as float pairs with exact error terms,

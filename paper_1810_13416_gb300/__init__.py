@@ -102,6 +102,7 @@ def _load():
     lib.ppm_set_rotation.argtypes = [P, C.c_double]
     lib.ppm_set_pass_design.argtypes = [P, C.c_int]
     lib.ppm_get_pass_design.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    lib.ppm_pass_times.argtypes = [P, _DP]
     lib.ppm_diagnostics.argtypes = [P, _DP, C.c_int, C.c_double, _DP, _DP]
     lib.ppm_sync.argtypes = [P]
     lib.ppm_launch_count.argtypes = [P]
@@ -287,6 +288,12 @@ class Context:
     def set_rotation(self, domega: float):
         """Rotation increment added by each following double step (0 ends the ramp)."""
         self._check(self.lib.ppm_set_rotation(self.h, float(domega)))
+
+    def pass_times(self) -> np.ndarray:
+        """Device ms of the six passes of the last double step (waits for it)."""
+        out = np.zeros(6)
+        self._check(self.lib.ppm_pass_times(self.h, out.ctypes.data_as(_DP)))
+        return out
 
     def set_pass_design(self, design: int):
         """PASS_MARCH or PASS_TILE (FP32 four-value form, nx % 4 == 0)."""

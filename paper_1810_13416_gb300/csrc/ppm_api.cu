@@ -96,6 +96,7 @@ struct ppm_ctx {
     cudaGraph_t graph;
     cudaGraphExec_t gexec;
     cudaGraphNode_t dt_node;   // first node of the step graph (dt_kernel)
+    cudaEvent_t pev[7];        // recorded inside the step graph around its six passes
     bool have_speed;           // a valid device max speed exists for dt <= 0
     long long launches;
     int design;                // PPM_PASS_MARCH or PPM_PASS_TILE
@@ -1017,6 +1018,8 @@ int region_io(ppm_ctx *c, const int lo[3], const int hi[3], double *const *arrs,
 
 void release(ppm_ctx *c) {
     if (!c) return;
+    for (int e = 0; e < 7; ++e)
+        if (c->pev[e]) cudaEventDestroy(c->pev[e]);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->graph) cudaGraphDestroy(c->graph);
     if (c->state) cudaFree(c->state);
@@ -1241,6 +1244,18 @@ int ppm_set_pass_design(ppm_ctx *c, int design) {
     return PPM_OK;
 }
 
+int ppm_pass_times(ppm_ctx *c, double ms[6]) {
+    if (!c || !ms) return fail(c, PPM_EINVAL, "null argument");
+    if (!c->gexec || !c->pev[0]) return fail(c, PPM_ESTATE, "no double step has run yet");
+    CK(c, cudaEventSynchronize(c->pev[6]));
+    for (int s = 0; s < 6; ++s) {
+        float t = 0.0f;
+        CK(c, cudaEventElapsedTime(&t, c->pev[s], c->pev[s + 1]));
+        ms[s] = t;
+    }
+    return PPM_OK;
+}
+
 int ppm_get_pass_design(const ppm_ctx *c, int *design, int *tile_available) {
     if (!c) return PPM_EINVAL;
     if (design) *design = c->design;
@@ -1306,16 +1321,21 @@ int ppm_cfl_dt(ppm_ctx *c, double cfl, double *dt_out) {
 }
 
 static int capture_step(ppm_ctx *c) {
+    for (int e = 0; e < 7; ++e)
+        if (!c->pev[e]) CK(c, cudaEventCreate(&c->pev[e]));
     CK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     const long long before = c->launches;
     dt_kernel<<<1, 32, 0, c->stream>>>(c->ds_dev, c->dx, -1.0);
     c->launches++;
     const int order[6] = {0, 1, 2, 2, 1, 0};
     int rc = PPM_OK;
-    for (int s = 0; s < 6 && rc == PPM_OK; ++s) {
+    cudaError_t er = cudaEventRecord(c->pev[0], c->stream);
+    for (int s = 0; s < 6 && rc == PPM_OK && er == cudaSuccess; ++s) {
         const int src = (s == 2 || s == 5) ? ((c->has_heat || c->has_damp) ? 1 : 0) : 0;
         rc = launch_sweep(c, order[s], src, s == 5 ? 1 : 0);
+        if (rc == PPM_OK) er = cudaEventRecord(c->pev[s + 1], c->stream);
     }
+    if (rc == PPM_OK && er != cudaSuccess) rc = fail(c, PPM_ECUDA, "event record in capture: %s", cudaGetErrorString(er));
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);
     c->graph_kernels = c->launches - before;  // captured, not yet launched

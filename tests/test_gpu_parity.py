@@ -515,3 +515,30 @@ def test_gravity_configs_20_steps(which, precision):
         _assert_f64(qg, qo)
     else:
         _assert_f32(qg, qo)
+
+
+@pytest.mark.parametrize("design", [ppm.PASS_MARCH, ppm.PASS_TILE])
+def test_pass_times_inside_the_step(design):
+    """ppm_pass_times: ESTATE before any step; afterwards six positive pass
+    durations that add up to no more than the step itself (timed around it
+    with CUDA events on the context's stream)."""
+    p = workloads.sphere(shape=(64, 64, 64))
+    q = workloads.build(p)
+    stream = torch.cuda.Stream()
+    with ppm.Context.from_problem(p, precision=ppm.FP32_DEVIATION, stream=stream) as ctx:
+        ctx.set_pass_design(design)
+        with pytest.raises(ppm.PpmError):
+            ctx.pass_times()
+        ctx.set_state(q)
+        ctx.cfl_dt(p.cfl, fetch=False)
+        ctx.step(0.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.step(0.0)
+        e1.record(stream)
+        pt = ctx.pass_times()
+        e1.synchronize()
+        step_ms = e0.elapsed_time(e1)
+    assert pt.shape == (6,) and (pt > 0).all()
+    assert pt.sum() <= step_ms * 1.001 + 0.01
