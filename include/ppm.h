@@ -187,8 +187,21 @@ int ppm_set_rotation(ppm_ctx *ctx, double domega);
  * graph is captured again). */
 enum { PPM_PASS_MARCH = 0, PPM_PASS_TILE = 1 };
 int ppm_set_pass_design(ppm_ctx *ctx, int design);
-/* The current design and whether PPM_PASS_TILE applies (either may be NULL). */
-int ppm_get_pass_design(const ppm_ctx *ctx, int *design, int *tile_available);
+/* The same per pass axis (design[3] for the x, y, z passes). */
+int ppm_set_pass_designs(ppm_ctx *ctx, const int design[3]);
+/* The current design of each axis and whether PPM_PASS_TILE applies (either
+ * may be NULL). */
+int ppm_get_pass_design(const ppm_ctx *ctx, int design[3], int *tile_available);
+/* Autotuner of the single-box pass: when the tile form applies, times one
+ * pass of each design along each axis on the current state (a copy of the
+ * state is saved in device memory and restored after every timed pass, so
+ * the state is unchanged; ENOMEM when the copy does not fit) and keeps the
+ * faster design per axis.  cache_path (may be NULL): text file of
+ * "signature<TAB>design_x design_y design_z" lines, signature = GPU name,
+ * extents, precision, gravity kind, boundaries, sources and PPB form; a
+ * matching line is used without timing (*from_cache = 1).  Needs a valid
+ * state; the device time step must be recomputed afterwards (ppm_cfl_dt). */
+int ppm_tune(ppm_ctx *ctx, const char *cache_path, int *from_cache);
 
 /* Device durations (ms) of the six passes X Y Z Z Y X of the most recent
  * ppm_step, from CUDA events recorded inside the step graph between its pass

@@ -102,6 +102,8 @@ def _load():
     lib.ppm_set_rotation.argtypes = [P, C.c_double]
     lib.ppm_set_pass_design.argtypes = [P, C.c_int]
     lib.ppm_get_pass_design.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    lib.ppm_set_pass_designs.argtypes = [P, C.POINTER(C.c_int)]
+    lib.ppm_tune.argtypes = [P, C.c_char_p, C.POINTER(C.c_int)]
     lib.ppm_pass_times.argtypes = [P, _DP]
     lib.ppm_diagnostics.argtypes = [P, _DP, C.c_int, C.c_double, _DP, _DP]
     lib.ppm_sync.argtypes = [P]
@@ -295,21 +297,39 @@ class Context:
         self._check(self.lib.ppm_pass_times(self.h, out.ctypes.data_as(_DP)))
         return out
 
-    def set_pass_design(self, design: int):
-        """PASS_MARCH or PASS_TILE (FP32 four-value form, nx % 4 == 0)."""
-        self._check(self.lib.ppm_set_pass_design(self.h, int(design)))
+    def set_pass_design(self, design):
+        """PASS_MARCH or PASS_TILE for every axis, or a sequence of three
+        (x, y, z); PASS_TILE needs the FP32 four-value form and nx % 4 == 0."""
+        if isinstance(design, (list, tuple)):
+            d = (C.c_int * 3)(*[int(x) for x in design])
+            self._check(self.lib.ppm_set_pass_designs(self.h, d))
+        else:
+            self._check(self.lib.ppm_set_pass_design(self.h, int(design)))
+
+    def _designs(self):
+        d, a = (C.c_int * 3)(), C.c_int()
+        self._check(self.lib.ppm_get_pass_design(self.h, d, C.byref(a)))
+        return tuple(d), bool(a.value)
 
     @property
-    def pass_design(self) -> int:
-        d, a = C.c_int(), C.c_int()
-        self._check(self.lib.ppm_get_pass_design(self.h, C.byref(d), C.byref(a)))
-        return d.value
+    def pass_design(self):
+        """The design of every axis when they agree, else the (x, y, z) tuple."""
+        d, _ = self._designs()
+        return d[0] if d[0] == d[1] == d[2] else d
+
+    @property
+    def pass_designs(self) -> tuple:
+        return self._designs()[0]
 
     @property
     def tile_available(self) -> bool:
-        d, a = C.c_int(), C.c_int()
-        self._check(self.lib.ppm_get_pass_design(self.h, C.byref(d), C.byref(a)))
-        return bool(a.value)
+        return self._designs()[1]
+
+    def tune(self, cache_path: Optional[str] = None) -> bool:
+        """Autotune the pass design per axis; True when taken from the cache."""
+        fc = C.c_int()
+        self._check(self.lib.ppm_tune(self.h, cache_path.encode() if cache_path else None, C.byref(fc)))
+        return bool(fc.value)
 
     def diagnostics(self, nbins: int = 0, rmax: float = 1.0):
         tot = np.zeros(7)

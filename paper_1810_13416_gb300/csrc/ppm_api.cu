@@ -99,7 +99,7 @@ struct ppm_ctx {
     cudaEvent_t pev[7];        // recorded inside the step graph around its six passes
     bool have_speed;           // a valid device max speed exists for dt <= 0
     long long launches;
-    int design;                // PPM_PASS_MARCH or PPM_PASS_TILE
+    int design[3];             // per pass axis: PPM_PASS_MARCH or PPM_PASS_TILE
     bool tile_ok;              // the tile form applies to this context
     CUtensorMap tmap[3];       // its TMA maps of the state, one box shape per pass axis
     std::string err;
@@ -194,7 +194,7 @@ int launch_sweep(ppm_ctx *c, int axis, int sources, int cfl) {
         a.sources = sources;
         a.cfl = cfl;
         dim3 grid((a.nlane + SWEEP_BLOCK - 1) / SWEEP_BLOCK, a.nblk);
-        if (c->design == PPM_PASS_TILE && c->tile_ok)
+        if (c->design[axis] == PPM_PASS_TILE && c->tile_ok)
             launch_tile_f32(a, &c->tmap[axis], c->stream);
         else
             launch_sweep_f32(a, grid, block, c->stream);
@@ -1214,7 +1214,7 @@ int ppm_create(ppm_ctx **out, int nx, int ny, int nz, double gamma, const int bc
     }
     // the tile form of the pass: FP32 four-value state, no confining sphere
     // or shock dissipation, and rows of whole 16-byte groups for TMA
-    c->design = PPM_PASS_MARCH;
+    c->design[0] = c->design[1] = c->design[2] = PPM_PASS_MARCH;
     c->tile_ok = false;
     if (c->prec == PPM_FP32_DEVIATION && c->nmom == 3 && !(c->confine_r > 0.0) && !(c->shock_k > 0.0) &&
         nx % 4 == 0) {
@@ -1227,21 +1227,142 @@ int ppm_create(ppm_ctx **out, int nx, int ny, int nz, double gamma, const int bc
     return PPM_OK;
 }
 
-int ppm_set_pass_design(ppm_ctx *c, int design) {
-    if (!c) return PPM_EINVAL;
-    if (design != PPM_PASS_MARCH && design != PPM_PASS_TILE) return fail(c, PPM_EINVAL, "unknown pass design %d", design);
-    if (design == PPM_PASS_TILE && !c->tile_ok)
-        return fail(c, PPM_EINVAL, "the tile pass needs the FP32 four-value form, no confining sphere or shock "
-                                   "dissipation, and nx %% 4 == 0");
-    if (design != c->design) {
+int ppm_set_pass_designs(ppm_ctx *c, const int design[3]) {
+    if (!c || !design) return fail(c, PPM_EINVAL, "null argument");
+    for (int a = 0; a < 3; ++a) {
+        if (design[a] != PPM_PASS_MARCH && design[a] != PPM_PASS_TILE)
+            return fail(c, PPM_EINVAL, "unknown pass design %d (axis %d)", design[a], a);
+        if (design[a] == PPM_PASS_TILE && !c->tile_ok)
+            return fail(c, PPM_EINVAL, "the tile pass needs the FP32 four-value form, no confining sphere or shock "
+                                       "dissipation, and nx %% 4 == 0");
+    }
+    if (design[0] != c->design[0] || design[1] != c->design[1] || design[2] != c->design[2]) {
         // the step graph holds the pass kernels: capture it again
         if (c->gexec) cudaGraphExecDestroy(c->gexec);
         if (c->graph) cudaGraphDestroy(c->graph);
         c->gexec = nullptr;
         c->graph = nullptr;
-        c->design = design;
+        for (int a = 0; a < 3; ++a) c->design[a] = design[a];
     }
     return PPM_OK;
+}
+
+int ppm_set_pass_design(ppm_ctx *c, int design) {
+    const int d[3] = {design, design, design};
+    return ppm_set_pass_designs(c, d);
+}
+
+int ppm_get_pass_design(const ppm_ctx *c, int design[3], int *tile_available) {
+    if (!c) return PPM_EINVAL;
+    if (design)
+        for (int a = 0; a < 3; ++a) design[a] = c->design[a];
+    if (tile_available) *tile_available = c->tile_ok ? 1 : 0;
+    return PPM_OK;
+}
+
+// Signature of what the pass timing depends on: GPU, extents, precision,
+// gravity kind, boundaries, sources, PPB form.
+static std::string ctx_signature(const ppm_ctx *c) {
+    cudaDeviceProp prop;
+    char name[256] = "gpu";
+    if (cudaGetDeviceProperties(&prop, c->device) == cudaSuccess) snprintf(name, sizeof(name), "%s", prop.name);
+    else cudaGetLastError();
+    char buf[512];
+    snprintf(buf, sizeof(buf), "%s|%d %d %d|prec %d|grav %d|bc %d%d%d%d%d%d|src %d%d|nmom %d", name, c->n[0], c->n[1],
+             c->n[2], c->prec, c->grav, c->bc[0], c->bc[1], c->bc[2], c->bc[3], c->bc[4], c->bc[5], c->has_heat,
+             c->has_damp, c->nmom);
+    for (char *q = buf; *q; ++q)
+        if (*q == '\t' || *q == '\n') *q = ' ';
+    return buf;
+}
+
+int ppm_tune(ppm_ctx *c, const char *cache_path, int *from_cache) {
+    if (!c) return PPM_EINVAL;
+    if (from_cache) *from_cache = 0;
+    if (!c->tile_ok) return PPM_OK;   // one design applies: nothing to choose
+    const std::string key = ctx_signature(c);
+    if (cache_path) {
+        FILE *f = fopen(cache_path, "r");
+        if (f) {
+            char line[1024];
+            while (fgets(line, sizeof(line), f)) {
+                char *tab = strchr(line, '\t');
+                if (!tab) continue;
+                *tab = 0;
+                if (key != line) continue;
+                int d[3];
+                if (sscanf(tab + 1, "%d %d %d", &d[0], &d[1], &d[2]) == 3) {
+                    fclose(f);
+                    if (from_cache) *from_cache = 1;
+                    return ppm_set_pass_designs(c, d);
+                }
+            }
+            fclose(f);
+        }
+    }
+    // snapshot the state, time each design's pass along each axis on the real
+    // data (three launches, the first a warm-up), restore after every launch
+    const size_t bytes = (size_t)c->nvar * c->ncell * (c->prec == PPM_FP32_DEVIATION ? 4 : 8);
+    void *snap = nullptr;
+    if (cudaMalloc(&snap, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, PPM_ENOMEM, "the tuner needs a copy of the state (%zu bytes)", bytes);
+    }
+    int rc = PPM_OK;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    if (cudaMemcpyAsync(snap, c->state, bytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess ||
+        cudaEventCreate(&t0) != cudaSuccess || cudaEventCreate(&t1) != cudaSuccess)
+        rc = fail(c, PPM_ECUDA, "tuner set-up failed");
+    double dtc = 0.0;
+    if (rc == PPM_OK && ppm_cfl_dt(c, 0.5, &dtc) != PPM_OK)
+        rc = fail(c, PPM_ENONPHYS, "no valid state to tune on");
+    if (rc == PPM_OK) set_scalar_kernel<<<1, 32, 0, c->stream>>>(&c->ds_dev->dt, 0.5 * dtc);
+    const int saved[3] = {c->design[0], c->design[1], c->design[2]};
+    int best_d[3] = {PPM_PASS_MARCH, PPM_PASS_MARCH, PPM_PASS_MARCH};
+    for (int a = 0; a < 3 && rc == PPM_OK; ++a) {
+        float best = 1e30f;
+        for (int d = PPM_PASS_MARCH; d <= PPM_PASS_TILE && rc == PPM_OK; ++d) {
+            c->design[a] = d;
+            float ms = 0.0f;
+            for (int rep = 0; rep < 3 && rc == PPM_OK; ++rep) {
+                cudaEventRecord(t0, c->stream);
+                rc = launch_sweep(c, a, 0, 0);
+                cudaEventRecord(t1, c->stream);
+                if (rc == PPM_OK && cudaMemcpyAsync(c->state, snap, bytes, cudaMemcpyDeviceToDevice, c->stream) !=
+                                        cudaSuccess)
+                    rc = fail(c, PPM_ECUDA, "tuner restore failed");
+                if (rc == PPM_OK && cudaEventSynchronize(t1) != cudaSuccess)
+                    rc = fail(c, PPM_ECUDA, "tuner event sync failed");
+                float m = 0.0f;
+                if (rc == PPM_OK) cudaEventElapsedTime(&m, t0, t1);
+                if (rep > 0) ms += m;
+            }
+            if (rc == PPM_OK && ms < best) {
+                best = ms;
+                best_d[a] = d;
+            }
+        }
+        c->design[a] = saved[a];
+    }
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    cudaStreamSynchronize(c->stream);
+    cudaMemsetAsync(&c->ds_dev->flags, 0, sizeof(int), c->stream);
+    cudaStreamSynchronize(c->stream);
+    cudaFree(snap);
+    c->have_speed = false;
+    if (rc != PPM_OK) return rc;
+    rc = check_flags(c);
+    if (rc != PPM_OK) return rc;
+    rc = ppm_set_pass_designs(c, best_d);
+    if (rc == PPM_OK && cache_path) {
+        FILE *f = fopen(cache_path, "a");
+        if (f) {
+            fprintf(f, "%s\t%d %d %d\n", key.c_str(), best_d[0], best_d[1], best_d[2]);
+            fclose(f);
+        }
+    }
+    return rc;
 }
 
 int ppm_pass_times(ppm_ctx *c, double ms[6]) {
@@ -1256,12 +1377,6 @@ int ppm_pass_times(ppm_ctx *c, double ms[6]) {
     return PPM_OK;
 }
 
-int ppm_get_pass_design(const ppm_ctx *c, int *design, int *tile_available) {
-    if (!c) return PPM_EINVAL;
-    if (design) *design = c->design;
-    if (tile_available) *tile_available = c->tile_ok ? 1 : 0;
-    return PPM_OK;
-}
 
 int ppm_set_region(ppm_ctx *c, const int lo[3], const int hi[3], const double *const q[], int mem) {
     return region_io(c, lo, hi, const_cast<double *const *>(q), mem, true);

@@ -178,3 +178,32 @@ def test_tile_not_available_is_refused():
             with pytest.raises(ppm.PpmError):
                 ctx.set_pass_design(ppm.PASS_TILE)
             assert ctx.pass_design == ppm.PASS_MARCH
+
+
+def test_tuner_keeps_the_state_and_uses_its_cache(tmp_path):
+    """ppm_tune times both designs per axis on the live state, leaves the
+    state bit for bit as it was, picks a valid design per axis, writes the
+    cache, and a second context takes the same choice from the cache."""
+    p = workloads.sphere(shape=(64, 48, 40))
+    q = workloads.build(p)
+    cache = str(tmp_path / "tune.txt")
+    with ppm.Context.from_problem(p, precision=ppm.FP32_DEVIATION) as ctx:
+        ctx.set_state(q)
+        ctx.step(ctx.cfl_dt(0.7))
+        before = ctx.get_state()
+        assert ctx.tune(cache) is False
+        after = ctx.get_state()
+        for v in range(9):
+            assert np.array_equal(before[v], after[v]), v
+        chosen = ctx.pass_designs
+        assert all(d in (ppm.PASS_MARCH, ppm.PASS_TILE) for d in chosen)
+        ctx.step(ctx.cfl_dt(0.7))          # steps after tuning run
+    with ppm.Context.from_problem(p, precision=ppm.FP32_DEVIATION) as ctx:
+        ctx.set_state(q)
+        assert ctx.tune(cache) is True
+        assert ctx.pass_designs == chosen
+    # one design only: nothing to tune
+    with ppm.Context.from_problem(p, precision=ppm.FP64_PLAIN) as ctx:
+        ctx.set_state(q)
+        assert ctx.tune(cache) is False
+        assert ctx.pass_designs == (ppm.PASS_MARCH,) * 3
