@@ -311,6 +311,22 @@ int ppm_ensemble_sync(ppm_ens *e);
  * instead of one block per item; vec (axis 0 only): 16-byte x-pass copies for
  * boxes with nx % 8 == 0 (FP32). */
 int ppm_ensemble_set_config(ppm_ens *e, int axis, int block, int persistent, int vec);
+/* Launch mode of a double step.  PPM_ENS_PER_PASS: one launch per pass (as
+ * configured above).  PPM_ENS_ONE_LAUNCH: the six passes of every box in one
+ * launch of a resident grid taking 128-pencil items of all passes in order
+ * from a counter; an item of a box's pass waits (bounded, about a second)
+ * until that box's previous pass is complete, so the passes of different
+ * boxes overlap; results are bit for bit those of PPM_ENS_PER_PASS.  A wait
+ * that gives up makes ppm_ensemble_sync return PPM_ETIMEOUT (the states are
+ * then undefined; the context stays usable).  The step graph is then the dt
+ * kernel plus one launch. */
+enum { PPM_ENS_PER_PASS = 0, PPM_ENS_ONE_LAUNCH = 1 };
+int ppm_ensemble_set_launch_mode(ppm_ens *e, int mode);
+int ppm_ensemble_get_launch_mode(const ppm_ens *e);
+/* For tests of the failure path only: with on != 0, the first item each
+ * block takes in PPM_ENS_ONE_LAUNCH mode waits for a count that no item ever
+ * reaches, so every wait runs out and the step ends with PPM_ETIMEOUT. */
+int ppm_ensemble_set_wait_test(ppm_ens *e, int on);
 /* cfg[7] = {block_x, persistent_x, block_y, persistent_y, block_z, persistent_z, vec}. */
 int ppm_ensemble_get_config(const ppm_ens *e, int cfg[7]);
 /* Autotuner: times every configuration of each axis on the current states

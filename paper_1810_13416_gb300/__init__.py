@@ -33,6 +33,8 @@ FP64_PLAIN = 0
 FP32_DEVIATION = 1
 PASS_MARCH = 0      # one thread per pencil, register window
 PASS_TILE = 1       # cell-parallel tiles of 8 pencils x 32 cells, TMA staging
+ENS_PER_PASS = 0    # ensemble: one launch per pass
+ENS_ONE_LAUNCH = 1  # ensemble: the whole double step in one launch
 BC_PERIODIC = 0
 BC_REFLECT = 1
 GRAV_NONE = 0
@@ -125,6 +127,9 @@ def _load():
     lib.ppm_ensemble_set_config.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int]
     lib.ppm_ensemble_get_config.argtypes = [P, C.POINTER(C.c_int)]
     lib.ppm_ensemble_tune.argtypes = [P, C.c_char_p, C.POINTER(C.c_int)]
+    lib.ppm_ensemble_set_launch_mode.argtypes = [P, C.c_int]
+    lib.ppm_ensemble_get_launch_mode.argtypes = [P]
+    lib.ppm_ensemble_set_wait_test.argtypes = [P, C.c_int]
     lib.ppm_ensemble_launch_count.argtypes = [P]
     lib.ppm_ensemble_launch_count.restype = C.c_longlong
     lib.ppm_ensemble_last_error.argtypes = [P]
@@ -473,6 +478,20 @@ class Ensemble:
         path = cache_path.encode() if cache_path else None
         self._check(self.lib.ppm_ensemble_tune(self.h, path, C.byref(fc)))
         return bool(fc.value)
+
+    def set_launch_mode(self, mode: int):
+        """ENS_PER_PASS (one launch per pass) or ENS_ONE_LAUNCH (the double
+        step of every box in one launch)."""
+        self._check(self.lib.ppm_ensemble_set_launch_mode(self.h, int(mode)))
+
+    @property
+    def launch_mode(self) -> int:
+        return int(self.lib.ppm_ensemble_get_launch_mode(self.h))
+
+    def set_wait_test(self, on: bool):
+        """Tests of the failure path only: every bounded wait of the next
+        one-launch step runs out (the step ends with PPM_ETIMEOUT)."""
+        self._check(self.lib.ppm_ensemble_set_wait_test(self.h, 1 if on else 0))
 
     @property
     def launch_count(self) -> int:

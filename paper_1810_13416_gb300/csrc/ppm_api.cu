@@ -24,6 +24,10 @@ int ensemble_blocks_per_sm(int f32, int vec, int nb);
 void launch_sweep_ensemble(int f32, int vec, int nb, const void *args, const WorkItem *work, int nwork,
                            int *counter, int persistent, int grid, cudaStream_t st);
 cudaError_t prepare_tile_f32();
+cudaError_t prepare_ensemble_step();
+int ensemble_step_blocks_per_sm(int f32);
+void launch_ensemble_step(int f32, const void *args, int nbox, const WorkItem *work, int nwork, int *ticket,
+                          int *done, const int *need, int wait_test, int grid, cudaStream_t st);
 int tile_encode_map(CUtensorMap *m, void *state, int nx, int ny, int nz, int axis);
 void launch_tile_f32(const SweepArgs<float> &a, const CUtensorMap *m, cudaStream_t st);
 }  // namespace ppm
@@ -1444,11 +1448,13 @@ static int capture_step(ppm_ctx *c) {
     c->launches++;
     const int order[6] = {0, 1, 2, 2, 1, 0};
     int rc = PPM_OK;
-    cudaError_t er = cudaEventRecord(c->pev[0], c->stream);
+    // external event nodes (a plain record inside a capture would only be a
+    // dependency marker of the capture)
+    cudaError_t er = cudaEventRecordWithFlags(c->pev[0], c->stream, cudaEventRecordExternal);
     for (int s = 0; s < 6 && rc == PPM_OK && er == cudaSuccess; ++s) {
         const int src = (s == 2 || s == 5) ? ((c->has_heat || c->has_damp) ? 1 : 0) : 0;
         rc = launch_sweep(c, order[s], src, s == 5 ? 1 : 0);
-        if (rc == PPM_OK) er = cudaEventRecord(c->pev[s + 1], c->stream);
+        if (rc == PPM_OK) er = cudaEventRecordWithFlags(c->pev[s + 1], c->stream, cudaEventRecordExternal);
     }
     if (rc == PPM_OK && er != cudaSuccess) rc = fail(c, PPM_ECUDA, "event record in capture: %s", cudaGetErrorString(er));
     cudaGraph_t g = nullptr;
@@ -1618,7 +1624,13 @@ struct ppm_ens {
     WorkItem *d_work = nullptr;     // work lists, [axis][variant] slices
     int work_off[3][2] = {{0, 0}, {0, 0}, {0, 0}};
     int nwork[3][2] = {{0, 0}, {0, 0}, {0, 0}};
-    int *d_counters = nullptr;      // [6 passes][2 variants]
+    int *d_counters = nullptr;      // [6 passes][2 variants], then ticket, sentinel, done[6][nbox]
+    bool one_launch = false;        // the whole double step in one launch (besides the dt kernel)
+    int wait_test = 0;              // tests only: the first item of each block waits for nothing that comes
+    WorkItem *d_work1 = nullptr;    // one-launch work list: all passes in order, pad = pass * 2 + vec
+    int nwork1 = 0;
+    int *d_need = nullptr;          // items per (pass, box)
+    int bps1 = 1;                   // resident blocks per SM of the one-launch kernel
     DevScal **d_ds = nullptr;
     double *d_dx = nullptr;
     int cfg_nb[3] = {128, 128, 128};
@@ -1720,6 +1732,36 @@ int build_work(ppm_ens *e) {
     e->d_work = nullptr;
     ECK(e, cudaMalloc(&e->d_work, std::max<size_t>(1, all.size()) * sizeof(WorkItem)));
     ECK(e, cudaMemcpy(e->d_work, all.data(), all.size() * sizeof(WorkItem), cudaMemcpyHostToDevice));
+    // one-launch list: the six passes in order, 128-pencil blocks, longest
+    // pencils first within a pass; need[s][b] = items of pass s of box b
+    {
+        std::vector<WorkItem> list;
+        std::vector<int> need((size_t)6 * e->nbox, 0);
+        for (int s = 0; s < 6; ++s) {
+            const int a = ENS_PASS_AXIS[s];
+            std::vector<WorkItem> items;
+            for (int b = 0; b < e->nbox; ++b) {
+                const int v = ((a == 0) && e->cfg_vec && box_vec_ok(e, b)) ? 1 : 0;
+                int nlane, nblk;
+                pencils_along(e->box[b], a, &nlane, &nblk);
+                const int nlb = (nlane + 127) / 128;
+                for (int k = 0; k < nblk; ++k)
+                    for (int l = 0; l < nlb; ++l) items.push_back(WorkItem{b, l, k, s * 2 + v});
+                need[(size_t)s * e->nbox + b] = nblk * nlb;
+            }
+            std::stable_sort(items.begin(), items.end(), [&](const WorkItem &x, const WorkItem &y) {
+                return e->box[x.box]->n[a] > e->box[y.box]->n[a];
+            });
+            list.insert(list.end(), items.begin(), items.end());
+        }
+        if (e->d_work1) cudaFree(e->d_work1);
+        e->d_work1 = nullptr;
+        e->nwork1 = (int)list.size();
+        ECK(e, cudaMalloc(&e->d_work1, std::max<size_t>(1, list.size()) * sizeof(WorkItem)));
+        ECK(e, cudaMemcpy(e->d_work1, list.data(), list.size() * sizeof(WorkItem), cudaMemcpyHostToDevice));
+        if (!e->d_need) ECK(e, cudaMalloc(&e->d_need, need.size() * sizeof(int)));
+        ECK(e, cudaMemcpy(e->d_need, need.data(), need.size() * sizeof(int), cudaMemcpyHostToDevice));
+    }
     if (e->gexec) cudaGraphExecDestroy(e->gexec);
     if (e->graph) cudaGraphDestroy(e->graph);
     e->gexec = nullptr;
@@ -1749,12 +1791,29 @@ int ens_launch_pass(ppm_ens *e, int pass) {
     return PPM_OK;
 }
 
+int ens_ncounters(const ppm_ens *e) { return 14 + 6 * e->nbox; }
+
+// The whole double step of every box as one launch of the step kernel.
+int ens_launch_step(ppm_ens *e) {
+    const int f32 = e->prec == PPM_FP32_DEVIATION;
+    const int grid = std::max(1, std::min(e->nwork1, e->nsm * e->bps1));
+    int *ctr = e->d_counters + 12;
+    launch_ensemble_step(f32, e->d_args, e->nbox, e->d_work1, e->nwork1, ctr, ctr + 2, e->d_need, e->wait_test, grid,
+                         e->stream);
+    e->launches++;
+    ECK(e, cudaGetLastError());
+    return PPM_OK;
+}
+
 int ens_capture(ppm_ens *e) {
     ECK(e, cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal));
-    ens_dt_kernel<<<1, 256, 0, e->stream>>>(e->d_ds, e->d_dx, e->nbox, e->d_counters, 12, -1.0);
+    ens_dt_kernel<<<1, 256, 0, e->stream>>>(e->d_ds, e->d_dx, e->nbox, e->d_counters, ens_ncounters(e), -1.0);
     int rc = PPM_OK;
     const long long l0 = e->launches;
-    for (int s = 0; s < 6 && rc == PPM_OK; ++s) rc = ens_launch_pass(e, s);
+    if (e->one_launch)
+        rc = ens_launch_step(e);
+    else
+        for (int s = 0; s < 6 && rc == PPM_OK; ++s) rc = ens_launch_pass(e, s);
     e->launches = l0;
     cudaGraph_t g = nullptr;
     cudaError_t ce = cudaStreamEndCapture(e->stream, &g);
@@ -1773,6 +1832,7 @@ int ens_capture(ppm_ens *e) {
 }
 
 int graph_launches_per_step(const ppm_ens *e) {
+    if (e->one_launch) return 2;
     int n = 1;
     for (int s = 0; s < 6; ++s)
         for (int var = 0; var < 2; ++var) n += e->nwork[ENS_PASS_AXIS[s]][var] > 0 ? 1 : 0;
@@ -1788,6 +1848,8 @@ void ens_release(ppm_ens *e) {
     if (e->d_args) cudaFree(e->d_args);
     if (e->d_work) cudaFree(e->d_work);
     if (e->d_counters) cudaFree(e->d_counters);
+    if (e->d_work1) cudaFree(e->d_work1);
+    if (e->d_need) cudaFree(e->d_need);
     if (e->d_ds) cudaFree(e->d_ds);
     if (e->d_dx) cudaFree(e->d_dx);
     if (e->own_stream && e->stream) cudaStreamDestroy(e->stream);
@@ -1893,7 +1955,8 @@ int ppm_ensemble_create(ppm_ens **out, int nbox, const ppm_box *boxes, double ga
         hds[b] = e->box[b]->ds_dev;
         hdx[b] = e->box[b]->dx;
     }
-    if (cudaMalloc(&e->d_args, h.size()) != cudaSuccess || cudaMalloc(&e->d_counters, 12 * sizeof(int)) != cudaSuccess ||
+    if (cudaMalloc(&e->d_args, h.size()) != cudaSuccess ||
+        cudaMalloc(&e->d_counters, (size_t)(14 + 6 * nbox) * sizeof(int)) != cudaSuccess ||
         cudaMalloc(&e->d_ds, nbox * sizeof(DevScal *)) != cudaSuccess ||
         cudaMalloc(&e->d_dx, nbox * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
@@ -1904,7 +1967,8 @@ int ppm_ensemble_create(ppm_ens **out, int nbox, const ppm_box *boxes, double ga
     if (cudaMemcpy(e->d_args, h.data(), h.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(e->d_ds, hds.data(), nbox * sizeof(DevScal *), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(e->d_dx, hdx.data(), nbox * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemset(e->d_counters, 0, 12 * sizeof(int)) != cudaSuccess) {
+        cudaMemset(e->d_counters, 0, (size_t)(14 + 6 * nbox) * sizeof(int)) != cudaSuccess ||
+        prepare_ensemble_step() != cudaSuccess) {
         efail(e, PPM_ECUDA, "initialising ensemble tables failed");
         return bail(PPM_ECUDA);
     }
@@ -1915,6 +1979,7 @@ int ppm_ensemble_create(ppm_ens **out, int nbox, const ppm_box *boxes, double ga
         e->bps[0] = ensemble_blocks_per_sm(f32, 0, 64);
         e->bps[1] = ensemble_blocks_per_sm(f32, 0, 128);
         e->bps[2] = ensemble_blocks_per_sm(f32, 1, 128);
+        e->bps1 = ensemble_step_blocks_per_sm(f32);
     }
     const int rc = build_work(e);
     if (rc != PPM_OK) return bail(rc);
@@ -1967,7 +2032,7 @@ int ppm_ensemble_step(ppm_ens *e, double dt) {
     }
     DevScal **dsp = e->d_ds;
     const double *dxp = e->d_dx;
-    int nb = e->nbox, *ctr = e->d_counters, nctr = 12;
+    int nb = e->nbox, *ctr = e->d_counters, nctr = ens_ncounters(e);
     double dtu = dt > 0.0 ? dt : -1.0;
     void *args[6] = {&dsp, &dxp, &nb, &ctr, &nctr, &dtu};
     cudaKernelNodeParams kp;
@@ -1993,11 +2058,16 @@ int ppm_ensemble_diagnostics(ppm_ens *e, int b, double totals[7], double *max_ma
 
 int ppm_ensemble_sync(ppm_ens *e) {
     if (!e) return PPM_EINVAL;
+    // every box's flags are read and cleared; the first error is reported
+    int first = PPM_OK;
     for (int b = 0; b < e->nbox; ++b) {
         const int rc = ppm_sync(e->box[b]);
-        if (rc != PPM_OK) return efail(e, rc, "box %d: %s", b, e->box[b]->err.c_str());
+        if (rc != PPM_OK && first == PPM_OK) {
+            first = rc;
+            efail(e, rc, "box %d: %s", b, e->box[b]->err.c_str());
+        }
     }
-    return PPM_OK;
+    return first;
 }
 
 int ppm_ensemble_set_config(ppm_ens *e, int axis, int block, int persistent, int vec) {
@@ -2008,6 +2078,35 @@ int ppm_ensemble_set_config(ppm_ens *e, int axis, int block, int persistent, int
     e->cfg_pers[axis] = persistent ? 1 : 0;
     if (axis == 0) e->cfg_vec = vec ? 1 : 0;
     return build_work(e);
+}
+
+int ppm_ensemble_set_launch_mode(ppm_ens *e, int mode) {
+    if (!e) return PPM_EINVAL;
+    if (mode != PPM_ENS_PER_PASS && mode != PPM_ENS_ONE_LAUNCH) return efail(e, PPM_EINVAL, "unknown launch mode %d", mode);
+    if ((mode == PPM_ENS_ONE_LAUNCH) != e->one_launch) {
+        if (e->gexec) cudaGraphExecDestroy(e->gexec);
+        if (e->graph) cudaGraphDestroy(e->graph);
+        e->gexec = nullptr;
+        e->graph = nullptr;
+        e->one_launch = (mode == PPM_ENS_ONE_LAUNCH);
+    }
+    return PPM_OK;
+}
+
+int ppm_ensemble_get_launch_mode(const ppm_ens *e) {
+    return e ? (e->one_launch ? PPM_ENS_ONE_LAUNCH : PPM_ENS_PER_PASS) : PPM_EINVAL;
+}
+
+int ppm_ensemble_set_wait_test(ppm_ens *e, int on) {
+    if (!e) return PPM_EINVAL;
+    if ((on != 0) != (e->wait_test != 0)) {
+        if (e->gexec) cudaGraphExecDestroy(e->gexec);
+        if (e->graph) cudaGraphDestroy(e->graph);
+        e->gexec = nullptr;
+        e->graph = nullptr;
+        e->wait_test = on ? 1 : 0;
+    }
+    return PPM_OK;
 }
 
 int ppm_ensemble_get_config(const ppm_ens *e, int cfg[7]) {

@@ -1377,4 +1377,84 @@ __global__ void __launch_bounds__(NB, 1) sweep_ensemble_kernel(const SweepArgs<R
     }
 }
 
+// ---------------------------------------------------------------------------
+// Whole double step of an ensemble in one launch.  The work list holds the
+// items of the six passes X Y Z Z Y X of every box in pass order (item.pad =
+// pass * 2 + vec); a resident grid takes items from a ticket counter in list
+// order.  An item of pass s > 0 of box b first waits until every item of pass
+// s-1 of box b is done (done[(s-1) nbox + b] == need[...]), so the pass
+// reads a complete state; as items are handed out in list order, an item
+// only ever waits for items already held by running blocks, and the earliest
+// unfinished item has nothing to wait for.  Ordering across SMs: the block
+// that finishes an item fences and then counts it (release); the waiting
+// thread reads the count with acquire semantics and the block's loads follow
+// it through a block barrier.  Each wait is bounded: after ENS_WAIT_LIMIT
+// polls the block sets FLAG_TIMEOUT in its box's flags and leaves (every
+// item depending on it then gives up the same way), so the host reports
+// PPM_ETIMEOUT and the context stays usable.  wait_test != 0 (tests of that
+// path only): the first item of every block waits for a count that no item
+// ever reaches.
+// ---------------------------------------------------------------------------
+constexpr long long ENS_WAIT_LIMIT = 1ll << 22;   // polls of ~0.25 us: about a second
+
+__device__ __forceinline__ int ld_acquire_gpu(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+template <typename R, bool PLAIN, int NB>
+__global__ void __launch_bounds__(NB, 1) sweep_ensemble_step_kernel(const SweepArgs<R> *__restrict__ args, int nbox,
+                                                                    const WorkItem *__restrict__ work, int nwork,
+                                                                    int *ticket, int *done, const int *need,
+                                                                    int wait_test) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ SweepArgs<R> sA;
+    __shared__ int s_item, s_fail;
+    bool first = true;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_item = atomicAdd(ticket, 1);
+            s_fail = 0;
+        }
+        __syncthreads();
+        const int item = s_item;
+        if (item >= nwork) break;
+        const WorkItem w = work[item];
+        const int pass = w.pad >> 1, vec = w.pad & 1;
+        if (threadIdx.x == 0) {
+            const bool test = wait_test && first;
+            if (pass > 0 || test) {
+                const int *cnt = test ? ticket + 1 : done + (pass - 1) * nbox + w.box;
+                const int want = test ? INT_MAX : need[(pass - 1) * nbox + w.box];
+                long long it = 0;
+                while (ld_acquire_gpu(cnt) < want) {
+                    if (++it > ENS_WAIT_LIMIT) {
+                        s_fail = 1;
+                        break;
+                    }
+                    __nanosleep(256);
+                }
+            }
+            if (!s_fail) sA = args[pass * nbox + w.box];
+        }
+        first = false;
+        __syncthreads();
+        if (s_fail) {
+            if (threadIdx.x == 0) atomicOr(args[pass * nbox + w.box].flags, FLAG_TIMEOUT);
+            return;
+        }
+        if (vec) {
+            if constexpr (!PLAIN) sweep_body<R, PLAIN, true, NB>(sA, w.lane_block, w.blk, smem_raw);
+        } else {
+            sweep_body<R, PLAIN, false, NB>(sA, w.lane_block, w.blk, smem_raw);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(done + pass * nbox + w.box, 1);
+        }
+    }
+}
+
 }  // namespace ppm

@@ -56,4 +56,42 @@ void launch_sweep_ensemble(int f32, int vec, int nb, const void *args, const Wor
     }
 }
 
+// The whole-step kernel (one launch per double step): shared memory for
+// either copy path of its items.
+template <typename R, bool PLAIN>
+constexpr int step_smem_bytes() {
+    return PLAIN ? sweep_smem_bytes<R, false, 128>()
+                 : (sweep_smem_bytes<R, true, 128>() > sweep_smem_bytes<R, false, 128>() ? sweep_smem_bytes<R, true, 128>()
+                                                                                       : sweep_smem_bytes<R, false, 128>());
+}
+
+cudaError_t prepare_ensemble_step() {
+    cudaError_t e = cudaFuncSetAttribute(sweep_ensemble_step_kernel<float, false, 128>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, step_smem_bytes<float, false>());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(sweep_ensemble_step_kernel<double, true, 128>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, step_smem_bytes<double, true>());
+}
+
+int ensemble_step_blocks_per_sm(int f32) {
+    int nblk = 0;
+    if (f32)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nblk, sweep_ensemble_step_kernel<float, false, 128>, 128,
+                                                      step_smem_bytes<float, false>());
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nblk, sweep_ensemble_step_kernel<double, true, 128>, 128,
+                                                      step_smem_bytes<double, true>());
+    return nblk > 0 ? nblk : 1;
+}
+
+void launch_ensemble_step(int f32, const void *args, int nbox, const WorkItem *work, int nwork, int *ticket,
+                          int *done, const int *need, int wait_test, int grid, cudaStream_t st) {
+    if (f32)
+        sweep_ensemble_step_kernel<float, false, 128><<<grid, 128, step_smem_bytes<float, false>(), st>>>(
+            static_cast<const SweepArgs<float> *>(args), nbox, work, nwork, ticket, done, need, wait_test);
+    else
+        sweep_ensemble_step_kernel<double, true, 128><<<grid, 128, step_smem_bytes<double, true>(), st>>>(
+            static_cast<const SweepArgs<double> *>(args), nbox, work, nwork, ticket, done, need, wait_test);
+}
+
 }  // namespace ppm

@@ -131,3 +131,74 @@ def test_ensemble_step_needs_dt():
         ens.step(0.0)
     assert e.value.code == -7
     ens.close()
+
+
+def _uneven_boxes():
+    # uneven extents (one with nx not a multiple of 8) and periodic x / y
+    shapes = [(48, 32, 40), (52, 36, 44), (64, 48, 32), (40, 40, 56), (32, 24, 24), (96, 64, 48)]
+    return [workloads.strat_box(shape=s, seed=7100 + i, heat_rate=1e-3 * (i + 1)) for i, s in enumerate(shapes)]
+
+
+@pytest.mark.parametrize("precision", [ppm.FP32_DEVIATION, ppm.FP64_PLAIN])
+def test_one_launch_step_equals_per_pass_bitwise(precision):
+    """The whole double step in one launch (items of all passes from one
+    counter, each pass of a box waiting for its previous pass) gives the
+    per-pass ensemble's result bit for bit, over 4 double steps with device
+    time steps, in two launches per step (dt kernel + the step)."""
+    probs = _uneven_boxes()
+    qs = [workloads.build(p) for p in probs]
+    out = {}
+    for mode in (ppm.ENS_PER_PASS, ppm.ENS_ONE_LAUNCH):
+        ens = ppm.Ensemble(probs, precision=precision)
+        ens.set_launch_mode(mode)
+        assert ens.launch_mode == mode
+        for b, q in enumerate(qs):
+            ens.set_state(b, q)
+        ens.cfl_dt(0.7, fetch=False)
+        l0 = ens.launch_count
+        for _ in range(4):
+            ens.step(0.0)
+        ens.sync()
+        if mode == ppm.ENS_ONE_LAUNCH:
+            assert (ens.launch_count - l0) == 2 * 4
+        out[mode] = [ens.get_state(b) for b in range(len(probs))]
+        ens.close()
+    for b in range(len(probs)):
+        for v in range(9):
+            assert np.array_equal(out[ppm.ENS_PER_PASS][b][v], out[ppm.ENS_ONE_LAUNCH][b][v]), (b, v)
+
+
+def test_one_launch_wait_that_runs_out_is_reported():
+    """Every bounded wait of the step made to run out (the test option: the
+    first item of each block waits for a count that never comes): the step
+    ends with PPM_ETIMEOUT instead of hanging, and the ensemble stays usable:
+    after a fresh upload a normal step matches the per-pass result."""
+    probs = _uneven_boxes()[:3]
+    qs = [workloads.build(p) for p in probs]
+    ens = ppm.Ensemble(probs, precision=ppm.FP32_DEVIATION)
+    ens.set_launch_mode(ppm.ENS_ONE_LAUNCH)
+    for b, q in enumerate(qs):
+        ens.set_state(b, q)
+    dt = ens.cfl_dt(0.7)
+    ens.set_wait_test(True)
+    ens.step(float(np.min(dt)))
+    with pytest.raises(ppm.PpmError) as ei:
+        ens.sync()
+    assert "PPM_ETIMEOUT" in str(ei.value)
+    ens.set_wait_test(False)
+    for b, q in enumerate(qs):
+        ens.set_state(b, q)
+    ens.step(float(np.min(dt)))
+    ens.sync()
+    got = [ens.get_state(b) for b in range(len(probs))]
+    ens.close()
+    ref = ppm.Ensemble(probs, precision=ppm.FP32_DEVIATION)
+    for b, q in enumerate(qs):
+        ref.set_state(b, q)
+    ref.step(float(np.min(dt)))
+    ref.sync()
+    for b in range(len(probs)):
+        r = ref.get_state(b)
+        for v in range(9):
+            assert np.array_equal(got[b][v], r[v]), (b, v)
+    ref.close()
