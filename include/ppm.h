@@ -314,7 +314,7 @@ int ppm_ensemble_set_config(ppm_ens *e, int axis, int block, int persistent, int
 /* Launch mode of a double step.  PPM_ENS_PER_PASS: one launch per pass (as
  * configured above).  PPM_ENS_ONE_LAUNCH: the six passes of every box in one
  * launch of a resident grid taking 128-pencil items of all passes in order
- * from a counter; an item of a box's pass waits (bounded, about a second)
+ * from a counter; an item of a box's pass waits (bounded: two seconds)
  * until that box's previous pass is complete, so the passes of different
  * boxes overlap; results are bit for bit those of PPM_ENS_PER_PASS.  A wait
  * that gives up makes ppm_ensemble_sync return PPM_ETIMEOUT (the states are

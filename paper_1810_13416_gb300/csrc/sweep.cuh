@@ -1388,14 +1388,21 @@ __global__ void __launch_bounds__(NB, 1) sweep_ensemble_kernel(const SweepArgs<R
 // unfinished item has nothing to wait for.  Ordering across SMs: the block
 // that finishes an item fences and then counts it (release); the waiting
 // thread reads the count with acquire semantics and the block's loads follow
-// it through a block barrier.  Each wait is bounded: after ENS_WAIT_LIMIT
-// polls the block sets FLAG_TIMEOUT in its box's flags and leaves (every
+// it through a block barrier.  Each wait is bounded: after ENS_WAIT_NS of
+// polling the block sets FLAG_TIMEOUT in its box's flags and leaves (every
 // item depending on it then gives up the same way), so the host reports
 // PPM_ETIMEOUT and the context stays usable.  wait_test != 0 (tests of that
 // path only): the first item of every block waits for a count that no item
 // ever reaches.
 // ---------------------------------------------------------------------------
-constexpr long long ENS_WAIT_LIMIT = 1ll << 22;   // polls of ~0.25 us: about a second
+constexpr unsigned long long ENS_WAIT_NS = 2000000000ull;   // a wait gives up after 2 s
+constexpr long long ENS_WAIT_POLLS = 1ll << 26;            // and after this many polls in any case
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+    return t;
+}
 
 __device__ __forceinline__ int ld_acquire_gpu(const int *p) {
     int v;
@@ -1428,8 +1435,9 @@ __global__ void __launch_bounds__(NB, 1) sweep_ensemble_step_kernel(const SweepA
                 const int *cnt = test ? ticket + 1 : done + (pass - 1) * nbox + w.box;
                 const int want = test ? INT_MAX : need[(pass - 1) * nbox + w.box];
                 long long it = 0;
+                const unsigned long long t0 = global_ns();
                 while (ld_acquire_gpu(cnt) < want) {
-                    if (++it > ENS_WAIT_LIMIT) {
+                    if (++it > ENS_WAIT_POLLS || global_ns() - t0 > ENS_WAIT_NS) {
                         s_fail = 1;
                         break;
                     }
