@@ -486,7 +486,9 @@ def run_ours(args):
         te = max_over_ranks(e0.elapsed_time(e1) * 1e-3)
         ens.sync()
         cells = sum(b.ncell for b in boxes)
-        ens_out = {"workload": f"{len(boxes)} stratified boxes, extents 48..192 (seeded), FP32, one launch per pass",
+        mode = "one launch per double step" if ens.launch_mode == ppm.ENS_ONE_LAUNCH else "one launch per pass"
+        ens_out = {"workload": f"{len(boxes)} stratified boxes, extents 48..192 (seeded), FP32",
+                   "launch_mode": mode + " (tuned)",
                    "cells": cells, "value": 2.0 * cells * args.steps / te, "unit": UNIT,
                    "ms_per_step": 1e3 * te / args.steps, "scaling": "strong (boxes shared over ranks)",
                    "launches_per_step": (ens.launch_count - l0) / args.steps,

@@ -2132,8 +2132,10 @@ int ppm_ensemble_tune(ppm_ens *e, const char *cache_path, int *from_cache) {
                 if (!tab) continue;
                 *tab = 0;
                 if (key != line) continue;
-                int v[7];
-                if (sscanf(tab + 1, "%d %d %d %d %d %d %d", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6]) == 7) {
+                int v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                const int nv = sscanf(tab + 1, "%d %d %d %d %d %d %d %d", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5],
+                                      &v[6], &v[7]);
+                if (nv == 7 || nv == 8) {
                     fclose(f);
                     for (int a = 0; a < 3; ++a) {
                         e->cfg_nb[a] = v[2 * a];
@@ -2141,7 +2143,8 @@ int ppm_ensemble_tune(ppm_ens *e, const char *cache_path, int *from_cache) {
                     }
                     e->cfg_vec = v[6];
                     if (from_cache) *from_cache = 1;
-                    return build_work(e);
+                    const int rc = build_work(e);
+                    return rc != PPM_OK ? rc : ppm_ensemble_set_launch_mode(e, v[7] ? PPM_ENS_ONE_LAUNCH : PPM_ENS_PER_PASS);
                 }
             }
             fclose(f);
@@ -2211,6 +2214,35 @@ int ppm_ensemble_tune(ppm_ens *e, const char *cache_path, int *from_cache) {
         e->cfg_pers[a] = bpers;
         if (a == 0) e->cfg_vec = bvec;
     }
+    // launch mode: one double step per mode with that configuration (after a
+    // warm-up step), the states restored after each
+    int best_mode = e->one_launch ? PPM_ENS_ONE_LAUNCH : PPM_ENS_PER_PASS;
+    if (rc == PPM_OK) rc = build_work(e);
+    double dt_min = 0.0;
+    for (int b = 0; b < e->nbox && rc == PPM_OK; ++b) {
+        double dtb = 0.0;
+        if (ppm_cfl_dt(e->box[b], 0.5, &dtb) != PPM_OK) rc = efail(e, PPM_ENONPHYS, "box %d has no valid state to tune on", b);
+        dt_min = (b == 0 || dtb < dt_min) ? dtb : dt_min;
+    }
+    if (rc == PPM_OK) rc = copy_all(false);
+    float best_step = 1e30f;
+    for (int mode = PPM_ENS_PER_PASS; mode <= PPM_ENS_ONE_LAUNCH && rc == PPM_OK; ++mode) {
+        rc = ppm_ensemble_set_launch_mode(e, mode);
+        float ms = 0.0f;
+        for (int rep = 0; rep < 2 && rc == PPM_OK; ++rep) {
+            cudaEventRecord(t0, e->stream);
+            rc = ppm_ensemble_step(e, 0.5 * dt_min);
+            cudaEventRecord(t1, e->stream);
+            if (rc == PPM_OK) rc = copy_all(false);
+            if (rc == PPM_OK && cudaEventSynchronize(t1) != cudaSuccess) rc = efail(e, PPM_ECUDA, "event sync failed");
+            if (rc == PPM_OK && rep == 1) cudaEventElapsedTime(&ms, t0, t1);
+        }
+        if (rc == PPM_OK && ms < best_step) {
+            best_step = ms;
+            best_mode = mode;
+        }
+    }
+    if (rc == PPM_OK) rc = ppm_ensemble_set_launch_mode(e, best_mode);
     if (t0) cudaEventDestroy(t0);
     if (t1) cudaEventDestroy(t1);
     cudaStreamSynchronize(e->stream);
@@ -2224,8 +2256,8 @@ int ppm_ensemble_tune(ppm_ens *e, const char *cache_path, int *from_cache) {
     if (cache_path) {
         FILE *f = fopen(cache_path, "a");
         if (f) {
-            fprintf(f, "%s\t%d %d %d %d %d %d %d\n", key.c_str(), e->cfg_nb[0], e->cfg_pers[0], e->cfg_nb[1],
-                    e->cfg_pers[1], e->cfg_nb[2], e->cfg_pers[2], e->cfg_vec);
+            fprintf(f, "%s\t%d %d %d %d %d %d %d %d\n", key.c_str(), e->cfg_nb[0], e->cfg_pers[0], e->cfg_nb[1],
+                    e->cfg_pers[1], e->cfg_nb[2], e->cfg_pers[2], e->cfg_vec, e->one_launch ? 1 : 0);
             fclose(f);
         }
     }

@@ -184,7 +184,7 @@ def test_tuner_keeps_the_state_and_uses_its_cache(tmp_path):
     """ppm_tune times both designs per axis on the live state, leaves the
     state bit for bit as it was, picks a valid design per axis, writes the
     cache, and a second context takes the same choice from the cache."""
-    p = workloads.sphere(shape=(64, 48, 40))
+    p = workloads.sphere(shape=(44, 36, 40))
     q = workloads.build(p)
     cache = str(tmp_path / "tune.txt")
     with ppm.Context.from_problem(p, precision=ppm.FP32_DEVIATION) as ctx:
