@@ -107,6 +107,15 @@ typedef struct {
                               the face, c the mean sound speed of the traced states); mass is
                               not diffused.  0 = off; not combined with confine_r or nmom 9
                               (EINVAL). */
+    int halo_z;            /* z slab of a larger grid (domain decomposition, Sec. 4/5: a grid
+                              brick is updated from its neighbours' boundary planes): bit 0 /
+                              bit 1 = the low / high z face takes 4 halo planes from the caller
+                              (ppm_slab_halo) instead of a boundary condition; its bc entry is
+                              ignored, and a z face without halo planes must be reflecting.  The
+                              halo planes must hold the neighbouring cells' current values before
+                              each z pass, so a slab is advanced pass by pass (ppm_sweep), not by
+                              ppm_step; the grid position (z0) is the slab's global one.  Not
+                              combined with confine_r, nmom 9 or shock_k (EINVAL).  0 = off. */
 } ppm_options;
 
 /* Create a context: nx, ny, nz >= 4; gamma > 1; bc[6] per face
@@ -202,6 +211,20 @@ int ppm_get_pass_design(const ppm_ctx *ctx, int design[3], int *tile_available);
  * matching line is used without timing (*from_cache = 1).  Needs a valid
  * state; the device time step must be recomputed afterwards (ppm_cfl_dt). */
 int ppm_tune(ppm_ctx *ctx, const char *cache_path, int *from_cache);
+
+/* Halo planes of a slab context (halo_z).  ppm_slab_halo: the device buffer
+ * of the low (side 0) or high (side 1) halo planes, layout [var][plane 0..3,
+ * outward order from the slab: planes k0-4..k0-1 below, k0+nz..k0+nz+3
+ * above][ny][nx] in the context's storage format (FP32 deviations or FP64
+ * full values), and its size; EINVAL for a face without halo planes.
+ * ppm_slab_pack: copies the context's own 4 boundary planes of that side
+ * (planes 0..3 or nz-4..nz-1, same layout) into a device buffer, e.g. the
+ * neighbouring slab's halo buffer, queued on the context's stream.  Both
+ * contexts must share precision and base state; the caller orders the copy
+ * against the two contexts' streams.  These carry no arithmetic of the
+ * method: the exchange step of a decomposition into z slabs. */
+int ppm_slab_halo(ppm_ctx *ctx, int side, void **dev_ptr, size_t *bytes);
+int ppm_slab_pack(ppm_ctx *ctx, int side, void *dst_dev);
 
 /* Device durations (ms) of the six passes X Y Z Z Y X of the most recent
  * ppm_step, from CUDA events recorded inside the step graph between its pass

@@ -104,6 +104,8 @@ struct ppm_ctx {
     bool have_speed;           // a valid device max speed exists for dt <= 0
     long long launches;
     int design[3];             // per pass axis: PPM_PASS_MARCH or PPM_PASS_TILE
+    int halo_z;                // bit 0 / bit 1: the low / high z face takes halo planes
+    void *halo[2];             // their buffers: nvar x 4 planes each, storage format
     bool tile_ok;              // the tile form applies to this context
     CUtensorMap tmap[3];       // its TMA maps of the state, one box shape per pass axis
     std::string err;
@@ -154,6 +156,18 @@ SweepArgs<R> make_args(ppm_ctx *c, int axis) {
     }
     a.bc_lo = c->bc[2 * axis];
     a.bc_hi = c->bc[2 * axis + 1];
+    if (axis == 2 && c->halo_z) {
+        const long long plane = (long long)nx * ny;
+        a.halo_vs = 4 * plane;
+        if (c->halo_z & 1) {
+            a.bc_lo = BC_HALO;
+            a.halo_lo = static_cast<const R *>(c->halo[0]);
+        }
+        if (c->halo_z & 2) {
+            a.bc_hi = BC_HALO;
+            a.halo_hi = static_cast<const R *>(c->halo[1]);
+        }
+    }
     a.grav = c->grav;
     for (int d = 0; d < 3; ++d) a.org[d] = c->org[d];
     a.dx = c->dx;
@@ -1024,6 +1038,8 @@ void release(ppm_ctx *c) {
     if (!c) return;
     for (int e = 0; e < 7; ++e)
         if (c->pev[e]) cudaEventDestroy(c->pev[e]);
+    for (int h = 0; h < 2; ++h)
+        if (c->halo[h]) cudaFree(c->halo[h]);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->graph) cudaGraphDestroy(c->graph);
     if (c->state) cudaFree(c->state);
@@ -1057,6 +1073,7 @@ int ppm_create(ppm_ctx **out, int nx, int ny, int nz, double gamma, const int bc
     if (nx < 4 || ny < 4 || nz < 4) return fail(nullptr, PPM_EINVAL, "every extent must be >= 4 (got %d %d %d)", nx, ny, nz);
     if (!(gamma > 1.0)) return fail(nullptr, PPM_EINVAL, "gamma must exceed 1");
     for (int d = 0; d < 3; ++d) {
+        if (d == 2 && opt->halo_z) continue;   // z faces checked with the halo planes below
         for (int s = 0; s < 2; ++s)
             if (bc[2 * d + s] != PPM_BC_PERIODIC && bc[2 * d + s] != PPM_BC_REFLECT)
                 return fail(nullptr, PPM_EINVAL, "bad boundary kind on face %d", 2 * d + s);
@@ -1077,6 +1094,17 @@ int ppm_create(ppm_ctx **out, int nx, int ny, int nz, double gamma, const int bc
     if (nmom != 3 && nmom != 9) return fail(nullptr, PPM_EINVAL, "nmom must be 3 or 9 (got %d)", opt->nmom);
     if (nmom == 9 && opt->confine_r > 0.0)
         return fail(nullptr, PPM_EINVAL, "the ten-value PPB (nmom 9) is not combined with a confining sphere");
+    if (opt->halo_z < 0 || opt->halo_z > 3) return fail(nullptr, PPM_EINVAL, "halo_z must be 0..3");
+    if (opt->halo_z) {
+        if (opt->confine_r > 0.0 || opt->nmom == 9 || opt->shock_k > 0.0)
+            return fail(nullptr, PPM_EINVAL, "halo planes are not combined with a confining sphere, nmom 9 or "
+                                             "shock dissipation");
+        // a z face without halo planes needs a wall (a periodic pair cannot be split)
+        for (int s2 = 0; s2 < 2; ++s2)
+            if (!(opt->halo_z & (1 << s2)) && bc[4 + s2] != PPM_BC_REFLECT)
+                return fail(nullptr, PPM_EINVAL, "a z face without halo planes must be reflecting when the other "
+                                                 "takes halo planes");
+    }
     if (!(opt->shock_k >= 0.0) || !std::isfinite(opt->shock_k))
         return fail(nullptr, PPM_EINVAL, "shock_k must be finite and >= 0");
     if (opt->shock_k > 0.0 && (opt->confine_r > 0.0 || nmom == 9))
@@ -1107,6 +1135,7 @@ int ppm_create(ppm_ctx **out, int nx, int ny, int nz, double gamma, const int bc
     c->nvar = 6 + nmom;
     c->shock_k = opt->shock_k;
     c->device = opt->device;
+    c->halo_z = opt->halo_z;
 
     auto bail = [&](int code) {
         std::string m = c->err;
@@ -1137,6 +1166,14 @@ int ppm_create(ppm_ctx **out, int nx, int ny, int nz, double gamma, const int bc
         fail(c, PPM_ENOMEM, "cannot allocate %zu bytes of state", sbytes);
         return bail(PPM_ENOMEM);
     }
+    for (int h = 0; h < 2; ++h)
+        if ((c->halo_z & (1 << h)) &&
+            cudaMalloc(&c->halo[h], (size_t)c->nvar * 4 * (size_t)nx * ny * es) != cudaSuccess) {
+            cudaGetLastError();
+            c->halo[h] = nullptr;
+            fail(c, PPM_ENOMEM, "cannot allocate the halo planes");
+            return bail(PPM_ENOMEM);
+        }
     if (c->shock_k > 0.0 && cudaMalloc(&c->divg, (size_t)c->ncell * es) != cudaSuccess) {
         cudaGetLastError();
         c->divg = nullptr;
@@ -1220,8 +1257,13 @@ int ppm_create(ppm_ctx **out, int nx, int ny, int nz, double gamma, const int bc
     // or shock dissipation, and rows of whole 16-byte groups for TMA
     c->design[0] = c->design[1] = c->design[2] = PPM_PASS_MARCH;
     c->tile_ok = false;
+    for (int h = 0; h < 2; ++h)
+        if (c->halo[h] && cudaMemset(c->halo[h], 0, (size_t)c->nvar * 4 * (size_t)nx * ny * es) != cudaSuccess) {
+            fail(c, PPM_ECUDA, "initialising the halo planes failed");
+            return bail(PPM_ECUDA);
+        }
     if (c->prec == PPM_FP32_DEVIATION && c->nmom == 3 && !(c->confine_r > 0.0) && !(c->shock_k > 0.0) &&
-        nx % 4 == 0) {
+        nx % 4 == 0 && !c->halo_z) {
         bool ok = prepare_tile_f32() == cudaSuccess;
         for (int a = 0; a < 3 && ok; ++a) ok = tile_encode_map(&c->tmap[a], c->state, nx, ny, nz, a) == 0;
         if (!ok) cudaGetLastError();
@@ -1367,6 +1409,31 @@ int ppm_tune(ppm_ctx *c, const char *cache_path, int *from_cache) {
         }
     }
     return rc;
+}
+
+int ppm_slab_halo(ppm_ctx *c, int side, void **dev_ptr, size_t *bytes) {
+    if (!c || !dev_ptr) return fail(c, PPM_EINVAL, "null argument");
+    if (side < 0 || side > 1) return fail(c, PPM_EINVAL, "side must be 0 (low z) or 1 (high z)");
+    if (!(c->halo_z & (1 << side))) return fail(c, PPM_EINVAL, "this z face takes no halo planes (halo_z)");
+    *dev_ptr = c->halo[side];
+    if (bytes)
+        *bytes = (size_t)c->nvar * 4 * (size_t)c->n[0] * c->n[1] *
+                 (c->prec == PPM_FP32_DEVIATION ? sizeof(float) : sizeof(double));
+    return PPM_OK;
+}
+
+int ppm_slab_pack(ppm_ctx *c, int side, void *dst_dev) {
+    if (!c || !dst_dev) return fail(c, PPM_EINVAL, "null argument");
+    if (side < 0 || side > 1) return fail(c, PPM_EINVAL, "side must be 0 (low z) or 1 (high z)");
+    const size_t es = (c->prec == PPM_FP32_DEVIATION) ? sizeof(float) : sizeof(double);
+    const size_t plane = (size_t)c->n[0] * c->n[1];
+    const size_t k0 = side == 0 ? 0 : (size_t)c->n[2] - 4;
+    for (int v = 0; v < c->nvar; ++v) {
+        const char *src = static_cast<const char *>(c->state) + ((size_t)v * c->ncell + k0 * plane) * es;
+        char *dst = static_cast<char *>(dst_dev) + (size_t)v * 4 * plane * es;
+        CK(c, cudaMemcpyAsync(dst, src, 4 * plane * es, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    return PPM_OK;
 }
 
 int ppm_pass_times(ppm_ctx *c, double ms[6]) {

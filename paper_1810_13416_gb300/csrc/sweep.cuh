@@ -56,7 +56,9 @@ struct SweepArgs {
     long long s_axis, s_lane, s_blk;  // element strides
     int lane_dim, blk_dim;            // physical axis of lane / block index
     int axis;
-    int bc_lo, bc_hi;     // 0 periodic, 1 reflect (along the pass)
+    int bc_lo, bc_hi;     // 0 periodic, 1 reflect, 2 halo planes from halo_lo / halo_hi (along the pass)
+    const R *halo_lo, *halo_hi;   // BC_HALO sides: 4 ghost planes, [var][plane 0..3][pencil offset]
+    long long halo_vs;            // their variable stride (4 x cells per plane)
     int grav;             // 0 none, 1 plane z, 2 central
     double org[3];
     double dx;
@@ -289,10 +291,14 @@ __device__ __forceinline__ int map_cell(int i, int n, int bl, int bh, bool &flip
     flip = true;
     return 2 * n - 1 - k;
 }
-// Position (cells from the low end) of face j+1/2 after the same mapping.
+constexpr int BC_HALO = 2;   // ghost cells come from caller-supplied halo planes
+
+// Position (cells from the low end) of face j+1/2 after the same mapping
+// (faces beyond a halo side keep their own position).
 __device__ __forceinline__ int map_face(int j, int n, int bl, int bh) {
     const int P = j + 1;
     if (P >= 0 && P <= n) return (P == n && bh == 0) ? 0 : P;
+    if ((P < 0 && bl == BC_HALO) || (P > n && bh == BC_HALO)) return P;
     if ((P < 0 && bl == 0) || (P > n && bh == 0)) {
         const int k = P % n;
         return k < 0 ? k + n : k;
@@ -416,7 +422,11 @@ constexpr int SWEEP_UNROLL = PPM_SWEEP_UNROLL;  // unroll factor of the march lo
 // stored values per cell), with a purely local parabola along the pass.
 // DISS: 3-D shock dissipation (momentum and E' diffuse across faces where the
 // cell velocity divergence marks a shock).
-template <typename R, bool PLAIN, bool VEC, int NB, bool CONF = false, bool TEN = false, bool DISS = false>
+// HALO: the pass along z of a slab of a larger grid, a side with bc BC_HALO
+// taking its 4 ghost planes from A.halo_lo / A.halo_hi (no wall there, ghost
+// cells at their own position).
+template <typename R, bool PLAIN, bool VEC, int NB, bool CONF = false, bool TEN = false, bool DISS = false,
+          bool HALO = false>
 __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block, int blk,
                                            unsigned char *smem_raw) {
     constexpr int SWEEP_NB = NB;
@@ -570,10 +580,21 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
     };
     auto xcell32 = [&](int mm) { return orgf + ((float)(i0 + mm) + 0.5f) * dxf; };
     auto xface32 = [&](int j) { return orgf + (float)(i0 + map_face(j, n, bcl, bch)) * dxf; };
+    // a cell beyond a halo side is its own ghost (no wrap, no mirror)
+    auto halo_cell = [&](int cc) {
+        return HALO && ((cc < 0 && bcl == BC_HALO) || (cc >= n && bch == BC_HALO));
+    };
+    auto mapc = [&](int cc, bool &fl) -> int {
+        if (halo_cell(cc)) {
+            fl = false;
+            return cc;
+        }
+        return map_cell(cc, n, bcl, bch, fl);
+    };
     TabFetch cell_next, face_next;
     if constexpr (F32) {
         bool fl0;
-        cell_next = tab_issue(xcell32(map_cell(-G, n, bcl, bch, fl0)));
+        cell_next = tab_issue(xcell32(mapc(-G, fl0)));
         face_next = tab_issue(xface32(-G - 3));
     }
 
@@ -591,7 +612,15 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
     auto vslot = [](int g) { return VSLOT == 4 ? (g & 3) : (g % VSLOT); };
     float *outv = reinterpret_cast<float *>(smem_raw) + VSLOT * NV * SWEEP_NB * 4;
     auto fetch = [&](int cf) {
-        if (cf < n) {
+        if (HALO && halo_cell(cf) && cf < n + G) {
+            // ghost plane of a halo side: [var][plane][pencil offset]
+            const R *hb = (cf < 0) ? A.halo_lo + (long long)(cf + G) * sa : A.halo_hi + (long long)(cf - n) * sa;
+            const R *src = hb + (long long)lane * A.s_lane + (long long)blk * A.s_blk;
+            R *dst = ring + ((cf + G) & (RING - 1)) * NV * SWEEP_NB + tid;
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+                cp_async<(int)sizeof(R)>(dst + v * SWEEP_NB, src + voff(v) / vs * A.halo_vs);
+        } else if (cf < n) {
             bool fl;
             const int mm = map_cell(cf, n, bcl, bch, fl);
             const R *src = q + (long long)mm * sa;
@@ -675,8 +704,8 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
         }
         R raw[NV];
         bool flip = false;
-        const int m = map_cell(c, n, bcl, bch, flip);
-        if (c >= n) {
+        const int m = mapc(c, flip);
+        if (c >= n && !halo_cell(c)) {
             const int si = m - stash_lo;
 #pragma unroll
             for (int v = 0; v < NV; ++v) raw[v] = stash[si][v];
@@ -707,7 +736,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
             b_p0 = bb.y;
             b_g = bb.z;
             bool fln;
-            cell_next = tab_issue(xcell32(map_cell(c + 1, n, bcl, bch, fln)));
+            cell_next = tab_issue(xcell32(mapc(c + 1, fln)));
         } else {
             R cx, cy, cz;
             point(coord(A, ax, i0 + m), cx, cy, cz);
@@ -1334,10 +1363,10 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
 // NB: threads per block (the ten-value x pass uses 64, so that two blocks
 // with their 16-byte rings fit in shared memory).
 template <typename R, bool PLAIN, bool VEC, bool CONF = false, bool TEN = false, bool DISS = false,
-          int NB = SWEEP_NB>
+          int NB = SWEEP_NB, bool HALO = false>
 __global__ void __launch_bounds__(NB, PPM_SWEEP_MINB) sweep_kernel(const SweepArgs<R> A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    sweep_body<R, PLAIN, VEC, NB, CONF, TEN, DISS>(A, blockIdx.x, blockIdx.y, smem_raw);
+    sweep_body<R, PLAIN, VEC, NB, CONF, TEN, DISS, HALO>(A, blockIdx.x, blockIdx.y, smem_raw);
 }
 
 // ---------------------------------------------------------------------------

@@ -26,12 +26,19 @@ cudaError_t prepare_sweep_f32() {
     e = cudaFuncSetAttribute(sweep_kernel<float, false, true, false, true, false, TEN_VEC_NB>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, sweep_smem_bytes<float, true, TEN_VEC_NB, 15>());
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(sweep_kernel<float, false, false, false, false, false, SWEEP_NB, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, sweep_smem_bytes<float, false>());
+    if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(sweep_kernel<float, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 sweep_smem_bytes<float, false>());
 }
 
 void launch_sweep_f32(const SweepArgs<float> &a, dim3 grid, dim3 block, cudaStream_t st) {
-    if (a.divg) {
+    if (a.halo_lo || a.halo_hi) {
+        // z pass of a slab with halo planes (no other feature combines with it)
+        sweep_kernel<float, false, false, false, false, false, SWEEP_NB, true>
+            <<<grid, block, sweep_smem_bytes<float, false>(), st>>>(a);
+    } else if (a.divg) {
         if (a.vec_x)
             sweep_kernel<float, false, true, false, false, true><<<grid, block, sweep_smem_bytes<float, true>(), st>>>(a);
         else

@@ -13,12 +13,18 @@ cudaError_t prepare_sweep_f64() {
     e = cudaFuncSetAttribute(sweep_kernel<double, true, false, false, false, true>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, sweep_smem_bytes<double, false>());
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(sweep_kernel<double, true, false, false, false, false, SWEEP_NB, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, sweep_smem_bytes<double, false>());
+    if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(sweep_kernel<double, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 sweep_smem_bytes<double, false>());
 }
 
 void launch_sweep_f64(const SweepArgs<double> &a, dim3 grid, dim3 block, cudaStream_t st) {
-    if (a.divg)
+    if (a.halo_lo || a.halo_hi)
+        sweep_kernel<double, true, false, false, false, false, SWEEP_NB, true>
+            <<<grid, block, sweep_smem_bytes<double, false>(), st>>>(a);
+    else if (a.divg)
         sweep_kernel<double, true, false, false, false, true><<<grid, block, sweep_smem_bytes<double, false>(), st>>>(a);
     else if (a.ten)
         sweep_kernel<double, true, false, false, true>
