@@ -114,8 +114,12 @@ typedef struct {
                               ignored, and a z face without halo planes must be reflecting.  The
                               halo planes must hold the neighbouring cells' current values before
                               each z pass, so a slab is advanced pass by pass (ppm_sweep), not by
-                              ppm_step; the grid position (z0) is the slab's global one.  Not
+                              ppm_step; give z0 of the whole grid and the slab's z_index0.  Not
                               combined with confine_r, nmom 9 or shock_k (EINVAL).  0 = off. */
+    int z_index0;          /* global index of the context's first z plane: cell centres are at
+                              z0 + (z_index0 + k + 1/2) dx, so that a slab whose z0 is the
+                              global grid's computes every position exactly as the whole grid
+                              does (bit-equal base states); 0 for a whole grid. */
 } ppm_options;
 
 /* Create a context: nx, ny, nz >= 4; gamma > 1; bc[6] per face

@@ -65,7 +65,7 @@ class _Options(C.Structure):
     _fields_ = [("x0", C.c_double), ("y0", C.c_double), ("z0", C.c_double), ("dx", C.c_double),
                 ("precision", C.c_int), ("heat", _DP), ("damp", _DP), ("stream", C.c_void_p),
                 ("device", C.c_int), ("confine_r", C.c_double), ("nmom", C.c_int),
-                ("shock_k", C.c_double), ("halo_z", C.c_int)]
+                ("shock_k", C.c_double), ("halo_z", C.c_int), ("z_index0", C.c_int)]
 
 
 class _Box(C.Structure):
@@ -157,7 +157,7 @@ class Context:
     def __init__(self, shape, gamma: float, bc: Sequence[int], grav_kind: int, s0: float, ds: float,
                  rho0, p0, g, origin=(0.0, 0.0, 0.0), dx: float = 1.0, precision: int = FP32_DEVIATION,
                  heat=None, damp=None, stream=None, device: int = 0, confine_r: float = 0.0,
-                 nmom: int = 3, shock_k: float = 0.0, halo_z: int = 0):
+                 nmom: int = 3, shock_k: float = 0.0, halo_z: int = 0, z_index0: int = 0):
         self.lib = _load()
         self.shape = tuple(int(v) for v in shape)
         self._keep = [_f64(rho0), _f64(p0), _f64(g)]
@@ -175,7 +175,8 @@ class Context:
         if stream is not None:
             sptr = int(getattr(stream, "cuda_stream", stream))
         opt = _Options(float(origin[0]), float(origin[1]), float(origin[2]), float(dx), int(precision),
-                       hp, dp, sptr, int(device), float(confine_r), int(nmom), float(shock_k), int(halo_z))
+                       hp, dp, sptr, int(device), float(confine_r), int(nmom), float(shock_k), int(halo_z),
+                       int(z_index0))
         h = C.c_void_p()
         rc = self.lib.ppm_create(C.byref(h), self.shape[0], self.shape[1], self.shape[2], float(gamma),
                                  (C.c_int * 6)(*[int(b) for b in bc]), C.byref(gr), C.byref(opt))
@@ -190,14 +191,15 @@ class Context:
     def slab(cls, p, k0: int, nzl: int, halo_z: int, precision: int = FP32_DEVIATION, stream=None,
              device: int = 0):
         """The z slab of planes [k0, k0 + nzl) of problem p, as its own
-        context: z origin at the slab's global position; halo_z bit 0 / bit 1
-        = its low / high z face takes halo planes (ppm_slab_halo)."""
+        context: the whole grid's origin with the slab's global z index k0
+        (so positions are computed exactly as on the whole grid); halo_z
+        bit 0 / bit 1 = its low / high z face takes halo planes (ppm_slab_halo)."""
         t = p.tables
-        origin = (p.origin[0], p.origin[1], p.origin[2] + k0 * p.dx)
         shape = (p.shape[0], p.shape[1], int(nzl))
-        return cls(shape, p.gamma, p.bc, p.grav, t.s0, t.ds, t.rho0, t.p0, t.g, origin=origin,
+        return cls(shape, p.gamma, p.bc, p.grav, t.s0, t.ds, t.rho0, t.p0, t.g, origin=p.origin,
                    dx=p.dx, precision=precision, heat=getattr(t, "heat", None),
-                   damp=getattr(t, "damp", None), stream=stream, device=device, halo_z=int(halo_z))
+                   damp=getattr(t, "damp", None), stream=stream, device=device, halo_z=int(halo_z),
+                   z_index0=int(k0))
 
     def slab_halo(self, side: int):
         """(device address, bytes) of the low (0) or high (1) halo planes."""

@@ -105,6 +105,7 @@ struct ppm_ctx {
     long long launches;
     int design[3];             // per pass axis: PPM_PASS_MARCH or PPM_PASS_TILE
     int halo_z;                // bit 0 / bit 1: the low / high z face takes halo planes
+    int z_index0;              // global index of plane 0 (slab of a larger grid)
     void *halo[2];             // their buffers: nvar x 4 planes each, storage format
     bool tile_ok;              // the tile form applies to this context
     CUtensorMap tmap[3];       // its TMA maps of the state, one box shape per pass axis
@@ -170,6 +171,8 @@ SweepArgs<R> make_args(ppm_ctx *c, int axis) {
     }
     a.grav = c->grav;
     for (int d = 0; d < 3; ++d) a.org[d] = c->org[d];
+    a.ioff[0] = a.ioff[1] = 0;
+    a.ioff[2] = c->z_index0;
     a.dx = c->dx;
     const R *t = std::is_same<R, float>::value ? (const R *)c->t32 : (const R *)c->t64;
     a.t_rho0 = t;
@@ -1136,6 +1139,7 @@ int ppm_create(ppm_ctx **out, int nx, int ny, int nz, double gamma, const int bc
     c->shock_k = opt->shock_k;
     c->device = opt->device;
     c->halo_z = opt->halo_z;
+    c->z_index0 = opt->z_index0;
 
     auto bail = [&](int code) {
         std::string m = c->err;

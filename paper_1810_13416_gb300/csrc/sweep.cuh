@@ -61,6 +61,7 @@ struct SweepArgs {
     long long halo_vs;            // their variable stride (4 x cells per plane)
     int grav;             // 0 none, 1 plane z, 2 central
     double org[3];
+    int ioff[3];          // global index of cell 0 along each axis (a slab of a larger grid; else 0)
     double dx;
     // tables in precision R (FP64 plain: the FP64 tables themselves)
     const R *t_rho0, *t_p0, *t_g, *t_heat, *t_damp;
@@ -181,7 +182,7 @@ __device__ __forceinline__ BaseAx<R> base_along(const SweepArgs<R> &A, R x, R y,
 
 template <typename R>
 __device__ __forceinline__ R coord(const SweepArgs<R> &A, int d, int idx) {
-    return xadd((R)A.org[d], xmul(xadd((R)idx, (R)0.5), (R)A.dx));
+    return xadd((R)A.org[d], xmul(xadd((R)(idx + A.ioff[d]), (R)0.5), (R)A.dx));
 }
 
 // ---------------------------------------------------------------------------
@@ -578,8 +579,9 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
         if (A.grav == 2) r.z *= t.xa;  // (g/r) * x_axis
         return r;
     };
-    auto xcell32 = [&](int mm) { return orgf + ((float)(i0 + mm) + 0.5f) * dxf; };
-    auto xface32 = [&](int j) { return orgf + (float)(i0 + map_face(j, n, bcl, bch)) * dxf; };
+    const int io = A.ioff[ax];
+    auto xcell32 = [&](int mm) { return orgf + ((float)(i0 + io + mm) + 0.5f) * dxf; };
+    auto xface32 = [&](int j) { return orgf + (float)(i0 + io + map_face(j, n, bcl, bch)) * dxf; };
     // a cell beyond a halo side is its own ghost (no wrap, no mirror)
     auto halo_cell = [&](int cc) {
         return HALO && ((cc < 0 && bcl == BC_HALO) || (cc >= n && bch == BC_HALO));
@@ -902,7 +904,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
                 p0 = bf.y;
                 face_next = tab_issue(xface32(j + 1));
             } else {
-                const R xf = xadd(lo, xmul((R)(i0 + map_face(j, n, bcl, bch)), (R)A.dx));
+                const R xf = xadd(lo, xmul((R)(i0 + io + map_face(j, n, bcl, bch)), (R)A.dx));
                 R fx, fy, fz;
                 point(xf, fx, fy, fz);
                 const BaseAx<R> bf = base_along(A, fx, fy, fz, ax);
