@@ -23,6 +23,8 @@ three vanish, so the rest-state pins cannot see them.  These pins can:
   +z), for any state, pass by pass.  In the scheme this holds only when the
   energy source has the sign and the time-centred mass flux it has.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -140,3 +142,69 @@ def test_energy_plus_potential_energy_conserved(axis_order):
     # the state is far from rest: both changes are well above rounding
     assert abs(dE) > 1e-6 * abs(E0)
     assert abs(dE - g * dZ) <= 1e-9 * abs(dE)
+
+
+def _isothermal_layer(nx, nz, lx=2.0, lz=1.0, gamma=5.0 / 3.0):
+    """Isothermal layer rho0 = p0 = exp(-z) under g = -1 (scale height 1),
+    periodic in x and y, rigid lids at z = 0 and z = lz."""
+    dz = lz / nz
+    ds = dz / 16.0
+    s = np.arange(-8 * 16, (nz + 8) * 16 + 1) * ds
+    tab = workloads.Tables(s0=float(s[0]), ds=ds, rho0=np.exp(-s), p0=np.exp(-s), g=-np.ones_like(s))
+    return workloads.Problem("isothermal_layer", (nx, 4, nz), (0.0, 0.0, 0.0), dz, gamma,
+                             (0, 0, 0, 0, 1, 1), workloads.GRAV_PLANE_Z, tab, cfl=0.7)
+
+
+def test_internal_gravity_wave_frequency():
+    """A standing internal gravity wave (k_x = pi over x in [0, 2], the
+    first vertical mode between the lids) oscillates at the gravity branch of
+    the exact dispersion relation of an isothermal atmosphere,
+    w^4 - w^2 c^2 (k^2 + 1/(4 H^2)) + N^2 c^2 k_x^2 = 0, with N^2 = (g/H)(1 - 1/gamma):
+    w = 0.4457 here (measured 0.4452 from the zero crossings of the mode's
+    momentum; bound 1%).
+    Without the buoyancy (or with its sign reversed) there is no such
+    oscillation; a wrong factor shifts the frequency."""
+    nx, nz = 64, 32
+    p = _isothermal_layer(nx, nz)
+    gam, g0, H = p.gamma, 1.0, 1.0
+    kx, kz = math.pi, math.pi
+    c2 = gam * g0 * H
+    N2 = (g0 / H) * (1.0 - 1.0 / gam)
+    bq = c2 * (kx * kx + kz * kz + 0.25 / H ** 2)
+    w_exact = math.sqrt(0.5 * (bq - math.sqrt(bq * bq - 4.0 * N2 * c2 * kx * kx)))
+    # the gravity mode's velocity (anelastic form of its eigenvector), rho' = p' = 0
+    x = (np.arange(nx) + 0.5) * p.dx
+    z = (np.arange(nz) + 0.5) * p.dx
+    Z, X = np.meshgrid(z, x, indexing="ij")
+    rho0 = np.exp(-Z)
+    amp = 1e-4
+    mw = amp * np.exp(-0.5 * Z) * np.sin(kz * Z) * np.cos(kx * X)                  # rho0 w
+    mu = -amp / kx * np.sin(kx * X) * np.exp(-0.5 * Z) * (kz * np.cos(kz * Z) - 0.5 * np.sin(kz * Z))
+    q = [np.zeros((nz, 4, nx)) for _ in range(9)]
+    q[0][:] = rho0[:, None, :]
+    q[1][:] = mu[:, None, :]
+    q[3][:] = mw[:, None, :]
+    q[4][:] = (np.exp(-Z) / (gam - 1.0) + 0.5 * (mu ** 2 + mw ** 2) / rho0)[:, None, :]
+    shape_w = (np.sin(kz * Z) * np.cos(kx * X) * np.exp(-0.5 * Z))[:, None, :]
+    o = oracle.Oracle(p)
+    dt = 0.5 * o.cfl_dt(q, 0.7)
+    t, ts, P = 0.0, [0.0], [float((q[3] * shape_w).sum())]
+    while t < 1.7 * math.pi / w_exact:
+        o.double_step(q, dt)
+        t += 2.0 * dt
+        ts.append(t)
+        P.append(float((q[3] * shape_w).sum()))
+    ts, P = np.array(ts), np.array(P)
+    # the sound waves the start also excites are fast (period ~1) and small:
+    # smooth over one of their periods, then take the zero crossings
+    k = max(1, int(round(2.0 * math.pi / math.sqrt(bq) / (2.0 * dt))))
+    Ps = np.convolve(P, np.ones(k) / k, mode="valid")
+    tsm = np.convolve(ts, np.ones(k) / k, mode="valid")
+    sgn = np.sign(Ps)
+    idx = np.where(sgn[1:] * sgn[:-1] < 0)[0]
+    assert len(idx) >= 2, "no oscillation"
+    tz = [tsm[i] - Ps[i] * (tsm[i + 1] - tsm[i]) / (Ps[i + 1] - Ps[i]) for i in idx[:2]]
+    w_meas = math.pi / (tz[1] - tz[0])
+    assert abs(w_meas - w_exact) <= 0.01 * w_exact, (w_meas, w_exact)
+    # and it stays a small oscillation (no growth)
+    assert np.abs(P).max() <= 1.5 * abs(P[0])
