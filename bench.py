@@ -37,6 +37,7 @@ METRIC = "cell-updates/s per 3-D step"
 UNIT = "cell-updates/s"
 BYTES_PER_CELL_PASS = {"f32": 72, "f64": 144}   # 9 values read + written per pass
 SWEEP_SRC = os.path.join(ROOT, "paper_1810_13416_gb300", "csrc", "sweep.cuh")
+TILE_SRC = os.path.join(ROOT, "paper_1810_13416_gb300", "csrc", "tile.cuh")
 TRAFFIC_JSON = os.path.join(ROOT, "profiles", "sweep_traffic.json")
 FP32_LANES_PER_SM = 128
 
@@ -51,26 +52,34 @@ def _peaks():
 
 
 def _src_hash() -> str:
-    """Hash of the FP32 pass as compiled: its source and its nvcc flags."""
+    """Hash of the FP32 passes as compiled: the sources of both designs and
+    their nvcc flags."""
     import importlib
     _b = importlib.import_module("paper_1810_13416_gb300.build")
-    with open(SWEEP_SRC, "rb") as f:
-        src = f.read()
-    return hashlib.sha256(src + repr(_b.UNIT_FLAGS.get("sweep_f32")).encode()).hexdigest()[:16]
+    src = b""
+    for path in (SWEEP_SRC, TILE_SRC):
+        with open(path, "rb") as f:
+            src += f.read()
+    flags = repr((_b.UNIT_FLAGS.get("sweep_f32"), _b.UNIT_FLAGS.get("tile_f32")))
+    return hashlib.sha256(src + flags.encode()).hexdigest()[:16]
 
 
-def _traffic_per_cell(prec: str):
-    """DRAM bytes per cell and pass of the sweep kernel, averaged over the six
-    passes of a double step (two x passes, four y/z passes), from the
-    committed ncu summary; None when absent or taken on another kernel source."""
+def _traffic_per_cell(prec: str, designs):
+    """DRAM bytes per cell and pass of the pass kernels the step runs (design
+    per axis), averaged over the six passes of a double step (two x passes,
+    four y/z passes), from the committed ncu summary; None when absent or
+    taken on another kernel source."""
     try:
         with open(TRAFFIC_JSON) as f:
             d = json.load(f)
         e = d[prec]
-        if e.get("sweep_src_sha256_16") != _src_hash():
+        if e.get("src_sha256_16") != _src_hash():
             return None
-        b = e["dram_bytes_per_cell_pass"]
-        return (2.0 * float(b["x"]) + 4.0 * float(b["yz"])) / 6.0
+        name = lambda dd: "tile" if dd == 1 else "march"
+        bx = float(e["dram_bytes_per_cell_pass"][name(designs[0])]["x"])
+        by = float(e["dram_bytes_per_cell_pass"][name(designs[1])]["yz"])
+        bz = float(e["dram_bytes_per_cell_pass"][name(designs[2])]["yz"])
+        return (2.0 * bx + 2.0 * by + 2.0 * bz) / 6.0
     except Exception:
         return None
 
@@ -319,7 +328,7 @@ def run_ours(args):
     # the events recorded between the passes inside every timed step.
     pass_s = float(pr.mean()) * 1e-3
     achieved = BYTES_PER_CELL_PASS["f32"] * ncell / pass_s / 1e9
-    tr = _traffic_per_cell("f32")
+    tr = _traffic_per_cell("f32", ctx.pass_designs)
     flops_cell = args.flops_per_cell
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     alu_peak = n_sm * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12

@@ -722,17 +722,35 @@ __global__ void __launch_bounds__(DIV_TX * DIV_TY) divergence_tile_kernel(SweepA
     const int k0 = blockIdx.z * DIV_ZRUN, k1 = min(nz, k0 + DIV_ZRUN);
     const float h = (float)(0.5 / A.dx);
     const float ox = (float)A.org[0], oy = (float)A.org[1], oz = (float)A.org[2], dxf = (float)A.dx;
-    // loads of cell (gi, gj, gk), mapped onto the grid when it is a ghost
-    auto issue = [&](int gi, int gj, int gk) -> DivLoad {
-        DivLoad d;
-        bool fx = false, fy = false, fz = false;
+    // A column (x-y position) of the march: mapped indices, mirror signs and
+    // position, fixed for the whole run of planes
+    struct Col {
+        long long xy;     // x-y offset of the mapped cell in a plane
+        float x2y2;       // x^2 + y^2 of the mapped cell (central gravity)
+        signed char sx, sy;
+    };
+    auto column = [&](int gi, int gj) -> Col {
+        Col c;
+        bool fx = false, fy = false;
         const int ii = map_cell(gi, nx, bx0, bx1, fx), jj = map_cell(gj, ny, by0, by1, fy);
+        c.xy = (long long)jj * nx + ii;
+        const float x = ox + ((float)ii + 0.5f) * dxf, y = oy + ((float)jj + 0.5f) * dxf;
+        c.x2y2 = fmaf(y, y, x * x);
+        c.sx = fx ? -1 : 1;
+        c.sy = fy ? -1 : 1;
+        return c;
+    };
+    const long long plane_cells = (long long)nx * ny;
+    // loads of the cell of column cl in plane gk (mapped onto the grid when a ghost)
+    auto issue = [&](const Col &cl, int gk) -> DivLoad {
+        DivLoad d;
+        bool fz = false;
         const int kk = map_cell(gk, nz, bz0, bz1, fz);
-        d.sx = fx ? -1 : 1;
-        d.sy = fy ? -1 : 1;
+        d.sx = cl.sx;
+        d.sy = cl.sy;
         d.sz = fz ? -1 : 1;
         d.ok = true;
-        const long long cc = ((long long)kk * ny + jj) * nx + ii;
+        const long long cc = (long long)kk * plane_cells + cl.xy;
         d.rd = __ldg(st + cc);
         d.m0 = __ldg(st + ncell + cc);
         d.m1 = __ldg(st + 2 * ncell + cc);
@@ -740,14 +758,8 @@ __global__ void __launch_bounds__(DIV_TX * DIV_TY) divergence_tile_kernel(SweepA
         d.ta = d.tb = (float)A.rho0_c;
         d.tw = 0.0f;
         if (A.grav != 0) {
-            float sv;
-            if (A.grav == 1) {
-                sv = oz + ((float)kk + 0.5f) * dxf;
-            } else {
-                const float x = ox + ((float)ii + 0.5f) * dxf, y = oy + ((float)jj + 0.5f) * dxf;
-                const float z = oz + ((float)kk + 0.5f) * dxf;
-                sv = fmaf(z, z, fmaf(y, y, x * x));
-            }
+            const float z = oz + ((float)kk + 0.5f) * dxf;
+            const float sv = (A.grav == 1) ? z : fmaf(z, z, cl.x2y2);
             const float uu = (sv - A.s4_0) * A.inv_ds4;
             const float fl = fminf(fmaxf(floorf(uu), 0.0f), (float)(A.ntab4 - 2));
             const int r = (int)fl;
@@ -794,8 +806,10 @@ __global__ void __launch_bounds__(DIV_TX * DIV_TY) divergence_tile_kernel(SweepA
     const int gi = blockIdx.x * DIV_TX + hx - 1, gj = blockIdx.y * DIV_TY + hy - 1;
     const bool halo_ok = hx >= 0 && gi >= -1 && gi <= nx && gj >= -1 && gj <= ny;
     // loads of plane kk: own slot (any kk in [-1, nz]) and halo (kk inside)
-    auto issue_own = [&](int kk) { return slot_ok ? issue(i, j, kk) : none(); };
-    auto issue_halo = [&](int kk) { return (halo_ok && kk < k1) ? issue(gi, gj, kk) : none(); };
+    const Col col_own = column(slot_ok ? i : 0, slot_ok ? j : 0);
+    const Col col_halo = column(halo_ok ? gi : 0, halo_ok ? gj : 0);
+    auto issue_own = [&](int kk) { return slot_ok ? issue(col_own, kk) : none(); };
+    auto issue_halo = [&](int kk) { return (halo_ok && kk < k1) ? issue(col_halo, kk) : none(); };
     // finish plane kk into buffer b; returns its u_z at this thread's cell
     auto put = [&](int b, const DivLoad &lo, const DivLoad &lh) {
         float u, v, w, uh, vh, wh;
@@ -810,7 +824,7 @@ __global__ void __launch_bounds__(DIV_TX * DIV_TY) divergence_tile_kernel(SweepA
         return w;
     };
     float wm, w0, wp, u_, v_;
-    finish(own ? issue(i, j, k0 - 1) : none(), u_, v_, wm);
+    finish(own ? issue(col_own, k0 - 1) : none(), u_, v_, wm);
     DivLoad lo1 = issue_own(k0), lh1 = issue_halo(k0);
     w0 = put(0, lo1, lh1);
     lo1 = issue_own(k0 + 1);

@@ -32,12 +32,17 @@ def test_traffic_figure_is_tied_to_the_pass_source_and_flags(monkeypatch):
     import bench
     b = importlib.import_module("paper_1810_13416_gb300.build")
     with open(bench.TRAFFIC_JSON) as f:
-        committed = json.load(f)["f32"]["sweep_src_sha256_16"]
+        committed = json.load(f)["f32"]["src_sha256_16"]
     current = bench._src_hash()
-    assert (bench._traffic_per_cell("f32") is not None) == (current == committed)
-    flags = dict(b.UNIT_FLAGS)
-    flags["sweep_f32"] = [f for f in flags["sweep_f32"] if f != "-ftz=true"]
-    monkeypatch.setattr(b, "UNIT_FLAGS", flags)
-    assert bench._src_hash() != current
+    march, tile = (0, 0, 0), (1, 0, 0)
+    assert (bench._traffic_per_cell("f32", march) is not None) == (current == committed)
     if current == committed:
-        assert bench._traffic_per_cell("f32") is None
+        # the figure follows the design of each axis
+        assert bench._traffic_per_cell("f32", march) != bench._traffic_per_cell("f32", tile)
+    for unit in ("sweep_f32", "tile_f32"):
+        flags = dict(b.UNIT_FLAGS)
+        flags[unit] = [f for f in flags[unit] if f != "-ftz=true"]
+        monkeypatch.setattr(b, "UNIT_FLAGS", flags)
+        assert bench._src_hash() != current
+        if current == committed:
+            assert bench._traffic_per_cell("f32", march) is None
