@@ -361,7 +361,7 @@ __global__ void __launch_bounds__(NT, 2) tile_pass_kernel(const SweepArgs<float>
             const float mn = q[pn], m1 = q[p1], m2 = q[p2];
             const float ed = q[4];
             const float rho = bb.x + rd;
-            const float rinv = 1.0f / rho;
+            const float rinv = qdiv(1.0f, rho);
             const float u = mn * rinv, v = m1 * rinv, w = m2 * rinv;
             const float ke = 0.5f * (mn * u + (m1 * v + m2 * w));
             const float pd = gm1 * (ed - ke);
@@ -416,40 +416,40 @@ __global__ void __launch_bounds__(NT, 2) tile_pass_kernel(const SweepArgs<float>
             float WLn[5], WRc[5];
             const float rho2 = r0c + wrd[2];
             const float p2 = p0c + wpd[2];
-            const float c2 = gam * p2 / rho2;
-            const float cs = rsq(c2);
+            const float c2 = qdiv(gam * p2, rho2);
+            const float cs = rsq<true>(c2);
             // flattening coefficient (a3)
             float f = 0.0f;
             {
                 const float dp1 = wpd[3] - wpd[1];
                 const float dp2 = wpd[4] - wpd[0];
-                const float pmin = rmin(p0p + wpd[3], p0m + wpd[1]);
+                const float pmin = rmin<true>(p0p + wpd[3], p0m + wpd[1]);
                 if (rabs(dp1) > 0.33f * pmin && wu[1] - wu[3] > 0.0f) {
-                    const float r = (dp2 != 0.0f) ? dp1 / dp2 : 1.0f;
-                    f = rclamp(10.0f * (r - 0.75f), 0.0f, 1.0f);
+                    const float r = (dp2 != 0.0f) ? qdiv(dp1, dp2) : 1.0f;
+                    f = rsat<true>(10.0f * (r - 0.75f));
                 }
             }
             // parabolas of the five variables (a3, a4)
             float aL[5], aR[5], a6[5];
             {
-                const float q0 = smooth5(wrd[0], wrd[1], wrd[2], wrd[3], wrd[4], rho2);
-                parabola(wrd[1], wrd[2], wrd[3], afp[0], afn[0], f, q0, aL[0], aR[0], a6[0]);
-                const float q1 = smooth5(wu[0], wu[1], wu[2], wu[3], wu[4], cs);
-                parabola(wu[1], wu[2], wu[3], afp[1], afn[1], f, q1, aL[1], aR[1], a6[1]);
-                const float q2 = smooth5(wv[0], wv[1], wv[2], wv[3], wv[4], cs);
-                parabola(wv[1], wv[2], wv[3], afp[2], afn[2], f, q2, aL[2], aR[2], a6[2]);
-                const float q3 = smooth5(ww[0], ww[1], ww[2], ww[3], ww[4], cs);
-                parabola(ww[1], ww[2], ww[3], afp[3], afn[3], f, q3, aL[3], aR[3], a6[3]);
-                const float q4 = smooth5(wpd[0], wpd[1], wpd[2], wpd[3], wpd[4], p2);
-                parabola(wpd[1], wpd[2], wpd[3], afp[4], afn[4], f, q4, aL[4], aR[4], a6[4]);
+                const float q0 = smooth5<float, true>(wrd[0], wrd[1], wrd[2], wrd[3], wrd[4], rho2);
+                parabola<float, true>(wrd[1], wrd[2], wrd[3], afp[0], afn[0], f, q0, aL[0], aR[0], a6[0]);
+                const float q1 = smooth5<float, true>(wu[0], wu[1], wu[2], wu[3], wu[4], cs);
+                parabola<float, true>(wu[1], wu[2], wu[3], afp[1], afn[1], f, q1, aL[1], aR[1], a6[1]);
+                const float q2 = smooth5<float, true>(wv[0], wv[1], wv[2], wv[3], wv[4], cs);
+                parabola<float, true>(wv[1], wv[2], wv[3], afp[2], afn[2], f, q2, aL[2], aR[2], a6[2]);
+                const float q3 = smooth5<float, true>(ww[0], ww[1], ww[2], ww[3], ww[4], cs);
+                parabola<float, true>(ww[1], ww[2], ww[3], afp[3], afn[3], f, q3, aL[3], aR[3], a6[3]);
+                const float q4 = smooth5<float, true>(wpd[0], wpd[1], wpd[2], wpd[3], wpd[4], p2);
+                parabola<float, true>(wpd[1], wpd[2], wpd[3], afp[4], afn[4], f, q4, aL[4], aR[4], a6[4]);
             }
             // characteristic tracing (waves u-c, u, u+c) + buoyancy (a5)
             const float uc = wu[2];
             const float C = rho2 * cs;
             const float lm = uc - cs, l0 = uc, lp = uc + cs;
-            const float hg = hdt * ((wrd[2] / rho2) * gc);
+            const float hg = hdt * (qdiv(wrd[2], rho2) * gc);
             {   // right edge -> left state of face c+1/2
-                const float sp = rmax(lp, 0.0f) * dtdx;
+                const float sp = rmax<true>(lp, 0.0f) * dtdx;
                 float st[5];
 #pragma unroll
                 for (int q = 0; q < 5; ++q) st[q] = fR(aL[q], aR[q], a6[q], sp);
@@ -458,7 +458,7 @@ __global__ void __launch_bounds__(NT, 2) tile_pass_kernel(const SweepArgs<float>
                     const float sq = l0 * dtdx;
                     const float dr = rr - fR(aL[0], aR[0], a6[0], sq);
                     const float dp = rp - fR(aL[4], aR[4], a6[4], sq);
-                    st[0] = st[0] - (dr - dp / c2);
+                    st[0] = st[0] - (dr - qdiv(dp, c2));
                     st[2] = st[2] - (rv - fR(aL[2], aR[2], a6[2], sq));
                     st[3] = st[3] - (rw - fR(aL[3], aR[3], a6[3], sq));
                 }
@@ -467,8 +467,8 @@ __global__ void __launch_bounds__(NT, 2) tile_pass_kernel(const SweepArgs<float>
                     const float du = ru - fR(aL[1], aR[1], a6[1], sq);
                     const float dp = rp - fR(aL[4], aR[4], a6[4], sq);
                     const float Aa = 0.5f * (dp - C * du);
-                    st[0] = st[0] - Aa / c2;
-                    st[1] = st[1] + Aa / C;
+                    st[0] = st[0] - qdiv(Aa, c2);
+                    st[1] = st[1] + qdiv(Aa, C);
                     st[4] = st[4] - Aa;
                 }
                 st[1] = st[1] + hg;
@@ -476,7 +476,7 @@ __global__ void __launch_bounds__(NT, 2) tile_pass_kernel(const SweepArgs<float>
                 for (int q = 0; q < 5; ++q) WLn[q] = st[q];
             }
             {   // left edge -> right state of face c-1/2
-                const float sq0 = rmax(-lm, 0.0f) * dtdx;
+                const float sq0 = rmax<true>(-lm, 0.0f) * dtdx;
                 float st[5];
 #pragma unroll
                 for (int q = 0; q < 5; ++q) st[q] = fL(aL[q], aR[q], a6[q], sq0);
@@ -485,7 +485,7 @@ __global__ void __launch_bounds__(NT, 2) tile_pass_kernel(const SweepArgs<float>
                     const float sq = -l0 * dtdx;
                     const float dr = rr - fL(aL[0], aR[0], a6[0], sq);
                     const float dp = rp - fL(aL[4], aR[4], a6[4], sq);
-                    st[0] = st[0] - (dr - dp / c2);
+                    st[0] = st[0] - (dr - qdiv(dp, c2));
                     st[2] = st[2] - (rv - fL(aL[2], aR[2], a6[2], sq));
                     st[3] = st[3] - (rw - fL(aL[3], aR[3], a6[3], sq));
                 }
@@ -494,8 +494,8 @@ __global__ void __launch_bounds__(NT, 2) tile_pass_kernel(const SweepArgs<float>
                     const float du = ru - fL(aL[1], aR[1], a6[1], sq);
                     const float dp = rp - fL(aL[4], aR[4], a6[4], sq);
                     const float Aa = 0.5f * (dp + C * du);
-                    st[0] = st[0] - Aa / c2;
-                    st[1] = st[1] - Aa / C;
+                    st[0] = st[0] - qdiv(Aa, c2);
+                    st[1] = st[1] - qdiv(Aa, C);
                     st[4] = st[4] - Aa;
                 }
                 st[1] = st[1] + hg;
@@ -510,19 +510,19 @@ __global__ void __launch_bounds__(NT, 2) tile_pass_kernel(const SweepArgs<float>
                 const float a2 = 0.25f * (X(sm.x0, on_, sp1) - X(sm.x0, on_, sm1));
                 const float ep = 0.5f * mm + a2 * (1.0f / 6.0f);
                 const float em = a2 * (1.0f / 6.0f) - 0.5f * mm;
-                float gmax = rmax(ep, em), gmin = rmin(ep, em);
+                float gmax = rmax<true>(ep, em), gmin = rmin<true>(ep, em);
                 const bool nz = (a2 != 0.0f);
-                const float xv = -mm / (2.0f * (nz ? a2 : 1.0f));
+                const float xv = qdiv(-mm, 2.0f * (nz ? a2 : 1.0f));
                 const float gv = mm * xv + a2 * (xv * xv - (1.0f / 12.0f));
                 const bool in = nz && (rabs(xv) < 0.5f);
-                gmax = in ? rmax(gmax, gv) : gmax;
-                gmin = in ? rmin(gmin, gv) : gmin;
+                gmax = in ? rmax<true>(gmax, gv) : gmax;
+                gmin = in ? rmin<true>(gmin, gv) : gmin;
                 float th = 1.0f;
                 const float omf = fv_complement(fs);
                 const bool hi = gmax > omf, lo = -gmin > F;
-                const float t1 = omf / (hi ? gmax : 1.0f), t2 = F / (lo ? -gmin : 1.0f);
-                th = hi ? rmin(th, t1) : th;
-                th = lo ? rmin(th, t2) : th;
+                const float t1 = qdiv(omf, hi ? gmax : 1.0f), t2 = qdiv(F, lo ? -gmin : 1.0f);
+                th = hi ? rmin<true>(th, t1) : th;
+                th = lo ? rmin<true>(th, t2) : th;
                 me2 = th * mm;
                 ae2 = th * a2;
             }
@@ -552,17 +552,19 @@ __global__ void __launch_bounds__(NT, 2) tile_pass_kernel(const SweepArgs<float>
             const float rdR = WRc[0], uR = WRc[1], pdR = WRc[4];
             const float rL = r0 + rdL, pL = p0 + pdL;
             const float rR = r0 + rdR, pR = p0 + pdR;
-            const float CL = rsq(gam * pL * rL), CR = rsq(gam * pR * rR);
-            const float pfl = 1e-10f * rmin(pL, pR);
+            const float CL = rsq<true>(gam * pL * rL), CR = rsq<true>(gam * pR * rR);
+            const float pfl = 1e-10f * rmin<true>(pL, pR);
             float den = CL + CR;
-            float pst = pdL + CL * (CR * (uL - uR) + (pdR - pdL)) / den;
-            float ust = uL + (CR * (uR - uL) + (pdL - pdR)) / den;
+            float iden = qdiv(1.0f, den);
+            float pst = pdL + CL * (CR * (uL - uR) + (pdR - pdL)) * iden;
+            float ust = uL + (CR * (uR - uL) + (pdL - pdR)) * iden;
             if (p0 + pst < pfl) pst = pfl - p0;
-            const float WLi = CL * rsq(1.0f + kk * (pst - pdL) / pL);
-            const float WRi = CR * rsq(1.0f + kk * (pst - pdR) / pR);
+            const float WLi = CL * rsq<true>(1.0f + qdiv(kk * (pst - pdL), pL));
+            const float WRi = CR * rsq<true>(1.0f + qdiv(kk * (pst - pdR), pR));
             den = WLi + WRi;
-            pst = pdL + WLi * (WRi * (uL - uR) + (pdR - pdL)) / den;
-            ust = uL + (WRi * (uR - uL) + (pdL - pdR)) / den;
+            iden = qdiv(1.0f, den);
+            pst = pdL + WLi * (WRi * (uL - uR) + (pdR - pdL)) * iden;
+            ust = uL + (WRi * (uR - uL) + (pdL - pdR)) * iden;
             if (p0 + pst < pfl) pst = pfl - p0;
             const bool wall = (j == -1 && bcl == 1) || (j == n - 1 && bch == 1);
             if (wall) ust = 0.0f;
@@ -574,12 +576,12 @@ __global__ void __launch_bounds__(NT, 2) tile_pass_kernel(const SweepArgs<float>
             float vst = left ? WLp[2] : WRc[2];
             float wst = left ? WLp[3] : WRc[3];
             const float dps = pst - pds;
-            float rdst = rds + rs * dps / (gam * pss + 0.5f * gm1 * dps);
+            float rdst = rds + qdiv(rs * dps, gam * pss + 0.5f * gm1 * dps);
             {
                 // the two-shock solution at x/t = 0: upwind traced state where
                 // both waves move to one side
-                const bool supL = !wall && (uL - WLi / rL >= 0.0f);
-                const bool supR = !wall && !supL && (uR + WRi / rR <= 0.0f);
+                const bool supL = !wall && (uL * rL >= WLi);
+                const bool supR = !wall && !supL && (uR * rR <= -WRi);
                 ust = supL ? uL : (supR ? uR : ust);
                 pst = supL ? pdL : (supR ? pdR : pst);
                 rdst = supL ? rdL : (supR ? rdR : rdst);
@@ -672,13 +674,13 @@ __global__ void __launch_bounds__(NT, 2) tile_pass_kernel(const SweepArgs<float>
                 const float GLc = X(sm.x3, 7, sc), GLp = X(sm.x3, 7, sl);
                 const float Ac = X(sm.x3, 8, sc), Ap = X(sm.x3, 8, sl);
                 const float cL = rold * fv_unfold(X(sm.x0, 5, sc)) - (GLc - GLp);
-                const float FVL = cL / rnew;
-                const float Pp = rmax(0.0f, Ap) - rmin(0.0f, Ac);
-                const float Pm = rmax(0.0f, Ac) - rmin(0.0f, Ap);
+                const float FVL = qdiv(cL, rnew);
+                const float Pp = rmax<true>(0.0f, Ap) - rmin<true>(0.0f, Ac);
+                const float Pm = rmax<true>(0.0f, Ac) - rmin<true>(0.0f, Ap);
                 const float Qp = (1.0f - FVL) * rnew;
                 const float Qm = FVL * rnew;
-                X(sm.x4, 0, sc) = (Pp > 0.0f) ? rclamp(Qp / Pp, 0.0f, 1.0f) : 0.0f;
-                X(sm.x4, 1, sc) = (Pm > 0.0f) ? rclamp(Qm / Pm, 0.0f, 1.0f) : 0.0f;
+                X(sm.x4, 0, sc) = (Pp > 0.0f) ? rsat<true>(qdiv(Qp, Pp)) : 0.0f;
+                X(sm.x4, 1, sc) = (Pm > 0.0f) ? rsat<true>(qdiv(Qm, Pm)) : 0.0f;
                 X(sm.x4, 2, sc) = rnew;
             }
             // heating and damping after the pass (fused), checks and CFL
@@ -688,8 +690,8 @@ __global__ void __launch_bounds__(NT, 2) tile_pass_kernel(const SweepArgs<float>
                 const float4 hs = tab4(A.t4_src, A.ntab4, A.s4_0, A.inv_ds4, sv);
                 if (A.t_heat) edo = edo + dt * hs.x;
                 if (A.t_damp) {
-                    const float fd = rmax(0.0f, 1.0f - dt * hs.y);
-                    const float kin = 0.5f * (mno * mno + (m1o * m1o + m2o * m2o)) / rnew;
+                    const float fd = rmax<true>(0.0f, 1.0f - dt * hs.y);
+                    const float kin = qdiv(0.5f * (mno * mno + (m1o * m1o + m2o * m2o)), rnew);
                     mno = mno * fd;
                     m1o = m1o * fd;
                     m2o = m2o * fd;
@@ -697,14 +699,14 @@ __global__ void __launch_bounds__(NT, 2) tile_pass_kernel(const SweepArgs<float>
                 }
             }
             if (c >= 0 && c < n && pen_ok) {
-                const float ri = 1.0f / rnew;
+                const float ri = qdiv(1.0f, rnew);
                 const float uu = mno * ri, vv = m1o * ri, wv_ = m2o * ri;
                 const float kin = 0.5f * (mno * uu + (m1o * vv + m2o * wv_));
                 const float pr = p0c + gm1 * (edo - kin);
                 if (!(rnew > 0.0f) || !(pr > 0.0f)) bad = true;
                 if (A.cfl) {
-                    const float spd = rmax(rmax(rabs(uu), rabs(vv)), rabs(wv_)) + rsq(gam * pr * ri);
-                    smax_local = rmax(smax_local, spd);
+                    const float spd = rmax<true>(rmax<true>(rabs(uu), rabs(vv)), rabs(wv_)) + rsq<true>(gam * pr * ri);
+                    smax_local = rmax<true>(smax_local, spd);
                 }
             }
             float *o = &sm.out[(l == S - 1 ? k + 1 : k) & 1][posD];
@@ -727,8 +729,8 @@ __global__ void __launch_bounds__(NT, 2) tile_pass_kernel(const SweepArgs<float>
             const float Rpr = X(sm.x4, 0, sr), Rmr = X(sm.x4, 1, sr);
             // limited transfers of the right face (c+1/2) and the left face (c-1/2)
             const float Ar = X(sm.x3, 8, sc), Al = X(sm.x3, 8, sl);
-            const float Cfr = (Ar >= 0.0f) ? rmin(Rpr, Rmc) : rmin(Rpc, Rmr);
-            const float Cfl = (Al >= 0.0f) ? rmin(Rpc, Rml) : rmin(Rpl, Rmc);
+            const float Cfr = (Ar >= 0.0f) ? rmin<true>(Rpr, Rmc) : rmin<true>(Rpc, Rmr);
+            const float Cfl = (Al >= 0.0f) ? rmin<true>(Rpc, Rml) : rmin<true>(Rpl, Rmc);
             const float KLr = X(sm.x3, 9, sc), KLl = X(sm.x3, 9, sl);
             const float Gc4 = X(sm.x3, 7, sc) + Cfr * Ar;
             const float Kc4 = KLr + Cfr * (X(sm.x3, 10, sc) - KLr);
@@ -771,16 +773,16 @@ __global__ void __launch_bounds__(NT, 2) tile_pass_kernel(const SweepArgs<float>
             const float Zr = (rold - m_out) * sbar + zr_in - zr_out;
             const float dPhi = PHIp - PHIq;
             const float dG = Gc4 - Gq;
-            const float rinvn = 1.0f / rnew;
+            const float rinvn = qdiv(1.0f, rnew);
             const float fvs = fv_add(fs0, (fv0 * dPhi - dG) * rinvn);
             const float fvn = fv_unfold(fvs);
             const float bnd = fv_moment_bound(fvs);
             float onn = on0 + (on0 * dPhi + 12.0f * (dZc - fvn * Zr)) * rinvn;
             float o1 = o10 + (o10 * dPhi - (T1p - T1q)) * rinvn;
             float o2 = o20 + (o20 * dPhi - (T2p - T2q)) * rinvn;
-            onn = rclamp(onn, -bnd, bnd);
-            o1 = rclamp(o1, -bnd, bnd);
-            o2 = rclamp(o2, -bnd, bnd);
+            onn = rclamp<true>(onn, -bnd, bnd);
+            o1 = rclamp<true>(o1, -bnd, bnd);
+            o2 = rclamp<true>(o2, -bnd, bnd);
             float *o = &sm.out[k & 1][posA];
             o[5 * (S * P)] = fvs;
             o[on_ * (S * P)] = onn;
