@@ -702,13 +702,18 @@ __global__ void divergence_kernel(SweepArgs<R> A, const R *st, R *D, long long n
 // are issued two planes ahead of their use.  Ghost neighbours as in the
 // passes: periodic wrap, or the mirror cell with the normal velocity
 // reversed.  Differences summed in x, y, z order, times 1/(2 dx).
-constexpr int DIV_TX = 32, DIV_TY = 16, DIV_ZRUN = 64;
+#ifndef PPM_DIV_TY
+#define PPM_DIV_TY 16
+#endif
+#ifndef PPM_DIV_ZRUN
+#define PPM_DIV_ZRUN 64
+#endif
+constexpr int DIV_TX = 32, DIV_TY = PPM_DIV_TY, DIV_ZRUN = PPM_DIV_ZRUN;
 
 struct DivLoad {
-    float rd, m0, m1, m2;   // rho', rho u, rho v, rho w
-    float ta, tb, tw;       // rho0 table rows and weight
-    bool ok;                // a cell was loaded
-    signed char sx, sy, sz; // mirror signs of u, v, w
+    float rd, m0, m1, m2;   // rho', rho u, rho v, rho w (all 0 where no cell is loaded)
+    float ta, tb, tw;       // rho0 table rows and weight (rho0 = 1 where no cell is loaded)
+    unsigned sz;            // sign-bit mask of w (mirror image below / above a wall)
 };
 
 __global__ void __launch_bounds__(DIV_TX * DIV_TY) divergence_tile_kernel(SweepArgs<float> A, const float *st,
@@ -724,10 +729,12 @@ __global__ void __launch_bounds__(DIV_TX * DIV_TY) divergence_tile_kernel(SweepA
     const float ox = (float)A.org[0], oy = (float)A.org[1], oz = (float)A.org[2], dxf = (float)A.dx;
     // A column (x-y position) of the march: mapped indices, mirror signs and
     // position, fixed for the whole run of planes
+    // (mirror signs are applied as sign-bit masks: no conversions, no
+    // multiplications)
     struct Col {
         long long xy;     // x-y offset of the mapped cell in a plane
         float x2y2;       // x^2 + y^2 of the mapped cell (central gravity)
-        signed char sx, sy;
+        unsigned sx, sy;  // sign-bit masks of u and v
     };
     auto column = [&](int gi, int gj) -> Col {
         Col c;
@@ -736,20 +743,18 @@ __global__ void __launch_bounds__(DIV_TX * DIV_TY) divergence_tile_kernel(SweepA
         c.xy = (long long)jj * nx + ii;
         const float x = ox + ((float)ii + 0.5f) * dxf, y = oy + ((float)jj + 0.5f) * dxf;
         c.x2y2 = fmaf(y, y, x * x);
-        c.sx = fx ? -1 : 1;
-        c.sy = fy ? -1 : 1;
+        c.sx = fx ? 0x80000000u : 0u;
+        c.sy = fy ? 0x80000000u : 0u;
         return c;
     };
+    auto flipf = [](float v, unsigned m) { return __uint_as_float(__float_as_uint(v) ^ m); };
     const long long plane_cells = (long long)nx * ny;
     // loads of the cell of column cl in plane gk (mapped onto the grid when a ghost)
     auto issue = [&](const Col &cl, int gk) -> DivLoad {
         DivLoad d;
         bool fz = false;
         const int kk = map_cell(gk, nz, bz0, bz1, fz);
-        d.sx = cl.sx;
-        d.sy = cl.sy;
-        d.sz = fz ? -1 : 1;
-        d.ok = true;
+        d.sz = fz ? 0x80000000u : 0u;
         const long long cc = (long long)kk * plane_cells + cl.xy;
         d.rd = __ldg(st + cc);
         d.m0 = __ldg(st + ncell + cc);
@@ -771,21 +776,17 @@ __global__ void __launch_bounds__(DIV_TX * DIV_TY) divergence_tile_kernel(SweepA
     };
     auto none = []() {
         DivLoad d;
-        d.rd = d.m0 = d.m1 = d.m2 = d.ta = d.tb = d.tw = 0.0f;
-        d.ok = false;
-        d.sx = d.sy = d.sz = 1;
+        d.rd = d.m0 = d.m1 = d.m2 = d.tw = 0.0f;
+        d.ta = d.tb = 1.0f;
+        d.sz = 0u;
         return d;
     };
-    auto finish = [&](const DivLoad &d, float &u, float &v, float &w) {
-        if (!d.ok) {
-            u = v = w = 0.0f;
-            return;
-        }
+    auto finish = [&](const DivLoad &d, const Col &cl, float &u, float &v, float &w) {
         const float rho0 = fmaf(d.tw, d.tb - d.ta, d.ta);
-        const float ri = 1.0f / (rho0 + d.rd);
-        u = d.sx * (d.m0 * ri);
-        v = d.sy * (d.m1 * ri);
-        w = d.sz * (d.m2 * ri);
+        const float ri = qdiv(1.0f, rho0 + d.rd);
+        u = flipf(d.m0 * ri, cl.sx);
+        v = flipf(d.m1 * ri, cl.sy);
+        w = flipf(d.m2 * ri, d.sz);
     };
     // this thread's slot of a plane, and for threads 0..95 one halo slot
     // (rows j = -1 and j = 16 across the tile, columns i = -1 and i = 32 along
@@ -813,18 +814,18 @@ __global__ void __launch_bounds__(DIV_TX * DIV_TY) divergence_tile_kernel(SweepA
     // finish plane kk into buffer b; returns its u_z at this thread's cell
     auto put = [&](int b, const DivLoad &lo, const DivLoad &lh) {
         float u, v, w, uh, vh, wh;
-        finish(lo, u, v, w);
+        finish(lo, col_own, u, v, w);
         ux[b][ty + 1][tx + 1] = u;
         uy[b][ty + 1][tx + 1] = v;
         if (hx >= 0) {
-            finish(lh, uh, vh, wh);
+            finish(lh, col_halo, uh, vh, wh);
             ux[b][hy][hx] = uh;
             uy[b][hy][hx] = vh;
         }
         return w;
     };
     float wm, w0, wp, u_, v_;
-    finish(own ? issue(col_own, k0 - 1) : none(), u_, v_, wm);
+    finish(own ? issue(col_own, k0 - 1) : none(), col_own, u_, v_, wm);
     DivLoad lo1 = issue_own(k0), lh1 = issue_halo(k0);
     w0 = put(0, lo1, lh1);
     lo1 = issue_own(k0 + 1);
@@ -841,7 +842,7 @@ __global__ void __launch_bounds__(DIV_TX * DIV_TY) divergence_tile_kernel(SweepA
         if (k + 1 < k1) {
             wp = put(b ^ 1, lo1, lh1);
         } else {
-            finish(lo1, u_, v_, wp);   // the plane above the run: only its u_z
+            finish(lo1, col_own, u_, v_, wp);   // the plane above the run: only its u_z
         }
         if (own) {
             const float dxu = ux[b][ty + 1][tx + 2] - ux[b][ty + 1][tx];
