@@ -702,13 +702,7 @@ __global__ void divergence_kernel(SweepArgs<R> A, const R *st, R *D, long long n
 // are issued two planes ahead of their use.  Ghost neighbours as in the
 // passes: periodic wrap, or the mirror cell with the normal velocity
 // reversed.  Differences summed in x, y, z order, times 1/(2 dx).
-#ifndef PPM_DIV_TY
-#define PPM_DIV_TY 16
-#endif
-#ifndef PPM_DIV_ZRUN
-#define PPM_DIV_ZRUN 64
-#endif
-constexpr int DIV_TX = 32, DIV_TY = PPM_DIV_TY, DIV_ZRUN = PPM_DIV_ZRUN;
+constexpr int DIV_TX = 32, DIV_TY = 16, DIV_ZRUN = 64;
 
 struct DivLoad {
     float rd, m0, m1, m2;   // rho', rho u, rho v, rho w (all 0 where no cell is loaded)

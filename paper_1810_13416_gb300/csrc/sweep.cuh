@@ -108,9 +108,6 @@ __device__ __forceinline__ float xsqrt(float a) { return sqrtf(a); }
 // limiter sums); the full-range form costs a range test and a scaling per
 // division (measured: the FP32 passes 4% faster with this one).  FP64: the
 // IEEE quotient.
-#ifndef PPM_SRCPF
-#define PPM_SRCPF 0
-#endif
 __device__ __forceinline__ double qdiv(double a, double b) { return a / b; }
 __device__ __forceinline__ float qdiv(float a, float b) { return __fdividef(a, b); }
 
@@ -626,25 +623,6 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
         return map_cell(cc, n, bcl, bch, fl);
     };
     TabFetch cell_next, face_next;
-#if PPM_SRCPF
-    // heating and damping rows of the next cell to be updated, fetched one
-    // cell ahead (same index and weight as a lookup of the source table)
-    float2 src_a = make_float2(0.f, 0.f), src_b = src_a;
-    float src_w = 0.0f;
-    auto src_issue = [&](int ii) {
-        const float xa = xcell32(ii);
-        const float sv = (A.grav == 1) ? (ax == 2 ? xa : (float)zt) : fmaf(xa, xa, rt2);
-        const float u = (sv - A.s4_0) * A.inv_ds4;
-        const float fl = fminf(fmaxf(floorf(u), 0.0f), (float)(A.ntab4 - 2));
-        const int r = (int)fl;
-        const float2 *t2 = reinterpret_cast<const float2 *>(A.t4_src);
-        src_a = __ldg(t2 + 2 * r);
-        src_b = __ldg(t2 + 2 * r + 2);
-        src_w = u - fl;
-    };
-    if constexpr (F32 && !NSRC)
-        if (A.sources) src_issue(0);
-#endif
     if constexpr (F32) {
         bool fl0;
         cell_next = tab_issue(xcell32(mapc(-G, fl0)));
@@ -1318,17 +1296,13 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
             if (!NSRC && A.sources) {
                 R heat = 0, kd = 0;
                 if constexpr (F32) {
-#if PPM_SRCPF
-                    heat = fmaf(src_w, src_b.x - src_a.x, src_a.x);
-                    kd = fmaf(src_w, src_b.y - src_a.y, src_a.y);
-                    if (i + 1 < n) src_issue(i + 1);
-#else
+                    // (fetching these rows a cell ahead, as the base-state rows
+                    // are, measured 2% slower here: 254 registers)
                     const float xa = xcell32(i);
                     const float s = (A.grav == 1) ? (ax == 2 ? xa : (float)zt) : fmaf(xa, xa, rt2);
                     const float4 hs = tab4(A.t4_src, A.ntab4, A.s4_0, A.inv_ds4, s);
                     heat = hs.x;
                     kd = hs.y;
-#endif
                 } else {
                     R cx, cy, cz;
                     point(coord(A, ax, i0 + i), cx, cy, cz);
