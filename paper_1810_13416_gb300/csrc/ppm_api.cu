@@ -698,33 +698,36 @@ __global__ void divergence_kernel(SweepArgs<R> A, const R *st, R *D, long long n
 // z-planes.  Each cell's velocity (rho u_d / (rho0 + rho'), rho0 from the
 // pass kernels' FP32 tables) is computed once; u_x and u_y of a plane, with a
 // one-cell halo, sit in shared memory (two planes, one barrier per plane),
-// u_z of the planes below and above stay in registers.  The loads of a plane
-// are issued two planes ahead of their use.  Ghost neighbours as in the
-// passes: periodic wrap, or the mirror cell with the normal velocity
-// reversed.  Differences summed in x, y, z order, times 1/(2 dx).
+// u_z of the planes below and above stay in registers.  Ghost neighbours as
+// in the passes: periodic wrap, or the mirror cell with the normal velocity
+// reversed (applied as a sign-bit mask).  Differences summed in x, y, z
+// order, times 1/(2 dx).
 constexpr int DIV_TX = 32, DIV_TY = 16, DIV_ZRUN = 64;
 
-struct DivLoad {
-    float rd, m0, m1, m2;   // rho', rho u, rho v, rho w (all 0 where no cell is loaded)
-    float ta, tb, tw;       // rho0 table rows and weight (rho0 = 1 where no cell is loaded)
-    unsigned sz;            // sign-bit mask of w (mirror image below / above a wall)
-};
+// Loads: each thread copies the stored values its cells need (rho', three
+// momenta and the two base-state table rows of its own cell; rho', one
+// momentum and two rows of its halo cell) DIV_PF planes ahead into a private
+// ring in shared memory with cp.async, so that DIV_PF planes of loads per
+// thread are in flight without holding them in registers (an earlier form
+// kept one plane of loads in registers and was bound by the memory latency:
+// 1.5 ms more per launch at 1024^3).
+constexpr int DIV_PF = 4;                      // planes in flight per thread
+constexpr int DIV_NT = DIV_TX * DIV_TY;
+constexpr int DIV_RV = 10;                     // ring values per thread and plane
+constexpr int div_ring_smem() { return DIV_PF * DIV_RV * DIV_NT * (int)sizeof(float); }
 
-__global__ void __launch_bounds__(DIV_TX * DIV_TY) divergence_tile_kernel(SweepArgs<float> A, const float *st,
-                                                                          float *D, long long ncell, int nx, int ny,
-                                                                          int nz, int bx0, int bx1, int by0, int by1,
-                                                                          int bz0, int bz1) {
+__global__ void __launch_bounds__(DIV_NT, 2) divergence_ring_kernel(SweepArgs<float> A, const float *st, float *D,
+                                                                    long long ncell, int nx, int ny, int nz, int bx0,
+                                                                    int bx1, int by0, int by1, int bz0, int bz1) {
+    extern __shared__ __align__(16) float ring[];   // [DIV_PF][DIV_RV][DIV_NT]
     __shared__ float ux[2][DIV_TY + 2][DIV_TX + 2];
     __shared__ float uy[2][DIV_TY + 2][DIV_TX + 2];
-    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tx = threadIdx.x, ty = threadIdx.y, t = ty * DIV_TX + tx;
     const int i = blockIdx.x * DIV_TX + tx, j = blockIdx.y * DIV_TY + ty;
     const int k0 = blockIdx.z * DIV_ZRUN, k1 = min(nz, k0 + DIV_ZRUN);
     const float h = (float)(0.5 / A.dx);
     const float ox = (float)A.org[0], oy = (float)A.org[1], oz = (float)A.org[2], dxf = (float)A.dx;
-    // A column (x-y position) of the march: mapped indices, mirror signs and
-    // position, fixed for the whole run of planes
-    // (mirror signs are applied as sign-bit masks: no conversions, no
-    // multiplications)
+    const bool tab = (A.grav != 0);
     struct Col {
         long long xy;     // x-y offset of the mapped cell in a plane
         float x2y2;       // x^2 + y^2 of the mapped cell (central gravity)
@@ -742,53 +745,21 @@ __global__ void __launch_bounds__(DIV_TX * DIV_TY) divergence_tile_kernel(SweepA
         return c;
     };
     auto flipf = [](float v, unsigned m) { return __uint_as_float(__float_as_uint(v) ^ m); };
+    // table coordinate of plane kk of a column: row index and weight
+    auto tab_u = [&](const Col &cl, int kk) {
+        const float z = oz + ((float)kk + 0.5f) * dxf;
+        const float sv = (A.grav == 1) ? z : fmaf(z, z, cl.x2y2);
+        return (sv - A.s4_0) * A.inv_ds4;
+    };
+    auto tab_fl = [&](float uu) { return fminf(fmaxf(floorf(uu), 0.0f), (float)(A.ntab4 - 2)); };
     const long long plane_cells = (long long)nx * ny;
-    // loads of the cell of column cl in plane gk (mapped onto the grid when a ghost)
-    auto issue = [&](const Col &cl, int gk) -> DivLoad {
-        DivLoad d;
-        bool fz = false;
-        const int kk = map_cell(gk, nz, bz0, bz1, fz);
-        d.sz = fz ? 0x80000000u : 0u;
-        const long long cc = (long long)kk * plane_cells + cl.xy;
-        d.rd = __ldg(st + cc);
-        d.m0 = __ldg(st + ncell + cc);
-        d.m1 = __ldg(st + 2 * ncell + cc);
-        d.m2 = __ldg(st + 3 * ncell + cc);
-        d.ta = d.tb = (float)A.rho0_c;
-        d.tw = 0.0f;
-        if (A.grav != 0) {
-            const float z = oz + ((float)kk + 0.5f) * dxf;
-            const float sv = (A.grav == 1) ? z : fmaf(z, z, cl.x2y2);
-            const float uu = (sv - A.s4_0) * A.inv_ds4;
-            const float fl = fminf(fmaxf(floorf(uu), 0.0f), (float)(A.ntab4 - 2));
-            const int r = (int)fl;
-            d.tw = uu - fl;
-            d.ta = __ldg(reinterpret_cast<const float *>(A.t4_base + r));
-            d.tb = __ldg(reinterpret_cast<const float *>(A.t4_base + r + 1));
-        }
-        return d;
-    };
-    auto none = []() {
-        DivLoad d;
-        d.rd = d.m0 = d.m1 = d.m2 = d.tw = 0.0f;
-        d.ta = d.tb = 1.0f;
-        d.sz = 0u;
-        return d;
-    };
-    auto finish = [&](const DivLoad &d, const Col &cl, float &u, float &v, float &w) {
-        const float rho0 = fmaf(d.tw, d.tb - d.ta, d.ta);
-        const float ri = qdiv(1.0f, rho0 + d.rd);
-        u = flipf(d.m0 * ri, cl.sx);
-        v = flipf(d.m1 * ri, cl.sy);
-        w = flipf(d.m2 * ri, d.sz);
-    };
-    // this thread's slot of a plane, and for threads 0..95 one halo slot
-    // (rows j = -1 and j = 16 across the tile, columns i = -1 and i = 32 along
-    // it; the corners are never used).  Just past the grid edge (i == nx or
-    // j == ny) the slot is the ghost neighbour of the last cell.
+    // this thread's slot of a plane and, for threads 0..95, one halo slot
+    // (rows j = -1 and j = DIV_TY across the tile need v; columns i = -1 and
+    // i = DIV_TX along it need u; the corners are never used).  Just past the
+    // grid edge (i == nx or j == ny) the slot is the ghost neighbour of the
+    // last cell.
     const bool own = (i < nx && j < ny);
     const bool slot_ok = i <= nx && j <= ny && !(i == nx && j == ny);
-    const int t = ty * DIV_TX + tx;
     int hx = -1, hy = -1;
     if (t < 2 * DIV_TX) {
         hx = (t % DIV_TX) + 1;
@@ -798,57 +769,98 @@ __global__ void __launch_bounds__(DIV_TX * DIV_TY) divergence_tile_kernel(SweepA
         hy = (r % DIV_TY) + 1;
         hx = (r < DIV_TY) ? 0 : DIV_TX + 1;
     }
+    const bool halo_u = (t >= 2 * DIV_TX);
     const int gi = blockIdx.x * DIV_TX + hx - 1, gj = blockIdx.y * DIV_TY + hy - 1;
     const bool halo_ok = hx >= 0 && gi >= -1 && gi <= nx && gj >= -1 && gj <= ny;
-    // loads of plane kk: own slot (any kk in [-1, nz]) and halo (kk inside)
     const Col col_own = column(slot_ok ? i : 0, slot_ok ? j : 0);
     const Col col_halo = column(halo_ok ? gi : 0, halo_ok ? gj : 0);
-    auto issue_own = [&](int kk) { return slot_ok ? issue(col_own, kk) : none(); };
-    auto issue_halo = [&](int kk) { return (halo_ok && kk < k1) ? issue(col_halo, kk) : none(); };
-    // finish plane kk into buffer b; returns its u_z at this thread's cell
-    auto put = [&](int b, const DivLoad &lo, const DivLoad &lh) {
-        float u, v, w, uh, vh, wh;
-        finish(lo, col_own, u, v, w);
-        ux[b][ty + 1][tx + 1] = u;
-        uy[b][ty + 1][tx + 1] = v;
-        if (hx >= 0) {
-            finish(lh, col_halo, uh, vh, wh);
-            ux[b][hy][hx] = uh;
-            uy[b][hy][hx] = vh;
+    // copies of plane gk into ring slot sl: the own cell for gk in
+    // [k0-1, k1] (the planes just below and above the run give u_z), the halo
+    // cell for gk in [k0, k1); one commit group per call, empty or not
+    auto issue = [&](int gk, int sl) {
+        if (gk <= k1) {
+            float *r = ring + (sl * DIV_RV) * DIV_NT + t;
+            if (slot_ok) {
+                bool fz = false;
+                const int kk = map_cell(gk, nz, bz0, bz1, fz);
+                const float *p = st + (long long)kk * plane_cells + col_own.xy;
+                cp_async<4>(r, p);
+                cp_async<4>(r + DIV_NT, p + ncell);
+                cp_async<4>(r + 2 * DIV_NT, p + 2 * ncell);
+                cp_async<4>(r + 3 * DIV_NT, p + 3 * ncell);
+                if (tab) {
+                    const int row = (int)tab_fl(tab_u(col_own, kk));
+                    cp_async<4>(r + 4 * DIV_NT, reinterpret_cast<const float *>(A.t4_base + row));
+                    cp_async<4>(r + 5 * DIV_NT, reinterpret_cast<const float *>(A.t4_base + row + 1));
+                }
+            }
+            if (halo_ok && gk >= k0 && gk < k1) {
+                const float *p = st + (long long)gk * plane_cells + col_halo.xy;
+                cp_async<4>(r + 6 * DIV_NT, p);
+                cp_async<4>(r + 7 * DIV_NT, p + (halo_u ? 1 : 2) * ncell);
+                if (tab) {
+                    const int row = (int)tab_fl(tab_u(col_halo, gk));
+                    cp_async<4>(r + 8 * DIV_NT, reinterpret_cast<const float *>(A.t4_base + row));
+                    cp_async<4>(r + 9 * DIV_NT, reinterpret_cast<const float *>(A.t4_base + row + 1));
+                }
+            }
         }
-        return w;
+        cp_commit();
     };
-    float wm, w0, wp, u_, v_;
-    finish(own ? issue(col_own, k0 - 1) : none(), col_own, u_, v_, wm);
-    DivLoad lo1 = issue_own(k0), lh1 = issue_halo(k0);
-    w0 = put(0, lo1, lh1);
-    lo1 = issue_own(k0 + 1);
-    lh1 = issue_halo(k0 + 1);
-    __syncthreads();
-    for (int k = k0; k < k1; ++k) {
-        const int b = (k - k0) & 1;
-        // plane k+2's loads in flight while plane k+1 is finished
-        DivLoad lo2 = none(), lh2 = none();
-        if (k + 2 <= k1) {
-            lo2 = issue_own(k + 2);
-            lh2 = issue_halo(k + 2);
+    // 1 / rho of a cell from its ring values (rho' at r[0], rows at r[a], r[b])
+    auto rinv = [&](const float *r, int a, const Col &cl, int kk) {
+        float rho0 = (float)A.rho0_c;
+        if (tab) {
+            const float uu = tab_u(cl, kk);
+            const float ta = r[a * DIV_NT], tb = r[(a + 1) * DIV_NT];
+            rho0 = fmaf(uu - tab_fl(uu), tb - ta, ta);
         }
-        if (k + 1 < k1) {
-            wp = put(b ^ 1, lo1, lh1);
-        } else {
-            finish(lo1, col_own, u_, v_, wp);   // the plane above the run: only its u_z
+        return qdiv(1.0f, rho0 + r[0]);
+    };
+#pragma unroll
+    for (int sl = 0; sl < DIV_PF; ++sl) issue(k0 - 1 + sl, sl);
+    float wm = 0.0f, w0 = 0.0f;   // u_z of planes q-2 and q-1
+    for (int q = k0 - 1; q <= k1; ++q) {
+        const int sl = (q - (k0 - 1)) & (DIV_PF - 1);
+        cp_wait<DIV_PF - 1>();   // this thread's copies of plane q have landed
+        const float *r = ring + (sl * DIV_RV) * DIV_NT + t;
+        float u = 0.0f, v = 0.0f, w = 0.0f, hv = 0.0f;
+        if (slot_ok) {
+            bool fz = false;
+            const int kk = map_cell(q, nz, bz0, bz1, fz);
+            const float ri = rinv(r, 4, col_own, kk);
+            u = flipf(r[DIV_NT] * ri, col_own.sx);
+            v = flipf(r[2 * DIV_NT] * ri, col_own.sy);
+            w = flipf(r[3 * DIV_NT] * ri, fz ? 0x80000000u : 0u);
         }
-        if (own) {
+        const bool hq = halo_ok && q >= k0 && q < k1;
+        if (hq) {
+            const float ri = rinv(r + 6 * DIV_NT, 8 - 6, col_halo, q);
+            hv = flipf(r[7 * DIV_NT] * ri, halo_u ? col_halo.sx : col_halo.sy);
+        }
+        issue(q + DIV_PF, sl);   // the slot is free again
+        if (q >= k0 && q < k1) {
+            const int b = q & 1;
+            ux[b][ty + 1][tx + 1] = u;
+            uy[b][ty + 1][tx + 1] = v;
+            if (hq) {
+                if (halo_u)
+                    ux[b][hy][hx] = hv;
+                else
+                    uy[b][hy][hx] = hv;
+            }
+        }
+        if (q > k0 && own) {   // plane q-1: u_x, u_y written last iteration, u_z of q-2 and q
+            const int b = (q - 1) & 1;
             const float dxu = ux[b][ty + 1][tx + 2] - ux[b][ty + 1][tx];
             const float dyv = uy[b][ty + 2][tx + 1] - uy[b][ty][tx + 1];
-            D[((long long)k * ny + j) * nx + i] = ((dxu + dyv) + (wp - wm)) * h;
+            D[((long long)(q - 1) * ny + j) * nx + i] = ((dxu + dyv) + (w - wm)) * h;
         }
         wm = w0;
-        w0 = wp;
-        lo1 = lo2;
-        lh1 = lh2;
+        w0 = w;
         __syncthreads();
     }
+    cp_wait<0>();
 }
 
 int launch_divergence(ppm_ctx *c) {
@@ -857,7 +869,7 @@ int launch_divergence(ppm_ctx *c) {
     if (c->prec == PPM_FP32_DEVIATION) {
         const dim3 grid((c->n[0] + DIV_TX - 1) / DIV_TX, (c->n[1] + DIV_TY - 1) / DIV_TY,
                         (c->n[2] + DIV_ZRUN - 1) / DIV_ZRUN);
-        divergence_tile_kernel<<<grid, dim3(DIV_TX, DIV_TY), 0, c->stream>>>(
+        divergence_ring_kernel<<<grid, dim3(DIV_TX, DIV_TY), div_ring_smem(), c->stream>>>(
             make_args<float>(c, 0), (const float *)c->state, (float *)c->divg, c->ncell, c->n[0], c->n[1], c->n[2],
             b[0], b[1], b[2], b[3], b[4], b[5]);
     } else
@@ -1261,6 +1273,8 @@ int ppm_create(ppm_ctx **out, int nx, int ny, int nz, double gamma, const int bc
         cudaMemcpy(c->t4, h4.data(), h4.size() * sizeof(float4), cudaMemcpyHostToDevice) != cudaSuccess ||
         prepare_sweep_f32() != cudaSuccess || prepare_sweep_f64() != cudaSuccess ||
         prepare_sweep_ensemble() != cudaSuccess ||
+        cudaFuncSetAttribute(divergence_ring_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             div_ring_smem()) != cudaSuccess ||
         cudaMemset(c->ds_dev, 0, sizeof(DevScal)) != cudaSuccess ||
         cudaMemset(c->state, 0, sbytes) != cudaSuccess) {
         fail(c, PPM_ECUDA, "initialising device buffers failed");
