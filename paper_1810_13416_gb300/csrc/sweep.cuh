@@ -425,9 +425,20 @@ __host__ __device__ constexpr int vec_stage(int NV) { return NV > 9 ? 4 : 8; }
 
 // Dynamic shared memory of one block of the pass (NV stored values per cell:
 // 9, or 15 with the ten-value PPB).
+// FP32 scalar path: heating and damping table rows of each cell to be
+// updated, copied with the state (two 8-byte rows and the weight per slot;
+// measured: the pass with sources 48.6 -> 45.7 ms at 1024^3, where a
+// synchronous lookup exposed the table latency and a prefetch into
+// registers cost more than it saved)
+constexpr int SRC_SLOTS = 8;
+template <typename R, bool VEC>
+constexpr int src_ring_bytes(int NB) {
+    return (!VEC && sizeof(R) == 4) ? SRC_SLOTS * NB * (2 * 8 + 4) : 0;
+}
 template <typename R, bool VEC, int NB = SWEEP_NB, int NV = 9>
 constexpr int sweep_smem_bytes() {
-    return VEC ? (vec_slots(NV) * NV * NB * 16 + NV * NB * 4 * vec_stage(NV)) : (RING * NV * NB * (int)sizeof(R));
+    return VEC ? (vec_slots(NV) * NV * NB * 16 + NV * NB * 4 * vec_stage(NV))
+               : (RING * NV * NB * (int)sizeof(R) + src_ring_bytes<R, VEC>(NB));
 }
 
 #ifndef PPM_SWEEP_UNROLL
@@ -642,7 +653,27 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
     constexpr int VSLOT = vec_slots(NV), VSTAGE = vec_stage(NV);
     auto vslot = [](int g) { return VSLOT == 4 ? (g & 3) : (g % VSLOT); };
     float *outv = reinterpret_cast<float *>(smem_raw) + VSLOT * NV * SWEEP_NB * 4;
+    constexpr bool SRING = F32 && !VEC && !NSRC;
+    float2 *srow = reinterpret_cast<float2 *>(smem_raw + RING * NV * SWEEP_NB * sizeof(R));
+    float *sw = reinterpret_cast<float *>(srow + SRC_SLOTS * 2 * SWEEP_NB);
+    // table rows of cell cs (issued with the state copies of cell cs + PREF,
+    // so they have landed when cell cs is updated, PREF iterations later)
+    auto fetch_src = [&](int cs) {
+        if (cs < 0 || cs >= n) return;
+        const float xa = xcell32(cs);
+        const float sv = (A.grav == 1) ? (ax == 2 ? xa : (float)zt) : fmaf(xa, xa, rt2);
+        const float u = (sv - A.s4_0) * A.inv_ds4;
+        const float fl = fminf(fmaxf(floorf(u), 0.0f), (float)(A.ntab4 - 2));
+        const int r = (int)fl;
+        const float2 *t2 = reinterpret_cast<const float2 *>(A.t4_src);
+        const int sl = cs & (SRC_SLOTS - 1);
+        cp_async<8>(srow + (sl * 2) * SWEEP_NB + tid, t2 + 2 * r);
+        cp_async<8>(srow + (sl * 2 + 1) * SWEEP_NB + tid, t2 + 2 * r + 2);
+        sw[sl * SWEEP_NB + tid] = u - fl;
+    };
     auto fetch = [&](int cf) {
+        if constexpr (SRING)
+            if (A.sources) fetch_src(cf - PREF);
         if (HALO && halo_cell(cf) && cf < n + G) {
             // ghost plane of a halo side: [var][plane][pencil offset]
             const R *hb = (cf < 0) ? A.halo_lo + (long long)(cf + G) * sa : A.halo_hi + (long long)(cf - n) * sa;
@@ -1296,13 +1327,19 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
             if (!NSRC && A.sources) {
                 R heat = 0, kd = 0;
                 if constexpr (F32) {
-                    // (fetching these rows a cell ahead, as the base-state rows
-                    // are, measured 2% slower here: 254 registers)
-                    const float xa = xcell32(i);
-                    const float s = (A.grav == 1) ? (ax == 2 ? xa : (float)zt) : fmaf(xa, xa, rt2);
-                    const float4 hs = tab4(A.t4_src, A.ntab4, A.s4_0, A.inv_ds4, s);
-                    heat = hs.x;
-                    kd = hs.y;
+                    if constexpr (SRING) {
+                        const int sl = i & (SRC_SLOTS - 1);
+                        const float2 ra = srow[(sl * 2) * SWEEP_NB + tid], rb = srow[(sl * 2 + 1) * SWEEP_NB + tid];
+                        const float w = sw[sl * SWEEP_NB + tid];
+                        heat = fmaf(w, rb.x - ra.x, ra.x);
+                        kd = fmaf(w, rb.y - ra.y, ra.y);
+                    } else {
+                        const float xa = xcell32(i);
+                        const float s = (A.grav == 1) ? (ax == 2 ? xa : (float)zt) : fmaf(xa, xa, rt2);
+                        const float4 hs = tab4(A.t4_src, A.ntab4, A.s4_0, A.inv_ds4, s);
+                        heat = hs.x;
+                        kd = hs.y;
+                    }
                 } else {
                     R cx, cy, cz;
                     point(coord(A, ax, i0 + i), cx, cy, cz);

@@ -146,7 +146,9 @@ __device__ __forceinline__ int slot_add(int s, int d) {
 // face l - 2, l - 3, l - 3, l - 4 behind it in stages B to E, and the block
 // stores cells [kS, kS + S) at the end of the step.
 // ---------------------------------------------------------------------------
-template <int AX>
+// FULL = false: a pass without sources and without the CFL maximum (its own
+// instantiation, without that code)
+template <int AX, bool FULL = true>
 __global__ void __launch_bounds__(NT, 2) tile_pass_kernel(const SweepArgs<float> A,
                                                          const __grid_constant__ CUtensorMap tmap) {
     constexpr bool XP = (AX == 0);
@@ -541,7 +543,7 @@ __global__ void __launch_bounds__(NT, 2) tile_pass_kernel(const SweepArgs<float>
         // 3% faster on the pass with sources)
         float2 hsa = make_float2(0.f, 0.f), hsb = hsa;
         float hsw = 0.0f;
-        if (A.sources) {
+        if (FULL && A.sources) {
             const float xa = xcell_f(fk + (float)(l + 1));
             const float sv = (A.grav == 1) ? (ax == 2 ? xa : zt) : fmaf(xa, xa, rt2);
             const float u = (sv - A.s4_0) * A.inv_ds4;
@@ -700,7 +702,7 @@ __global__ void __launch_bounds__(NT, 2) tile_pass_kernel(const SweepArgs<float>
                 X(sm.x4, 2, sc) = rnew;
             }
             // heating and damping after the pass (fused), checks and CFL
-            if (A.sources) {
+            if (FULL && A.sources) {
                 const float2 hs = make_float2(fmaf(hsw, hsb.x - hsa.x, hsa.x), fmaf(hsw, hsb.y - hsa.y, hsa.y));
                 if (A.t_heat) edo = edo + dt * hs.x;
                 if (A.t_damp) {
@@ -718,7 +720,7 @@ __global__ void __launch_bounds__(NT, 2) tile_pass_kernel(const SweepArgs<float>
                 const float kin = 0.5f * (mno * uu + (m1o * vv + m2o * wv_));
                 const float pr = p0c + gm1 * (edo - kin);
                 if (!(rnew > 0.0f) || !(pr > 0.0f)) bad = true;
-                if (A.cfl) {
+                if (FULL && A.cfl) {
                     const float spd = rmax<true>(rmax<true>(rabs(uu), rabs(vv)), rabs(wv_)) + rsq<true>(gam * pr * ri);
                     smax_local = rmax<true>(smax_local, spd);
                 }
@@ -823,7 +825,7 @@ __global__ void __launch_bounds__(NT, 2) tile_pass_kernel(const SweepArgs<float>
         bulk_wait_all();
     }
     if (bad && pen_ok) atomicOr(A.flags, FLAG_NONPHYS);
-    if (A.cfl) {
+    if (FULL && A.cfl) {
         double smx = (double)smax_local;
         for (int o = 16; o > 0; o >>= 1) smx = fmax(smx, __shfl_xor_sync(0xffffffffu, smx, o));
         if ((threadIdx.x & 31) == 0) atomicMax(A.smax, dbits(smx));

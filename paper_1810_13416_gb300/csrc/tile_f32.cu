@@ -9,14 +9,14 @@
 namespace ppm {
 
 cudaError_t prepare_tile_f32() {
-    cudaError_t e = cudaFuncSetAttribute(tile::tile_pass_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)tile::SMEM_BYTES);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(tile::tile_pass_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)tile::SMEM_BYTES);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(tile::tile_pass_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)tile::SMEM_BYTES);
+    const int sm = (int)tile::SMEM_BYTES;
+    const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(tile::tile_pass_kernel<0, true>, at, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(tile::tile_pass_kernel<1, true>, at, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(tile::tile_pass_kernel<2, true>, at, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(tile::tile_pass_kernel<0, false>, at, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(tile::tile_pass_kernel<1, false>, at, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(tile::tile_pass_kernel<2, false>, at, sm);
     return e;
 }
 
@@ -59,12 +59,17 @@ int tile_encode_map(CUtensorMap *m, void *state, int nx, int ny, int nz, int axi
 
 void launch_tile_f32(const SweepArgs<float> &a, const CUtensorMap *m, cudaStream_t st) {
     const dim3 grid((a.nlane + tile::P - 1) / tile::P, a.nblk);
-    if (a.axis == 0)
-        tile::tile_pass_kernel<0><<<grid, tile::NT, tile::SMEM_BYTES, st>>>(a, *m);
-    else if (a.axis == 1)
-        tile::tile_pass_kernel<1><<<grid, tile::NT, tile::SMEM_BYTES, st>>>(a, *m);
-    else
-        tile::tile_pass_kernel<2><<<grid, tile::NT, tile::SMEM_BYTES, st>>>(a, *m);
+    const bool full = a.sources || a.cfl;   // else the instantiation without that code
+    if (a.axis == 0) {
+        if (full) tile::tile_pass_kernel<0, true><<<grid, tile::NT, tile::SMEM_BYTES, st>>>(a, *m);
+        else tile::tile_pass_kernel<0, false><<<grid, tile::NT, tile::SMEM_BYTES, st>>>(a, *m);
+    } else if (a.axis == 1) {
+        if (full) tile::tile_pass_kernel<1, true><<<grid, tile::NT, tile::SMEM_BYTES, st>>>(a, *m);
+        else tile::tile_pass_kernel<1, false><<<grid, tile::NT, tile::SMEM_BYTES, st>>>(a, *m);
+    } else {
+        if (full) tile::tile_pass_kernel<2, true><<<grid, tile::NT, tile::SMEM_BYTES, st>>>(a, *m);
+        else tile::tile_pass_kernel<2, false><<<grid, tile::NT, tile::SMEM_BYTES, st>>>(a, *m);
+    }
 }
 
 }  // namespace ppm
