@@ -1,8 +1,9 @@
 """GPU parity of the 3-D shock dissipation (Sec. 1) against the FP64 oracle,
-through the C ABI: Sod and Lax tubes along each axis and a periodic box with
-forming shocks, FP64 (relative L-inf <= 1e-10), and FP32 (relative L1 <= 1e-5
-on rho and E) on the Sod tubes and the box; the dissipation is active in
-these runs (oracle counter)."""
+through the C ABI: Sod and Lax tubes along each axis, a periodic box with
+forming shocks, and converging flows in the sphere (central gravity) and the
+stratified layer (plane gravity, walls in z) with even and odd nx, FP64
+(relative L-inf <= 1e-10), and FP32 (relative L1 <= 1e-5 on rho and E) on all
+but the Lax tube; the dissipation is active in these runs (oracle counter)."""
 import copy
 
 import numpy as np
@@ -44,12 +45,37 @@ def _shock_box():
     return p, q
 
 
+def _converging(p, q, amp):
+    """Add a converging (irrotational) flow along x and z, u = -amp sin(2 pi s)
+    in the cell-index coordinate s in (0, 1), so that shocks form and the
+    dissipation switches on in a gravitating state."""
+    nx, ny, nz = p.shape
+    x = (np.arange(nx) + 0.5) / nx
+    z = (np.arange(nz) + 0.5) / nz
+    Z, _, X = np.meshgrid(z, np.arange(ny), x, indexing="ij")
+    rho = q[0]
+    ke0 = 0.5 * (q[1] ** 2 + q[2] ** 2 + q[3] ** 2) / rho
+    q[1] = q[1] - rho * amp * np.sin(2 * np.pi * X)
+    q[3] = q[3] - rho * amp * np.sin(2 * np.pi * Z)
+    q[4] = q[4] - ke0 + 0.5 * (q[1] ** 2 + q[2] ** 2 + q[3] ** 2) / rho
+    return q
+
+
 def _cases():
     out = []
     for axis in range(3):
         out.append(("sod", axis))
     out.append(("lax", 0))
     out.append(("box", None))
+    # gravitating states (the divergence takes rho0 from the base-state
+    # tables): central gravity, plane gravity with walls in z, even and odd nx
+    out.append(("sphere", (24, 24, 24)))
+    out.append(("sphere", (23, 24, 24)))
+    out.append(("strat", (24, 20, 18)))
+    out.append(("strat", (23, 20, 18)))
+    # several tiles in x, in y (the last one partial, with the ghost row in
+    # its own slots) and several runs in z
+    out.append(("strat", (70, 18, 80)))
     return out
 
 
@@ -57,6 +83,10 @@ def _problem(case):
     kind, axis = case
     if kind == "box":
         return _shock_box()
+    if kind in ("sphere", "strat"):
+        p = workloads.sphere(n=axis[0], shape=axis) if kind == "sphere" else workloads.strat_box(shape=axis)
+        p = _with_k(p)
+        return p, _converging(p, workloads.build(p), 0.8 if axis[2] > 64 else 0.3)
     p = _with_k(workloads.tube(kind, n=96, axis=axis, length=2.0 if kind == "lax" else 1.0))
     return p, workloads.build(p)
 
