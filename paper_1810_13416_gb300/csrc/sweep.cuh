@@ -432,13 +432,13 @@ __host__ __device__ constexpr int vec_stage(int NV) { return NV > 9 ? 4 : 8; }
 // registers cost more than it saved)
 constexpr int SRC_SLOTS = 8;
 template <typename R, bool VEC>
-constexpr int src_ring_bytes(int NB) {
-    return (!VEC && sizeof(R) == 4) ? SRC_SLOTS * NB * (2 * 8 + 4) : 0;
+constexpr int src_ring_bytes(int NB, int NV) {
+    return (!VEC && sizeof(R) == 4 && NV == 9) ? SRC_SLOTS * NB * (2 * 8 + 4) : 0;
 }
 template <typename R, bool VEC, int NB = SWEEP_NB, int NV = 9>
 constexpr int sweep_smem_bytes() {
     return VEC ? (vec_slots(NV) * NV * NB * 16 + NV * NB * 4 * vec_stage(NV))
-               : (RING * NV * NB * (int)sizeof(R) + src_ring_bytes<R, VEC>(NB));
+               : (RING * NV * NB * (int)sizeof(R) + src_ring_bytes<R, VEC>(NB, NV));
 }
 
 #ifndef PPM_SWEEP_UNROLL
@@ -653,7 +653,9 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
     constexpr int VSLOT = vec_slots(NV), VSTAGE = vec_stage(NV);
     auto vslot = [](int g) { return VSLOT == 4 ? (g & 3) : (g % VSLOT); };
     float *outv = reinterpret_cast<float *>(smem_raw) + VSLOT * NV * SWEEP_NB * 4;
-    constexpr bool SRING = F32 && !VEC && !NSRC;
+    // (not in the ten-value and confined instantiations: measured slower
+    // there, 65.0 -> 74.2 and 42.9 -> 43.7 ms per pass at 1024^3)
+    constexpr bool SRING = F32 && !VEC && !NSRC && !TEN && !CONF;
     float2 *srow = reinterpret_cast<float2 *>(smem_raw + RING * NV * SWEEP_NB * sizeof(R));
     float *sw = reinterpret_cast<float *>(srow + SRC_SLOTS * 2 * SWEEP_NB);
     // table rows of cell cs (issued with the state copies of cell cs + PREF,
