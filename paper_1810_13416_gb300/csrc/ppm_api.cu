@@ -21,7 +21,7 @@ cudaError_t prepare_sweep_f32();
 cudaError_t prepare_sweep_f64();
 cudaError_t prepare_sweep_ensemble();
 int ensemble_blocks_per_sm(int f32, int vec, int nb);
-void launch_sweep_ensemble(int f32, int vec, int nb, const void *args, const WorkItem *work, int nwork,
+void launch_sweep_ensemble(int f32, int vec, int nb, int nsrc, const void *args, const WorkItem *work, int nwork,
                            int *counter, int persistent, int grid, cudaStream_t st);
 cudaError_t prepare_tile_f32();
 cudaError_t prepare_ensemble_step();
@@ -1877,8 +1877,10 @@ int ens_launch_pass(ppm_ens *e, int pass) {
         const int pers = e->cfg_pers[a];
         int grid = nw;
         if (pers) grid = std::min(nw, e->nsm * e->bps[vec ? 2 : (nb == 64 ? 0 : 1)]);
-        launch_sweep_ensemble(f32, vec, nb, args, e->d_work + e->work_off[a][var], nw, e->d_counters + pass * 2 + var,
-                              pers, grid, e->stream);
+        // passes 2 and 5 carry the sources, pass 5 the CFL maximum
+        const int nsrc = (pass != 2 && pass != 5) ? 1 : 0;
+        launch_sweep_ensemble(f32, vec, nb, nsrc, args, e->d_work + e->work_off[a][var], nw,
+                              e->d_counters + pass * 2 + var, pers, grid, e->stream);
         e->launches++;
         ECK(e, cudaGetLastError());
     }

@@ -1467,7 +1467,7 @@ struct WorkItem {
     int box, lane_block, blk, pad;
 };
 
-template <typename R, bool PLAIN, bool VEC, int NB>
+template <typename R, bool PLAIN, bool VEC, int NB, bool NSRC = false>
 __global__ void __launch_bounds__(NB, 1) sweep_ensemble_kernel(const SweepArgs<R> *__restrict__ args,
                                                                const WorkItem *__restrict__ work, int nwork,
                                                                int *counter, int persistent) {
@@ -1484,7 +1484,7 @@ __global__ void __launch_bounds__(NB, 1) sweep_ensemble_kernel(const SweepArgs<R
         const WorkItem w = work[item];
         if (threadIdx.x == 0) sA = args[w.box];
         __syncthreads();
-        sweep_body<R, PLAIN, VEC, NB>(sA, w.lane_block, w.blk, smem_raw);
+        sweep_body<R, PLAIN, VEC, NB, false, false, false, false, NSRC>(sA, w.lane_block, w.blk, smem_raw);
         __syncthreads();
         if (!persistent) break;
         if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);

@@ -6,17 +6,20 @@
 
 namespace ppm {
 
+template <bool VEC, int NB>
+static cudaError_t set_smem_f32() {
+    cudaError_t e = cudaFuncSetAttribute(sweep_ensemble_kernel<float, false, VEC, NB, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, sweep_smem_bytes<float, VEC, NB>());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(sweep_ensemble_kernel<float, false, VEC, NB, true>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, sweep_smem_bytes<float, VEC, NB>());
+}
+
 cudaError_t prepare_sweep_ensemble() {
     cudaError_t e;
-    e = cudaFuncSetAttribute(sweep_ensemble_kernel<float, false, false, 64>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, sweep_smem_bytes<float, false, 64>());
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(sweep_ensemble_kernel<float, false, false, 128>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, sweep_smem_bytes<float, false, 128>());
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(sweep_ensemble_kernel<float, false, true, 128>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, sweep_smem_bytes<float, true, 128>());
-    if (e != cudaSuccess) return e;
+    if ((e = set_smem_f32<false, 64>()) != cudaSuccess) return e;
+    if ((e = set_smem_f32<false, 128>()) != cudaSuccess) return e;
+    if ((e = set_smem_f32<true, 128>()) != cudaSuccess) return e;
     return cudaFuncSetAttribute(sweep_ensemble_kernel<double, true, false, 128>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, sweep_smem_bytes<double, false, 128>());
 }
@@ -39,20 +42,31 @@ int ensemble_blocks_per_sm(int f32, int vec, int nb) {
     return nblk > 0 ? nblk : 1;
 }
 
-void launch_sweep_ensemble(int f32, int vec, int nb, const void *args, const WorkItem *work, int nwork,
+// nsrc: no box of this pass has sources or the CFL maximum (the
+// instantiation without that code; four of the six passes of a step)
+template <bool VEC, int NB>
+static void launch_f32(bool nsrc, const void *args, const WorkItem *work, int nwork, int *counter, int persistent,
+                       int grid, cudaStream_t st) {
+    const SweepArgs<float> *a = static_cast<const SweepArgs<float> *>(args);
+    if (nsrc)
+        sweep_ensemble_kernel<float, false, VEC, NB, true><<<grid, NB, sweep_smem_bytes<float, VEC, NB>(), st>>>(
+            a, work, nwork, counter, persistent);
+    else
+        sweep_ensemble_kernel<float, false, VEC, NB, false><<<grid, NB, sweep_smem_bytes<float, VEC, NB>(), st>>>(
+            a, work, nwork, counter, persistent);
+}
+
+void launch_sweep_ensemble(int f32, int vec, int nb, int nsrc, const void *args, const WorkItem *work, int nwork,
                            int *counter, int persistent, int grid, cudaStream_t st) {
     if (!f32) {
         sweep_ensemble_kernel<double, true, false, 128><<<grid, 128, sweep_smem_bytes<double, false, 128>(), st>>>(
             static_cast<const SweepArgs<double> *>(args), work, nwork, counter, persistent);
     } else if (vec) {
-        sweep_ensemble_kernel<float, false, true, 128><<<grid, 128, sweep_smem_bytes<float, true, 128>(), st>>>(
-            static_cast<const SweepArgs<float> *>(args), work, nwork, counter, persistent);
+        launch_f32<true, 128>(nsrc != 0, args, work, nwork, counter, persistent, grid, st);
     } else if (nb == 64) {
-        sweep_ensemble_kernel<float, false, false, 64><<<grid, 64, sweep_smem_bytes<float, false, 64>(), st>>>(
-            static_cast<const SweepArgs<float> *>(args), work, nwork, counter, persistent);
+        launch_f32<false, 64>(nsrc != 0, args, work, nwork, counter, persistent, grid, st);
     } else {
-        sweep_ensemble_kernel<float, false, false, 128><<<grid, 128, sweep_smem_bytes<float, false, 128>(), st>>>(
-            static_cast<const SweepArgs<float> *>(args), work, nwork, counter, persistent);
+        launch_f32<false, 128>(nsrc != 0, args, work, nwork, counter, persistent, grid, st);
     }
 }
 
