@@ -333,8 +333,8 @@ int ppm_ensemble_step(ppm_ens *e, double dt);
 int ppm_ensemble_diagnostics(ppm_ens *e, int box, double totals[7], double *max_mach);
 /* Wait for the ensemble's work; ENONPHYS if any box flagged a bad cell. */
 int ppm_ensemble_sync(ppm_ens *e);
-/* Tile configuration per axis: block = pencils per block (64 or 128; FP64:
- * 128), persistent != 0: a resident grid takes work items from a counter
+/* Tile configuration per axis: block = pencils per block (32, 64 or 128;
+ * FP64: 128; small boxes leave fewer lanes idle in smaller blocks), persistent != 0: a resident grid takes work items from a counter
  * instead of one block per item; vec (axis 0 only): 16-byte x-pass copies for
  * boxes with nx % 8 == 0 (FP32). */
 int ppm_ensemble_set_config(ppm_ens *e, int axis, int block, int persistent, int vec);

@@ -1730,7 +1730,7 @@ struct ppm_ens {
     int cfg_nb[3] = {128, 128, 128};
     int cfg_pers[3] = {1, 1, 1};
     int cfg_vec = 1;
-    int bps[3] = {1, 1, 1};         // resident blocks per SM: scalar 64, scalar 128, vec 128
+    int bps[2][3] = {{1, 1, 1}, {1, 1, 1}};   // resident blocks per SM: [vec][32, 64, 128 pencils]
     int nsm = 152;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -1807,7 +1807,7 @@ int build_work(ppm_ens *e) {
             for (int b = 0; b < e->nbox; ++b) {
                 const bool v = (a == 0) && e->cfg_vec && box_vec_ok(e, b);
                 if ((var == 1) != v) continue;
-                const int nb = v ? 128 : e->cfg_nb[a];
+                const int nb = e->cfg_nb[a];
                 int nlane, nblk;
                 pencils_along(e->box[b], a, &nlane, &nblk);
                 const int nlb = (nlane + nb - 1) / nb;
@@ -1873,10 +1873,10 @@ int ens_launch_pass(ppm_ens *e, int pass) {
         const int nw = e->nwork[a][var];
         if (nw == 0) continue;
         const int vec = var;
-        const int nb = vec ? 128 : (f32 ? e->cfg_nb[a] : 128);
+        const int nb = f32 ? e->cfg_nb[a] : 128;
         const int pers = e->cfg_pers[a];
         int grid = nw;
-        if (pers) grid = std::min(nw, e->nsm * e->bps[vec ? 2 : (nb == 64 ? 0 : 1)]);
+        if (pers) grid = std::min(nw, e->nsm * e->bps[vec][nb == 32 ? 0 : (nb == 64 ? 1 : 2)]);
         // passes 2 and 5 carry the sources, pass 5 the CFL maximum
         const int nsrc = (pass != 2 && pass != 5) ? 1 : 0;
         launch_sweep_ensemble(f32, vec, nb, nsrc, args, e->d_work + e->work_off[a][var], nw,
@@ -2072,9 +2072,8 @@ int ppm_ensemble_create(ppm_ens **out, int nbox, const ppm_box *boxes, double ga
         int nsm = 0;
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
         e->nsm = nsm > 0 ? nsm : 152;
-        e->bps[0] = ensemble_blocks_per_sm(f32, 0, 64);
-        e->bps[1] = ensemble_blocks_per_sm(f32, 0, 128);
-        e->bps[2] = ensemble_blocks_per_sm(f32, 1, 128);
+        for (int v = 0; v < 2; ++v)
+            for (int i = 0; i < 3; ++i) e->bps[v][i] = ensemble_blocks_per_sm(f32, v, 32 << i);
         e->bps1 = ensemble_step_blocks_per_sm(f32);
     }
     const int rc = build_work(e);
@@ -2168,7 +2167,7 @@ int ppm_ensemble_sync(ppm_ens *e) {
 
 int ppm_ensemble_set_config(ppm_ens *e, int axis, int block, int persistent, int vec) {
     if (!e || axis < 0 || axis > 2) return efail(e, PPM_EINVAL, "bad axis");
-    if (block != 64 && block != 128) return efail(e, PPM_EINVAL, "block must be 64 or 128");
+    if (block != 32 && block != 64 && block != 128) return efail(e, PPM_EINVAL, "block must be 32, 64 or 128");
     if (e->prec != PPM_FP32_DEVIATION && block != 128) return efail(e, PPM_EINVAL, "FP64 passes use 128-thread blocks");
     e->cfg_nb[axis] = block;
     e->cfg_pers[axis] = persistent ? 1 : 0;
@@ -2276,9 +2275,9 @@ int ppm_ensemble_tune(ppm_ens *e, const char *cache_path, int *from_cache) {
     for (int a = 0; a < 3 && rc == PPM_OK; ++a) {
         float best = 1e30f;
         int bnb = 128, bpers = 1, bvec = e->cfg_vec;
-        const int nbs[2] = {64, 128};
+        const int nbs[3] = {32, 64, 128};
         for (int vec = (a == 0 && f32) ? 1 : e->cfg_vec; vec >= 0 && rc == PPM_OK; --vec) {
-            for (int ib = (f32 ? 0 : 1); ib < 2 && rc == PPM_OK; ++ib) {
+            for (int ib = (f32 ? 0 : 2); ib < 3 && rc == PPM_OK; ++ib) {
                 for (int pers = 0; pers < 2 && rc == PPM_OK; ++pers) {
                     e->cfg_nb[a] = nbs[ib];
                     e->cfg_pers[a] = pers;

@@ -17,28 +17,33 @@ static cudaError_t set_smem_f32() {
 
 cudaError_t prepare_sweep_ensemble() {
     cudaError_t e;
+    if ((e = set_smem_f32<false, 32>()) != cudaSuccess) return e;
     if ((e = set_smem_f32<false, 64>()) != cudaSuccess) return e;
     if ((e = set_smem_f32<false, 128>()) != cudaSuccess) return e;
+    if ((e = set_smem_f32<true, 32>()) != cudaSuccess) return e;
+    if ((e = set_smem_f32<true, 64>()) != cudaSuccess) return e;
     if ((e = set_smem_f32<true, 128>()) != cudaSuccess) return e;
     return cudaFuncSetAttribute(sweep_ensemble_kernel<double, true, false, 128>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, sweep_smem_bytes<double, false, 128>());
 }
 
 // Resident blocks per SM of a variant (for sizing a persistent grid).
+template <bool VEC, int NB>
+static int bps_f32() {
+    int nblk = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nblk, sweep_ensemble_kernel<float, false, VEC, NB, false>, NB,
+                                                  sweep_smem_bytes<float, VEC, NB>());
+    return nblk;
+}
 int ensemble_blocks_per_sm(int f32, int vec, int nb) {
     int nblk = 0;
     if (!f32)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nblk, sweep_ensemble_kernel<double, true, false, 128>, 128,
                                                       sweep_smem_bytes<double, false, 128>());
     else if (vec)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nblk, sweep_ensemble_kernel<float, false, true, 128>, 128,
-                                                      sweep_smem_bytes<float, true, 128>());
-    else if (nb == 64)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nblk, sweep_ensemble_kernel<float, false, false, 64>, 64,
-                                                      sweep_smem_bytes<float, false, 64>());
+        nblk = (nb == 32) ? bps_f32<true, 32>() : (nb == 64) ? bps_f32<true, 64>() : bps_f32<true, 128>();
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nblk, sweep_ensemble_kernel<float, false, false, 128>, 128,
-                                                      sweep_smem_bytes<float, false, 128>());
+        nblk = (nb == 32) ? bps_f32<false, 32>() : (nb == 64) ? bps_f32<false, 64>() : bps_f32<false, 128>();
     return nblk > 0 ? nblk : 1;
 }
 
@@ -62,7 +67,11 @@ void launch_sweep_ensemble(int f32, int vec, int nb, int nsrc, const void *args,
         sweep_ensemble_kernel<double, true, false, 128><<<grid, 128, sweep_smem_bytes<double, false, 128>(), st>>>(
             static_cast<const SweepArgs<double> *>(args), work, nwork, counter, persistent);
     } else if (vec) {
-        launch_f32<true, 128>(nsrc != 0, args, work, nwork, counter, persistent, grid, st);
+        if (nb == 32) launch_f32<true, 32>(nsrc != 0, args, work, nwork, counter, persistent, grid, st);
+        else if (nb == 64) launch_f32<true, 64>(nsrc != 0, args, work, nwork, counter, persistent, grid, st);
+        else launch_f32<true, 128>(nsrc != 0, args, work, nwork, counter, persistent, grid, st);
+    } else if (nb == 32) {
+        launch_f32<false, 32>(nsrc != 0, args, work, nwork, counter, persistent, grid, st);
     } else if (nb == 64) {
         launch_f32<false, 64>(nsrc != 0, args, work, nwork, counter, persistent, grid, st);
     } else {

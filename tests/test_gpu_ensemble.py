@@ -39,6 +39,10 @@ CONFIGS = [
     [(64, 0, 0), (64, 0, 0), (64, 0, 0)],
     [(128, 0, 1), (64, 1, 0), (128, 0, 0)],
     [(64, 1, 0), (128, 0, 0), (64, 1, 0)],
+    # 32-pencil blocks, and the x-pass vector path in 32- and 64-pencil blocks
+    [(32, 0, 1), (32, 1, 0), (32, 0, 0)],
+    [(64, 1, 1), (32, 0, 0), (64, 0, 0)],
+    [(32, 1, 0), (128, 1, 0), (32, 1, 0)],
 ]
 
 
@@ -109,7 +113,7 @@ def test_tuner_keeps_states_and_uses_cache(tmp_path):
         for v in range(9):
             assert np.array_equal(before[b][v], after[b][v])
     for ax in "xyz":
-        assert cfg[ax][0] in (64, 128)
+        assert cfg[ax][0] in (32, 64, 128)
     ens.cfl_dt(0.7, fetch=False)
     ens.step(0.0)
     ens.sync()
