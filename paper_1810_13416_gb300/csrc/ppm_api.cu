@@ -77,6 +77,7 @@ struct ppm_ctx {
     double shock_k;            // 3-D shock dissipation coefficient (0 = off)
     long long graph_kernels;   // kernels in the step graph
     void *divg;                // its per-pass cell divergence (ncell values)
+    void *vel;                 // FP32: the cell velocities the y/z passes of a step leave (3 x ncell)
     int has_heat, has_damp;
     int device;
     cudaStream_t stream;
@@ -202,11 +203,15 @@ SweepArgs<R> make_args(ppm_ctx *c, int axis) {
     return a;
 }
 
-int launch_divergence(ppm_ctx *c);
+int launch_divergence(ppm_ctx *c, bool from_vel);
 
-int launch_sweep(ppm_ctx *c, int axis, int sources, int cfl) {
+// vel: (shock dissipation, FP32) 1 = this pass leaves the cell velocities
+// for the next pass's divergence, 2 = its divergence takes them from the pass
+// before, 3 = both (a step's passes Y Z Z Y write, Z Z Y X read); 0 for a
+// single pass
+int launch_sweep(ppm_ctx *c, int axis, int sources, int cfl, int vel) {
     if (c->divg) {
-        const int r = launch_divergence(c);
+        const int r = launch_divergence(c, (vel & 2) && c->vel);
         if (r != PPM_OK) return r;
     }
     dim3 block(SWEEP_BLOCK);
@@ -214,6 +219,7 @@ int launch_sweep(ppm_ctx *c, int axis, int sources, int cfl) {
         SweepArgs<float> a = make_args<float>(c, axis);
         a.sources = sources;
         a.cfl = cfl;
+        if ((vel & 1) && c->vel && !a.vec_x) a.vel_out = static_cast<float *>(c->vel);
         dim3 grid((a.nlane + SWEEP_BLOCK - 1) / SWEEP_BLOCK, a.nblk);
         if (c->design[axis] == PPM_PASS_TILE && c->tile_ok)
             launch_tile_f32(a, &c->tmap[axis], c->stream);
@@ -863,15 +869,127 @@ __global__ void __launch_bounds__(DIV_NT, 2) divergence_ring_kernel(SweepArgs<fl
     cp_wait<0>();
 }
 
-int launch_divergence(ppm_ctx *c) {
+// The same divergence from the cell velocities the pass before left
+// (`SweepArgs::vel_out`: u_x, u_y, u_z arrays, the quotient and products of
+// the full form above taken in that pass): no table lookup and no quotient
+// here; a halo cell needs one component.  Ghosts as above.
+constexpr int DV_RV = 4;   // ring values per thread and plane: u, v, w; the halo component
+constexpr int div_vel_smem() { return DIV_PF * DV_RV * DIV_NT * (int)sizeof(float); }
+
+__global__ void __launch_bounds__(DIV_NT, 2) divergence_vel_kernel(const float *vel, float *D, double dx,
+                                                                   long long ncell, int nx, int ny, int nz, int bx0,
+                                                                   int bx1, int by0, int by1, int bz0, int bz1) {
+    extern __shared__ __align__(16) float ring[];   // [DIV_PF][DV_RV][DIV_NT]
+    __shared__ float ux[2][DIV_TY + 2][DIV_TX + 2];
+    __shared__ float uy[2][DIV_TY + 2][DIV_TX + 2];
+    const int tx = threadIdx.x, ty = threadIdx.y, t = ty * DIV_TX + tx;
+    const int i = blockIdx.x * DIV_TX + tx, j = blockIdx.y * DIV_TY + ty;
+    const int k0 = blockIdx.z * DIV_ZRUN, k1 = min(nz, k0 + DIV_ZRUN);
+    const float h = (float)(0.5 / dx);
+    struct Col {
+        long long xy;     // x-y offset of the mapped cell in a plane
+        unsigned sx, sy;  // sign-bit masks of u and v
+    };
+    auto column = [&](int gi, int gj) -> Col {
+        Col c;
+        bool fx = false, fy = false;
+        const int ii = map_cell(gi, nx, bx0, bx1, fx), jj = map_cell(gj, ny, by0, by1, fy);
+        c.xy = (long long)jj * nx + ii;
+        c.sx = fx ? 0x80000000u : 0u;
+        c.sy = fy ? 0x80000000u : 0u;
+        return c;
+    };
+    auto flipf = [](float v, unsigned m) { return __uint_as_float(__float_as_uint(v) ^ m); };
+    const long long plane_cells = (long long)nx * ny;
+    // slots and halo as in the full form
+    const bool own = (i < nx && j < ny);
+    const bool slot_ok = i <= nx && j <= ny && !(i == nx && j == ny);
+    int hx = -1, hy = -1;
+    if (t < 2 * DIV_TX) {
+        hx = (t % DIV_TX) + 1;
+        hy = (t < DIV_TX) ? 0 : DIV_TY + 1;
+    } else if (t < 2 * DIV_TX + 2 * DIV_TY) {
+        const int r = t - 2 * DIV_TX;
+        hy = (r % DIV_TY) + 1;
+        hx = (r < DIV_TY) ? 0 : DIV_TX + 1;
+    }
+    const bool halo_u = (t >= 2 * DIV_TX);
+    const int gi = blockIdx.x * DIV_TX + hx - 1, gj = blockIdx.y * DIV_TY + hy - 1;
+    const bool halo_ok = hx >= 0 && gi >= -1 && gi <= nx && gj >= -1 && gj <= ny;
+    const Col col_own = column(slot_ok ? i : 0, slot_ok ? j : 0);
+    const Col col_halo = column(halo_ok ? gi : 0, halo_ok ? gj : 0);
+    auto issue = [&](int gk, int sl) {
+        if (gk <= k1) {
+            float *r = ring + (sl * DV_RV) * DIV_NT + t;
+            if (slot_ok) {
+                bool fz = false;
+                const int kk = map_cell(gk, nz, bz0, bz1, fz);
+                const float *p = vel + (long long)kk * plane_cells + col_own.xy;
+                cp_async<4>(r, p);
+                cp_async<4>(r + DIV_NT, p + ncell);
+                cp_async<4>(r + 2 * DIV_NT, p + 2 * ncell);
+            }
+            if (halo_ok && gk >= k0 && gk < k1)
+                cp_async<4>(r + 3 * DIV_NT, vel + (halo_u ? 0 : ncell) + (long long)gk * plane_cells + col_halo.xy);
+        }
+        cp_commit();
+    };
+#pragma unroll
+    for (int sl = 0; sl < DIV_PF; ++sl) issue(k0 - 1 + sl, sl);
+    float wm = 0.0f, w0 = 0.0f;   // u_z of planes q-2 and q-1
+    for (int q = k0 - 1; q <= k1; ++q) {
+        const int sl = (q - (k0 - 1)) & (DIV_PF - 1);
+        cp_wait<DIV_PF - 1>();
+        const float *r = ring + (sl * DV_RV) * DIV_NT + t;
+        float u = 0.0f, v = 0.0f, w = 0.0f, hv = 0.0f;
+        if (slot_ok) {
+            bool fz = false;
+            (void)map_cell(q, nz, bz0, bz1, fz);
+            u = flipf(r[0], col_own.sx);
+            v = flipf(r[DIV_NT], col_own.sy);
+            w = flipf(r[2 * DIV_NT], fz ? 0x80000000u : 0u);
+        }
+        const bool hq = halo_ok && q >= k0 && q < k1;
+        if (hq) hv = flipf(r[3 * DIV_NT], halo_u ? col_halo.sx : col_halo.sy);
+        issue(q + DIV_PF, sl);
+        if (q >= k0 && q < k1) {
+            const int b = q & 1;
+            ux[b][ty + 1][tx + 1] = u;
+            uy[b][ty + 1][tx + 1] = v;
+            if (hq) {
+                if (halo_u)
+                    ux[b][hy][hx] = hv;
+                else
+                    uy[b][hy][hx] = hv;
+            }
+        }
+        if (q > k0 && own) {
+            const int b = (q - 1) & 1;
+            const float dxu = ux[b][ty + 1][tx + 2] - ux[b][ty + 1][tx];
+            const float dyv = uy[b][ty + 2][tx + 1] - uy[b][ty][tx + 1];
+            D[((long long)(q - 1) * ny + j) * nx + i] = ((dxu + dyv) + (w - wm)) * h;
+        }
+        wm = w0;
+        w0 = w;
+        __syncthreads();
+    }
+    cp_wait<0>();
+}
+
+int launch_divergence(ppm_ctx *c, bool from_vel) {
     const int g = grid_for(c->ncell, 256);
     const int *b = c->bc;
     if (c->prec == PPM_FP32_DEVIATION) {
         const dim3 grid((c->n[0] + DIV_TX - 1) / DIV_TX, (c->n[1] + DIV_TY - 1) / DIV_TY,
                         (c->n[2] + DIV_ZRUN - 1) / DIV_ZRUN);
-        divergence_ring_kernel<<<grid, dim3(DIV_TX, DIV_TY), div_ring_smem(), c->stream>>>(
-            make_args<float>(c, 0), (const float *)c->state, (float *)c->divg, c->ncell, c->n[0], c->n[1], c->n[2],
-            b[0], b[1], b[2], b[3], b[4], b[5]);
+        if (from_vel)
+            divergence_vel_kernel<<<grid, dim3(DIV_TX, DIV_TY), div_vel_smem(), c->stream>>>(
+                (const float *)c->vel, (float *)c->divg, c->dx, c->ncell, c->n[0], c->n[1], c->n[2], b[0], b[1],
+                b[2], b[3], b[4], b[5]);
+        else
+            divergence_ring_kernel<<<grid, dim3(DIV_TX, DIV_TY), div_ring_smem(), c->stream>>>(
+                make_args<float>(c, 0), (const float *)c->state, (float *)c->divg, c->ncell, c->n[0], c->n[1],
+                c->n[2], b[0], b[1], b[2], b[3], b[4], b[5]);
     } else
         divergence_kernel<double, true><<<g, 256, 0, c->stream>>>(make_args<double>(c, 0), (const double *)c->state,
                                                                   (double *)c->divg, c->ncell, c->n[0], c->n[1], c->n[2],
@@ -1068,6 +1186,7 @@ void release(ppm_ctx *c) {
     if (c->graph) cudaGraphDestroy(c->graph);
     if (c->state) cudaFree(c->state);
     if (c->divg) cudaFree(c->divg);
+    if (c->vel) cudaFree(c->vel);
     if (c->t64) cudaFree(c->t64);
     if (c->t32) cudaFree(c->t32);
     if (c->t4) cudaFree(c->t4);
@@ -1205,6 +1324,13 @@ int ppm_create(ppm_ctx **out, int nx, int ny, int nz, double gamma, const int bc
         fail(c, PPM_ENOMEM, "cannot allocate the divergence buffer");
         return bail(PPM_ENOMEM);
     }
+    if (c->shock_k > 0.0 && c->prec == PPM_FP32_DEVIATION &&
+        cudaMalloc(&c->vel, (size_t)3 * c->ncell * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        c->vel = nullptr;
+        fail(c, PPM_ENOMEM, "cannot allocate the velocity buffer");
+        return bail(PPM_ENOMEM);
+    }
     const int nt = grav->ntab;
     std::vector<double> h64((size_t)5 * nt, 0.0);
     std::vector<float> h32((size_t)5 * nt, 0.0f);
@@ -1275,6 +1401,8 @@ int ppm_create(ppm_ctx **out, int nx, int ny, int nz, double gamma, const int bc
         prepare_sweep_ensemble() != cudaSuccess ||
         cudaFuncSetAttribute(divergence_ring_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              div_ring_smem()) != cudaSuccess ||
+        cudaFuncSetAttribute(divergence_vel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             div_vel_smem()) != cudaSuccess ||
         cudaMemset(c->ds_dev, 0, sizeof(DevScal)) != cudaSuccess ||
         cudaMemset(c->state, 0, sbytes) != cudaSuccess) {
         fail(c, PPM_ECUDA, "initialising device buffers failed");
@@ -1399,7 +1527,7 @@ int ppm_tune(ppm_ctx *c, const char *cache_path, int *from_cache) {
             float ms = 0.0f;
             for (int rep = 0; rep < 3 && rc == PPM_OK; ++rep) {
                 cudaEventRecord(t0, c->stream);
-                rc = launch_sweep(c, a, 0, 0);
+                rc = launch_sweep(c, a, 0, 0, 0);
                 cudaEventRecord(t1, c->stream);
                 if (rc == PPM_OK && cudaMemcpyAsync(c->state, snap, bytes, cudaMemcpyDeviceToDevice, c->stream) !=
                                         cudaSuccess)
@@ -1547,7 +1675,10 @@ static int capture_step(ppm_ctx *c) {
     cudaError_t er = cudaEventRecordWithFlags(c->pev[0], c->stream, cudaEventRecordExternal);
     for (int s = 0; s < 6 && rc == PPM_OK && er == cudaSuccess; ++s) {
         const int src = (s == 2 || s == 5) ? ((c->has_heat || c->has_damp) ? 1 : 0) : 0;
-        rc = launch_sweep(c, order[s], src, s == 5 ? 1 : 0);
+        // the y and z passes leave the cell velocities for the divergence
+        // before the next pass (passes 2..5 take them)
+        const int vel = (s >= 1 && s <= 4 ? 1 : 0) | (s >= 2 ? 2 : 0);
+        rc = launch_sweep(c, order[s], src, s == 5 ? 1 : 0, vel);
         if (rc == PPM_OK) er = cudaEventRecordWithFlags(c->pev[s + 1], c->stream, cudaEventRecordExternal);
     }
     if (rc == PPM_OK && er != cudaSuccess) rc = fail(c, PPM_ECUDA, "event record in capture: %s", cudaGetErrorString(er));
@@ -1610,7 +1741,7 @@ int ppm_sweep(ppm_ctx *c, int axis, double dt, int sources) {
     c->launches++;
     CK(c, cudaGetLastError());
     if (sources < 0 || sources > 3) return fail(c, PPM_EINVAL, "sources must be 0..3");
-    int r = launch_sweep(c, axis, (sources & 1) && (c->has_heat || c->has_damp) ? 1 : 0, 0);
+    int r = launch_sweep(c, axis, (sources & 1) && (c->has_heat || c->has_damp) ? 1 : 0, 0, 0);
     c->have_speed = false;
     if (r == PPM_OK && (sources & 2) && c->domega != 0.0) r = launch_rotate(c, false);
     return r;

@@ -77,6 +77,7 @@ struct SweepArgs {
     double confine_r;     // > 0: confining sphere; each pencil updates its fluid run only
     int ten;              // ten-value PPB (15 stored values per cell)
     const R *divg;        // 3-D shock dissipation: cell velocity divergence (NULL: off)
+    R *vel_out;           // FP32 y/z passes with it: the final cell velocities (x, y, z arrays), else NULL
     double shock_k;       // its coefficient K
     double gamma;
     const double *dt;     // device time step
@@ -1364,6 +1365,16 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<R> &A, int lane_block
             {
                 const R ri = qdiv((R)1, rnew);
                 const R uu = mno * ri, vv = m1o * ri, wv_ = m2o * ri;
+                if constexpr (DISS && F32 && !VEC) {
+                    // the final velocities of the cell, for the next pass's
+                    // divergence (the same quotient and products it would take)
+                    if (A.vel_out) {
+                        R *vp = A.vel_out + (q - A.q) + (long long)i * sa;
+                        vp[(long long)ax * vs] = uu;
+                        vp[(long long)t1d * vs] = vv;
+                        vp[(long long)t2d * vs] = wv_;
+                    }
+                }
                 const R kin = (R)0.5 * (mno * uu + (m1o * vv + m2o * wv_));
                 const R pr = wp0[0] + gm1 * (edo - kin);
                 if (!(rnew > (R)0) || !(pr > (R)0)) bad = true;
