@@ -106,7 +106,10 @@ typedef struct {
                               with nu = K max(0, -div(u) dx - 0.05 c) (divergence averaged to
                               the face, c the mean sound speed of the traced states); mass is
                               not diffused.  0 = off; not combined with confine_r or nmom 9
-                              (EINVAL). */
+                              (EINVAL).  Device memory: 4 B per cell for the divergence, and in
+                              FP32 12 B per cell more for the cell velocities that the y and z
+                              passes of ppm_step leave for the divergence before the next pass
+                              (equal to the one taken from the state up to FP32 rounding). */
     int halo_z;            /* z slab of a larger grid (domain decomposition, Sec. 4/5: a grid
                               brick is updated from its neighbours' boundary planes): bit 0 /
                               bit 1 = the low / high z face takes 4 halo planes from the caller
