@@ -337,8 +337,8 @@ def run_ours(args):
                 "frac": achieved / hbm_peak,
                 "traffic": (tr * ncell if tr is not None else None),
                 "kernel": "fused PPM+PPB pass, per axis: " + ", ".join(
-                    f"{ax}: " + ("ppm::tile::tile_pass_kernel<AX> (cell-parallel tiles, TMA)" if d == ppm.PASS_TILE
-                                 else "ppm::sweep_kernel<float,0,VEC,0,0,0,128> (register-window march)")
+                    f"{ax}: " + ("ppm::tile::tile_pass_kernel<AX,FULL> (cell-parallel tiles, TMA)" if d == ppm.PASS_TILE
+                                 else "ppm::sweep_kernel<float,0,VEC,0,0,0,128,0,NSRC> (register-window march)")
                     for ax, d in zip("xyz", ctx_designs)),
                 "tuned": tune_info,
                 "algorithmic_bytes_per_launch": BYTES_PER_CELL_PASS["f32"] * ncell,
